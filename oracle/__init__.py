@@ -1,0 +1,21 @@
+"""FP64 CPU oracle for the coarse-grid correction of two-level DD-alpha-AMG.
+
+TEST INFRASTRUCTURE ONLY.  This package is the plain, slow, obviously correct
+statement of what the GPU library computes; it exists so the tests (and the
+benchmark's CPU-baseline leg) can check the CUDA path against it.  Nothing in
+the product path imports it, and it imports nothing from the product path.
+
+Modules (each function cites the passage of arXiv:1512.04506 it follows):
+
+* ``lattice`` -- geometry: blocks, aggregates, coarse neighbours (Sec. 2).
+* ``dirac``   -- gamma matrices, clover field, Wilson-clover D (Alg. 7 terms).
+* ``coarse``  -- Gram-Schmidt on aggregates, R, P = R^dagger, D_c = R D P,
+                 restriction, coarse-operator application, prolongation
+                 (Alg. 2, Alg. 5, Eq. R, Eq. cgo, Eq. dagger).
+* ``krylov``  -- the restarted FGMRES coarse solve of Alg. 2.
+
+All arithmetic is complex128.  Where the paper is silent (gamma basis, sign
+and normalisation of D, the clover term, boundary conditions) the readings
+are fixed in each function's docstring and pinned by tests/test_oracle_*.py
+against closed forms and brute force, not against this code.
+"""
