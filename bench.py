@@ -1,0 +1,379 @@
+"""Benchmark: coarse-grid correction throughput (GB/s) on one GB300 (replicas on N GPUs).
+
+One step is one coarse-grid correction of Alg. 2 on the 32^4 lattice with 4^4
+blocks (8^4 coarse sites) and N_tv = 20, FP64 setup and FP32 storage:
+restriction y_c = R y, restarted FGMRES(30) on D_c to relative residual 0.05
+(at most 200 applications), prolongation x = P x_c.  The value is the step's
+algorithmic bytes (every byte each kernel must move at least once: R twice,
+D_c once per application, the vectors of the Krylov basis for the
+Gram-Schmidt) divided by the step time.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--impl reference times the FP64 CPU oracle on the host cores instead, on a
+bounded sample of the same workload.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+L = (32, 32, 32, 32)
+B = (4, 4, 4, 4)
+NTV = 20
+EPS, M0, CSW = 0.3, -0.3, 1.0
+SEED = 20151204 + 2
+TOL, RESTART, MAX_APPLIES = 0.05, 30, 200
+METRIC = "coarse-grid correction GB/s & % HBM roofline; batched-mixed vs plain speedup"
+WORKLOAD = "fp32_32^4_b4_ntv20: 32^4 Wilson-clover, 4^4 blocks -> 8^4 coarse, Ntv=20, 1 RHS, " \
+           "FP64 setup, FP32 R and D_c; step = R y, FGMRES(30) to 0.05 (<=200 applies), P x_c"
+
+
+def geometry():
+    V = int(np.prod(L))
+    Vb = int(np.prod(B))
+    Vc = V // Vb
+    nc = 2 * NTV
+    return V, Vb, Vc, nc
+
+
+def bytes_model(applies, cycles_iters, elem=8):
+    """Algorithmic bytes of one step (FP32 complex = 8 B)."""
+    V, Vb, Vc, nc = geometry()
+    vec_c = Vc * nc * elem
+    vec_f = V * 12 * elem
+    R = Vc * 2 * NTV * 6 * Vb * elem
+    restrict = R + vec_f + vec_c
+    prolong = R + vec_c + vec_f
+    apply_ = Vc * 9 * nc * nc * elem + 2 * vec_c
+    # Arnoldi step j: dots read w and V_0..V_j, update reads w, V_0..V_j and writes w, scale r/w
+    gs = sum((2 * (j + 1) + 4) * vec_c for j in cycles_iters)
+    return restrict + prolong + applies * apply_ + gs, {"restrict": restrict, "apply": apply_, "prolong": prolong}
+
+
+def arnoldi_iterations(applies):
+    """Arnoldi step indices j of the FGMRES(RESTART) run with `applies` applications."""
+    its = []
+    left = applies
+    while left > 0:
+        m = min(RESTART, left)
+        its += list(range(m))
+        left -= m + 1  # one residual application per restart
+    return its
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index):
+        self.proc = None
+        self.index = index
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.samples = []
+        if self.proc is None:
+            return
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 8:
+                self.samples.append(f)
+
+    def summary(self):
+        if not getattr(self, "samples", None):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4) if s[4 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_gpu(args):
+    import torch
+    import paper_1512_04506_gb300 as amg
+    from synth import device as sd
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    V, Vb, Vc, nc = geometry()
+    stream = torch.cuda.current_stream()
+    seed = SEED + 1000 * rank  # independent replica per rank
+    U = sd.links(seed, EPS, L)
+    tv = sd.test_vectors(seed, NTV, L)
+    p = amg.make_params(L, B, NTV, 1, M0, CSW, amg.AMG_FP32, amg.AMG_FP32, amg.AMG_FP32)
+    h, _ = amg.amg_setup_coarse(p, U, tv, stream)
+    setup_ms = amg.amg_setup_timings(h)
+    del U, tv
+    torch.cuda.empty_cache()
+    y = sd.fine_rhs(seed, 1, L, torch.complex64)
+    x = torch.empty_like(y)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        return amg.amg_cgc(h, y, x, 1, TOL, RESTART, MAX_APPLIES, stream, info=False)
+
+    info = amg.amg_cgc(h, y, x, 1, TOL, RESTART, MAX_APPLIES, stream, info=True)
+    applies = info[0][0]
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    # ---- device-resident timed region
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = amg.amg_kernel_launches(h)
+    with Clocks(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    launches = amg.amg_kernel_launches(h) - launches0
+    if dist:
+        dist.barrier()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    t_total = sum(ms) / 1000.0
+    step_bytes, parts = bytes_model(applies, arnoldi_iterations(applies))
+    # ---- per-kernel live timing (events around each launch on the launching stream)
+    yc = torch.empty((Vc, 2, NTV, 1), dtype=torch.complex64, device="cuda")
+    zc = torch.empty_like(yc)
+    amg.amg_restrict(h, y, yc, 1, stream)
+
+    def timed(fn, n):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+        for _ in range(3):
+            fn()
+        for a, b in evs:
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in evs) / n / 1000.0
+
+    t_apply = timed(lambda: amg.amg_coarse_apply(h, yc, zc, 1, stream), 50)
+    t_restrict = timed(lambda: amg.amg_restrict(h, y, yc, 1, stream), 20)
+    t_prolong = timed(lambda: amg.amg_prolong(h, yc, x, 1, stream), 20)
+    # ---- end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    yh = y.cpu().pin_memory()
+    xh = torch.empty_like(yh).pin_memory()
+    yd = torch.empty_like(y)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        yd.copy_(yh, non_blocking=True)
+        amg.amg_cgc(h, yd, x, 1, TOL, RESTART, MAX_APPLIES, stream, info=False)
+        xh.copy_(x, non_blocking=True)
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    status = amg.amg_sync_status(h)
+    amg.amg_destroy(h)
+    if status != amg.AMG_OK:
+        raise RuntimeError("device error: %s" % amg.amg_status_string(status))
+    if dist:
+        t = torch.tensor([t_total, t_e2e], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_total, t_e2e = t.tolist()
+    value = world * step_bytes * args.steps / t_total / 1e9
+    e2e_value = world * step_bytes * args.steps / t_e2e / 1e9
+    peaks, src = measured_peaks()
+    apply_bytes = parts["apply"]
+    achieved = apply_bytes / t_apply / 1e9
+    result = {
+        "metric": METRIC,
+        "value": round(value, 2),
+        "unit": "GB/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(1000.0 * t_total / args.steps, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "L": list(L), "B": list(B), "ntv": NTV, "nrhs": 1,
+                   "coarse_solve": "FGMRES(%d) to %g, max %d applies" % (RESTART, TOL, MAX_APPLIES),
+                   "applies_per_step": applies, "bytes_per_step": step_bytes,
+                   "l2": "inputs larger than L2 (R %.2f GB, D_c %.2f GB) and a 256 MB flush before each step"
+                         % (parts["restrict"] / 1e9, Vc * 9 * nc * nc * 8 / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": {"bound": "hbm", "kernel": "coarse apply (FP32 links)", "achieved": round(achieved, 1),
+                     "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
+                     "peak_source": src, "traffic": None,
+                     "bytes_per_launch": apply_bytes, "avg_launch_us": round(t_apply * 1e6, 2)},
+        "kernels": {
+            "restrict": {"GB/s": round(parts["restrict"] / t_restrict / 1e9, 1), "us": round(t_restrict * 1e6, 1),
+                         "frac": round(parts["restrict"] / t_restrict / 1e9 / peaks["hbm_gbs"], 4)},
+            "apply": {"GB/s": round(achieved, 1), "us": round(t_apply * 1e6, 1),
+                      "frac": round(achieved / peaks["hbm_gbs"], 4)},
+            "prolong": {"GB/s": round(parts["prolong"] / t_prolong / 1e9, 1), "us": round(t_prolong * 1e6, 1),
+                        "frac": round(parts["prolong"] / t_prolong / 1e9 / peaks["hbm_gbs"], 4)},
+        },
+        "setup_ms": {"clover": round(setup_ms[0], 2), "gram_schmidt": round(setup_ms[1], 2),
+                     "assembly": round(setup_ms[2], 2), "quantise": round(setup_ms[3], 2)},
+        "e2e": {"value": round(e2e_value, 2), "unit": "GB/s", "h2d_bytes_per_step": V * 12 * 8,
+                "d2h_bytes_per_step": V * 12 * 8},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(applies)
+    if dist:
+        dist.destroy_process_group()
+    return result, rank
+
+
+def cpu_sample(applies, target_s=15.0):
+    """The oracle's restrict, FGMRES(coarse apply) and prolong on a sample lattice.
+
+    Sample: a 16^4 lattice with the workload's 4^4 blocks and N_tv = 20 (256
+    coarse sites, 1/16 of the workload), random orthonormal R and random D_c
+    blocks (the cost of these loops does not depend on the values), the
+    workload's number of D_c applications; repeated until target_s seconds.
+    Returns (GB/s in the workload's byte model per sample volume, seconds, repeats).
+    """
+    from oracle import coarse, krylov, lattice as lat
+    Ls = (16, 16, 16, 16)
+    Lc = lat.coarse_dims(Ls, B)
+    Vc = int(np.prod(Lc))
+    Vb = int(np.prod(B))
+    rng = np.random.default_rng(0)
+    W = rng.normal(size=(Vc, 2, 6 * Vb, NTV)) + 1j * rng.normal(size=(Vc, 2, 6 * Vb, NTV))
+    Q = np.linalg.qr(W)[0]
+    Dc = (rng.normal(size=(Vc, 9, 2 * NTV, 2 * NTV)) + 1j * rng.normal(size=(Vc, 9, 2 * NTV, 2 * NTV))) / 40
+    Dc[:, 0] += 4 * np.eye(2 * NTV)
+    y = rng.normal(size=(16, 16, 16, 16, 4, 3)) + 1j * rng.normal(size=(16, 16, 16, 16, 4, 3))
+    reps = 0
+    t0 = time.perf_counter()
+    while True:
+        yc = coarse.restrict(Q, y, B)
+        xc, _, _ = krylov.fgmres(lambda v: coarse.coarse_apply(Dc, v, Lc), yc, tol=0.0, restart=RESTART,
+                                 max_applies=applies)
+        coarse.prolong(Q, xc, Ls, B)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= target_s or reps >= 50:
+            break
+    # byte model of the sample (FP64 data: 16 B per complex)
+    Vs = int(np.prod(Ls))
+    nc = 2 * NTV
+    vec_c, vec_f = Vc * nc * 16, Vs * 12 * 16
+    R = Vc * 2 * NTV * 6 * Vb * 16
+    gs = sum((2 * (j + 1) + 4) * vec_c for j in arnoldi_iterations(applies))
+    sample_bytes = 2 * (R + vec_f + vec_c) + applies * (Vc * 9 * nc * nc * 16 + 2 * vec_c) + gs
+    return sample_bytes * reps / el / 1e9, el, reps
+
+
+def cpu_baseline(applies):
+    cores = len(os.sched_getaffinity(0))
+    gbs, el, reps = cpu_sample(applies)
+    return {"value": round(gbs, 3), "unit": "GB/s", "cores": cores, "kind": "oracle",
+            "sample": "oracle (numpy FP64) R y, FGMRES(%d) with %d D_c applications, P x_c on a 16^4 lattice "
+                      "(4^4 blocks, Ntv=20, 1/16 of the workload), %d repetitions in %.1f s; "
+                      "numpy's own threading (cores = threads available)" % (RESTART, applies, reps, el)}
+
+
+def run_reference(args):
+    world, rank, local = dist_setup()
+    if rank != 0:
+        return None, rank
+    applies = MAX_APPLIES
+    times = []
+    for _ in range(args.warmup + args.steps):
+        gbs, el, reps = cpu_sample(applies, target_s=0.0)
+        times.append((gbs, el))
+    run = times[args.warmup:]
+    tot_el = sum(t[1] for t in run)
+    value = statistics.mean(t[0] for t in run)
+    cores = len(os.sched_getaffinity(0))
+    sample = ("oracle (numpy FP64) R y, FGMRES(%d) with %d D_c applications, P x_c on a 16^4 lattice "
+              "(4^4 blocks, Ntv=20): one sample per step" % (RESTART, applies))
+    res = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": round(value, 3),
+        "unit": "GB/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(1000 * tot_el / max(1, len(run)), 2),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "L": list(L), "B": list(B), "ntv": NTV, "nrhs": 1},
+        "cpu_baseline": {"value": round(value, 3), "unit": "GB/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 3), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    return res, rank
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        res, rank = run_reference(args)
+    else:
+        res, rank = run_gpu(args)
+    if rank == 0 and res is not None:
+        print(json.dumps(res))
+
+
+if __name__ == "__main__":
+    main()

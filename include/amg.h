@@ -1,0 +1,163 @@
+/*
+ * amg.h -- C ABI of libamg: the coarse-grid correction of two-level
+ * DD-alpha-AMG (Heybrock, Rottmann, Georg, Wettig, "Adaptive algebraic
+ * multigrid on SIMD architectures", arXiv:1512.04506) on one GB300 GPU.
+ *
+ * Operations (paper passages in brackets):
+ *   setup      R from per-aggregate Gram-Schmidt and D_c = R D P  [Alg. 5, Eq. cgo, Eq. dagger]
+ *   restrict   y_c = R y                                          [Alg. 2, Eq. R; Alg. 6]
+ *   apply      y_c = D_c x_c                                      [Alg. 2; Sec. 3 "Application of
+ *                                                                  coarse-grid operator"]
+ *   prolong    x = P x_c, P = R^dagger                            [Alg. 2]
+ *   solve      x_c ~ D_c^{-1} y_c by restarted FGMRES              [Alg. 2, coarse-grid solve]
+ *   batch_cgc  x = P D_c R y for several lattices in one launch    [Alg. 2; persistent threads of Sec. 3]
+ *
+ * Conventions (all device buffers are owned by the caller unless stated):
+ *   - Fine lattice L = {Lx, Ly, Lz, Lt}, blocks B (B[mu] divides L[mu],
+ *     L[mu]/B[mu] >= 2), V = prod L, Vb = prod B, Vc = V / Vb.
+ *   - Sites are lexicographic with x fastest; coarse sites likewise.
+ *   - Gamma matrices in the chiral basis (gamma_5 = diag(1,1,-1,-1)):
+ *     aggregate l = spins {0,1}, aggregate r = spins {2,3} of a block.
+ *   - Wilson-clover operator, periodic in all directions:
+ *       D psi(x) = (4+m0) psi(x) + C(x) psi(x)
+ *                  - 1/2 sum_mu [(1-gamma_mu) U_mu(x) psi(x+mu) + (1+gamma_mu) U_mu(x-mu)^+ psi(x-mu)],
+ *       C(x) = csw (i/4) sum_{mu!=nu} sigma_{mu nu} F_{mu nu}(x), F = (Q - Q^+)/8 (clover leaves).
+ *   - Complex numbers are interleaved (re, im).  Element types:
+ *       AMG_FP64 -> 2 x double, AMG_FP32 -> 2 x float, AMG_BF16 -> 2 x bfloat16.
+ *   - Fine vectors: [V][4 spin][3 colour][nrhs]; coarse vectors:
+ *     [Vc][2 chirality][ntv][nrhs] (2*ntv components per coarse site, l then r).
+ *     Fine vectors have element type vec_prec; coarse vectors are FP64 when
+ *     vec_prec is AMG_FP64 and FP32 otherwise.
+ *   - Every pointer passed in must be 16-byte aligned.
+ *   - All calls are asynchronous on the given stream (a cudaStream_t passed
+ *     as void*, NULL = legacy default stream) unless stated.  The returned
+ *     status covers argument validation and launch errors; errors detected
+ *     on the device (rank deficiency, non-finite values, timeouts) are
+ *     reported by amg_sync_status() or by the next synchronising call.
+ *   - No C++ exception crosses this interface.  There is no global state.
+ */
+#ifndef AMG_H
+#define AMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    AMG_OK = 0,
+    AMG_ERR_INVALID_ARG = 1,     /* a size, pointer or precision was rejected           */
+    AMG_ERR_UNSUPPORTED = 2,     /* valid request that this build does not implement     */
+    AMG_ERR_OOM = 3,             /* device allocation failed                             */
+    AMG_ERR_CUDA = 4,            /* a CUDA runtime call or launch failed                 */
+    AMG_ERR_TIMEOUT = 5,         /* a bounded device-side wait ran out                   */
+    AMG_ERR_RANK_DEFICIENT = 6,  /* Gram-Schmidt norm below 1e-12 |v_j| on an aggregate  */
+    AMG_ERR_NONFINITE = 7        /* NaN/Inf met where the checked mode looks for it      */
+} amg_status;
+
+typedef enum {
+    AMG_FP64 = 0,
+    AMG_FP32 = 1,
+    AMG_FP16_SCALED = 2,  /* FP16 entries with one FP32 scale per (coarse site, stencil block) */
+    AMG_BF16 = 3
+} amg_prec;
+
+typedef struct {
+    int L[4];            /* fine lattice extents, mu = 0..3 = x, y, z, t               */
+    int B[4];            /* block extents                                              */
+    int ntv;             /* number of test vectors N_tv, 1..64, ntv <= 6 Vb            */
+    int max_nrhs;        /* largest nrhs later passed to the apply calls (1..64)       */
+    double m0;           /* bare mass                                                  */
+    double csw;          /* clover coefficient                                         */
+    amg_prec link_prec;  /* storage of D_c for apply/solve: FP64, FP32, FP16_SCALED, BF16 */
+    amg_prec r_prec;     /* storage of R for restrict/prolong: FP64, FP32, BF16         */
+    amg_prec vec_prec;   /* element type of fine vectors: FP64, FP32 or BF16            */
+} amg_params;
+
+typedef struct amg_coarse *amg_handle;
+
+/*
+ * amg_setup_coarse -- Alg. 5 on the GPU, in FP64.
+ *   d_U  [V][4 mu][3][3] complex double: U_mu(x), the link from x to x+mu.
+ *   d_tv [V][4][3][ntv] complex double: the test vectors v_j (Sec. 2.2).
+ * Builds the clover field C from d_U, orthonormalises the test vectors on
+ * every aggregate A_i^h by block classical Gram-Schmidt (Sec. 3, "Gram-Schmidt
+ * on aggregates"), assembles the self block and the four forward blocks of
+ * D_c = R D P (Eq. cgo, Alg. 7) and fills the four backward blocks from
+ * Eq. dagger, then stores R and D_c in r_prec / link_prec (Sec. 3: D_c may be
+ * kept in half precision).  The handle owns every buffer it allocates; the
+ * inputs are read only and may be freed once the call returns.  This call
+ * synchronises the stream before returning; it returns
+ * AMG_ERR_RANK_DEFICIENT when an aggregate's test vectors are dependent, and
+ * then *out is still a valid handle that must be destroyed.
+ */
+amg_status amg_setup_coarse(const amg_params *p, const void *d_U, const void *d_tv,
+                            void *stream, amg_handle *out);
+
+/* y_c = R y [Eq. R, Alg. 6].  d_y: fine vectors, d_yc: coarse vectors. */
+amg_status amg_restrict(amg_handle h, const void *d_y, void *d_yc, int nrhs, void *stream);
+
+/* y_c = D_c x_c [Alg. 2]; d_xc and d_yc must not overlap. */
+amg_status amg_coarse_apply(amg_handle h, const void *d_xc, void *d_yc, int nrhs, void *stream);
+
+/* x = P x_c with P = R^dagger [Alg. 2]. */
+amg_status amg_prolong(amg_handle h, const void *d_xc, void *d_x, int nrhs, void *stream);
+
+/*
+ * amg_coarse_solve -- the coarse-grid solve of Alg. 2: restarted FGMRES(m)
+ * (classical Gram-Schmidt Arnoldi, Givens rotations) on D_c, started from
+ * x_c = 0, until the implicit residual is <= tol ||b|| or max_applies
+ * applications of D_c have been made; each right-hand side independently.
+ * d_b, d_x: coarse vectors with nrhs right-hand sides.  info (host, may be
+ * NULL) receives per RHS {applies, final implicit relative residual} as
+ * info[2 r], info[2 r + 1]; passing info synchronises the stream.
+ */
+amg_status amg_coarse_solve(amg_handle h, const void *d_b, void *d_x, int nrhs, double tol,
+                            int restart, int max_applies, void *stream, double *info);
+
+/*
+ * amg_cgc -- one coarse-grid correction, Alg. 2: x = P FGMRES(D_c, R y).
+ * Same arguments as amg_coarse_solve for the solve.
+ */
+amg_status amg_cgc(amg_handle h, const void *d_y, void *d_x, int nrhs, double tol, int restart,
+                   int max_applies, void *stream, double *info);
+
+/*
+ * amg_batch_cgc -- x_k = P_k D_ck R_k y_k for n lattices (handles hs[k]) in one
+ * persistent launch: each lattice's restriction, one D_c application and its
+ * prolongation run as phases separated by per-lattice device barriers with a
+ * bounded wait (AMG_ERR_TIMEOUT when a wait runs out).  All handles must use
+ * FP32 coarse vectors.  The launch is capturable in a CUDA graph.
+ * Scratch: the first call for a given set of handles allocates a work buffer
+ * owned by hs[0]; later calls reuse it.
+ */
+amg_status amg_batch_cgc(const amg_handle *hs, int n, const void *const *d_y, void *const *d_x,
+                         const int *nrhs, void *stream);
+
+/* R as [Nblock][2][ntv][6 Vb] complex double (row j of R_i^h = v_j^dagger on A_i^h), device or host out. */
+amg_status amg_export_R(amg_handle h, void *out);
+/* D_c as [Vc][9][2 ntv][2 ntv] complex double, FP64 as assembled; directions 0,+x,-x,+y,-y,+z,-z,+t,-t. */
+amg_status amg_export_Dc(amg_handle h, void *out);
+/* The clover field as [V][2 chirality][6][6] complex double (C^{ll}, C^{rr} of Alg. 7). */
+amg_status amg_export_clover(amg_handle h, void *out);
+/* D_c as stored for the applies, dequantised to [Vc][9][2 ntv][2 ntv] complex double. */
+amg_status amg_export_Dc_stored(amg_handle h, void *out);
+
+/* Per-phase setup times in milliseconds: clover, Gram-Schmidt, assembly, dagger fill+quantise. */
+amg_status amg_setup_timings(amg_handle h, double out_ms[4]);
+
+/* Number of kernels this handle has launched so far (a host-side count, for benchmarks). */
+amg_status amg_kernel_launches(amg_handle h, unsigned long long *out);
+
+/* Waits for the handle's last stream and reports device-detected errors. */
+amg_status amg_sync_status(amg_handle h);
+
+amg_status amg_destroy(amg_handle h);
+const char *amg_status_string(amg_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AMG_H */

@@ -1,0 +1,220 @@
+"""Python binding of libamg (ctypes): the coarse-grid correction of DD-alpha-AMG on GB300.
+
+Argument marshalling only.  Every function has the name of the C entry point
+it calls (include/amg.h); pointers may be given as ints, torch tensors
+(``data_ptr()``), numpy arrays (host memory, where the C function accepts
+host memory) or None.  A non-zero status raises ``AmgError`` except where a
+function documents otherwise.  The library must have been built
+(``__graft_entry__.build()``); importing this module without it fails.
+"""
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libamg.so")
+
+AMG_OK = 0
+AMG_ERR_INVALID_ARG = 1
+AMG_ERR_UNSUPPORTED = 2
+AMG_ERR_OOM = 3
+AMG_ERR_CUDA = 4
+AMG_ERR_TIMEOUT = 5
+AMG_ERR_RANK_DEFICIENT = 6
+AMG_ERR_NONFINITE = 7
+
+AMG_FP64 = 0
+AMG_FP32 = 1
+AMG_FP16_SCALED = 2
+AMG_BF16 = 3
+
+
+class amg_params(ctypes.Structure):
+    _fields_ = [
+        ("L", ctypes.c_int * 4),
+        ("B", ctypes.c_int * 4),
+        ("ntv", ctypes.c_int),
+        ("max_nrhs", ctypes.c_int),
+        ("m0", ctypes.c_double),
+        ("csw", ctypes.c_double),
+        ("link_prec", ctypes.c_int),
+        ("r_prec", ctypes.c_int),
+        ("vec_prec", ctypes.c_int),
+    ]
+
+
+class AmgError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__("%s: %s (status %d)" % (where, amg_status_string(status), status))
+
+
+if not os.path.exists(_LIB_PATH):
+    raise ImportError("libamg.so is not built (run __graft_entry__.build()); there is no fallback")
+lib = ctypes.CDLL(_LIB_PATH)
+
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_d = ctypes.c_double
+_proto = {
+    "amg_setup_coarse": [ctypes.POINTER(amg_params), _vp, _vp, _vp, ctypes.POINTER(_vp)],
+    "amg_restrict": [_vp, _vp, _vp, _i, _vp],
+    "amg_coarse_apply": [_vp, _vp, _vp, _i, _vp],
+    "amg_prolong": [_vp, _vp, _vp, _i, _vp],
+    "amg_coarse_solve": [_vp, _vp, _vp, _i, _d, _i, _i, _vp, ctypes.POINTER(_d)],
+    "amg_cgc": [_vp, _vp, _vp, _i, _d, _i, _i, _vp, ctypes.POINTER(_d)],
+    "amg_batch_cgc": [ctypes.POINTER(_vp), _i, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                      ctypes.POINTER(_i), _vp],
+    "amg_export_R": [_vp, _vp],
+    "amg_export_Dc": [_vp, _vp],
+    "amg_export_clover": [_vp, _vp],
+    "amg_export_Dc_stored": [_vp, _vp],
+    "amg_setup_timings": [_vp, ctypes.POINTER(_d)],
+    "amg_kernel_launches": [_vp, ctypes.POINTER(ctypes.c_ulonglong)],
+    "amg_sync_status": [_vp],
+    "amg_destroy": [_vp],
+}
+for _name, _args in _proto.items():
+    _f = getattr(lib, _name)
+    _f.argtypes = _args
+    _f.restype = ctypes.c_int
+lib.amg_status_string.argtypes = [ctypes.c_int]
+lib.amg_status_string.restype = ctypes.c_char_p
+
+EXPORTED = sorted(list(_proto) + ["amg_status_string"])
+
+
+def amg_status_string(status):
+    return lib.amg_status_string(int(status)).decode()
+
+
+def ptr(x):
+    """Address of a buffer: int, None, torch tensor or numpy array."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError("cannot take the address of %r" % type(x))
+
+
+def stream_ptr(s):
+    """cudaStream_t of a torch stream, an int handle, or None (legacy default stream)."""
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _check(status, where, allow=()):
+    if status != AMG_OK and status not in allow:
+        raise AmgError(status, where)
+    return status
+
+
+def make_params(L, B, ntv, max_nrhs=1, m0=-0.3, csw=1.0, link_prec=AMG_FP32, r_prec=AMG_FP32,
+                vec_prec=AMG_FP32):
+    p = amg_params()
+    p.L[:] = list(L)
+    p.B[:] = list(B)
+    p.ntv = ntv
+    p.max_nrhs = max_nrhs
+    p.m0 = m0
+    p.csw = csw
+    p.link_prec = link_prec
+    p.r_prec = r_prec
+    p.vec_prec = vec_prec
+    return p
+
+
+def amg_setup_coarse(params, U, tv, stream=None, allow_rank_deficient=False):
+    """Returns (handle, status); raises on any error except, when allowed, rank deficiency."""
+    h = _vp()
+    st = lib.amg_setup_coarse(ctypes.byref(params), ptr(U), ptr(tv), stream_ptr(stream), ctypes.byref(h))
+    _check(st, "amg_setup_coarse", (AMG_ERR_RANK_DEFICIENT,) if allow_rank_deficient else ())
+    return h.value, st
+
+
+def amg_restrict(h, y, yc, nrhs=1, stream=None):
+    return _check(lib.amg_restrict(h, ptr(y), ptr(yc), nrhs, stream_ptr(stream)), "amg_restrict")
+
+
+def amg_coarse_apply(h, xc, yc, nrhs=1, stream=None):
+    return _check(lib.amg_coarse_apply(h, ptr(xc), ptr(yc), nrhs, stream_ptr(stream)), "amg_coarse_apply")
+
+
+def amg_prolong(h, xc, x, nrhs=1, stream=None):
+    return _check(lib.amg_prolong(h, ptr(xc), ptr(x), nrhs, stream_ptr(stream)), "amg_prolong")
+
+
+def _info(nrhs, want):
+    return (ctypes.c_double * (2 * nrhs))() if want else None
+
+
+def _info_out(info, nrhs):
+    if info is None:
+        return None
+    return [(int(info[2 * r]), float(info[2 * r + 1])) for r in range(nrhs)]
+
+
+def amg_coarse_solve(h, b, x, nrhs=1, tol=0.05, restart=30, max_applies=200, stream=None, info=True):
+    """Returns [(applies, implicit relative residual)] per right-hand side when info is True."""
+    buf = _info(nrhs, info)
+    _check(lib.amg_coarse_solve(h, ptr(b), ptr(x), nrhs, tol, restart, max_applies, stream_ptr(stream), buf),
+           "amg_coarse_solve")
+    return _info_out(buf, nrhs)
+
+
+def amg_cgc(h, y, x, nrhs=1, tol=0.05, restart=30, max_applies=200, stream=None, info=True):
+    buf = _info(nrhs, info)
+    _check(lib.amg_cgc(h, ptr(y), ptr(x), nrhs, tol, restart, max_applies, stream_ptr(stream), buf), "amg_cgc")
+    return _info_out(buf, nrhs)
+
+
+def amg_batch_cgc(hs, ys, xs, nrhs, stream=None):
+    n = len(hs)
+    H = (_vp * n)(*hs)
+    Y = (_vp * n)(*[ptr(y) for y in ys])
+    X = (_vp * n)(*[ptr(x) for x in xs])
+    R = (_i * n)(*nrhs)
+    return _check(lib.amg_batch_cgc(H, n, Y, X, R, stream_ptr(stream)), "amg_batch_cgc")
+
+
+def amg_export_R(h, out):
+    return _check(lib.amg_export_R(h, ptr(out)), "amg_export_R")
+
+
+def amg_export_Dc(h, out):
+    return _check(lib.amg_export_Dc(h, ptr(out)), "amg_export_Dc")
+
+
+def amg_export_clover(h, out):
+    return _check(lib.amg_export_clover(h, ptr(out)), "amg_export_clover")
+
+
+def amg_export_Dc_stored(h, out):
+    return _check(lib.amg_export_Dc_stored(h, ptr(out)), "amg_export_Dc_stored")
+
+
+def amg_setup_timings(h):
+    out = (ctypes.c_double * 4)()
+    _check(lib.amg_setup_timings(h, out), "amg_setup_timings")
+    return list(out)
+
+
+def amg_kernel_launches(h):
+    out = ctypes.c_ulonglong()
+    _check(lib.amg_kernel_launches(h, ctypes.byref(out)), "amg_kernel_launches")
+    return out.value
+
+
+def amg_sync_status(h):
+    """Returns the status (does not raise)."""
+    return lib.amg_sync_status(h)
+
+
+def amg_destroy(h):
+    return _check(lib.amg_destroy(h), "amg_destroy")

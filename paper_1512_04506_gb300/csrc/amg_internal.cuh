@@ -1,0 +1,159 @@
+// Internal declarations of libamg (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <string.h>
+
+#include "../../include/amg.h"
+
+#define AMG_MAX_NTV 64
+#define AMG_NDIR 9
+
+// Bits of the device error word.
+#define AMG_EBIT_RANK 1u
+#define AMG_EBIT_NONFINITE 2u
+#define AMG_EBIT_TIMEOUT 4u
+#define AMG_EBIT_INDEX 8u
+
+// ---------------------------------------------------------------- geometry
+struct Geom {
+  int L[4], B[4], Lc[4];
+  long long V, Vb, Vc;
+  int ntv, nc, nagg;  // nc = 2 ntv, nagg = 6 Vb (dof per aggregate)
+};
+
+__host__ __device__ inline long long site_index(const int* L, int x, int y, int z, int t) {
+  return (((long long)t * L[2] + z) * L[1] + y) * L[0] + x;
+}
+
+// Fine site of local site s (lexicographic, x fastest) in block blk.
+__host__ __device__ inline long long block_site(const Geom& g, long long blk, int s) {
+  int X = (int)(blk % g.Lc[0]);
+  long long r = blk / g.Lc[0];
+  int Y = (int)(r % g.Lc[1]);
+  r /= g.Lc[1];
+  int Z = (int)(r % g.Lc[2]);
+  int T = (int)(r / g.Lc[2]);
+  int bx = s % g.B[0];
+  int q = s / g.B[0];
+  int by = q % g.B[1];
+  q /= g.B[1];
+  int bz = q % g.B[2];
+  int bt = q / g.B[2];
+  return site_index(g.L, X * g.B[0] + bx, Y * g.B[1] + by, Z * g.B[2] + bz, T * g.B[3] + bt);
+}
+
+// ---------------------------------------------------------------- complex helpers
+__host__ __device__ inline double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ inline double2 cmulc(double2 a, double2 b) {  // conj(a) * b
+  return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__host__ __device__ inline double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ inline double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__host__ __device__ inline double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+__host__ __device__ inline double2 cscale(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__host__ __device__ inline void cfma(double2& acc, double2 a, double2 b) {  // acc += a b
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+}
+__host__ __device__ inline void cfmac(double2& acc, double2 a, double2 b) {  // acc += conj(a) b
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(-a.y, b.x, acc.y);
+}
+__host__ __device__ inline void cfma(float2& acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(-a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(a.y, b.x, acc.y);
+}
+__host__ __device__ inline void cfmac(float2& acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(-a.y, b.x, acc.y);
+}
+
+// ---------------------------------------------------------------- handle
+struct SolveWork {
+  int nrhs = 0, restart = 0;
+  void* basis = nullptr;     // (restart+1) coarse vectors
+  void* w = nullptr;         // one coarse vector
+  double2* part = nullptr;   // partial sums
+  double* scal = nullptr;    // device scalars (Hessenberg, Givens, g, flags)
+  int* flags = nullptr;
+  size_t part_elems = 0;
+};
+
+struct BatchWork {
+  void* buf = nullptr;
+  size_t bytes = 0;
+};
+
+struct amg_coarse {
+  amg_params p;
+  Geom g;
+  double2* clover = nullptr;  // [V][2][6][6]
+  double2* R64 = nullptr;     // [Nblock][2][ntv][6Vb], R_i^h row j = conj(q_j)
+  void* Rq = nullptr;         // R in r_prec (aliases R64 for FP64)
+  double2* Dc64 = nullptr;    // [Vc][9][nc][nc] canonical
+  void* Dq = nullptr;         // D_c in link_prec, apply layout [Vc][9][nc col][nc row]
+  float* Dscale = nullptr;    // [Vc][9] (FP16 scaled)
+  void* Dtc = nullptr;        // BF16 tensor-core layout (when link_prec == BF16)
+  void* Rtc = nullptr;        // BF16 tensor-core layout of R (when r_prec == BF16)
+  int* nbr = nullptr;         // [Vc][9]
+  unsigned int* err = nullptr;  // device error word
+  float setup_ms[4] = {0, 0, 0, 0};
+  cudaStream_t last_stream = 0;
+  SolveWork sw;
+  BatchWork bw;
+  void* xc_tmp = nullptr;     // coarse scratch for amg_cgc
+  void* yc_tmp = nullptr;
+  size_t tmp_bytes = 0;
+  unsigned long long launches = 0;  // kernels launched through this handle (host-side count)
+};
+
+// ---------------------------------------------------------------- shared host helpers
+#define AMG_CUDA_TRY(call)                                \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) {                              \
+      return e_ == cudaErrorMemoryAllocation ? AMG_ERR_OOM : AMG_ERR_CUDA; \
+    }                                                     \
+  } while (0)
+
+#define AMG_LAUNCH_CHECK()                                \
+  do {                                                    \
+    if (cudaGetLastError() != cudaSuccess) return AMG_ERR_CUDA; \
+  } while (0)
+
+inline bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+inline size_t vec_elem_bytes(amg_prec p) {
+  return p == AMG_FP64 ? 16 : (p == AMG_FP32 ? 8 : 4);
+}
+inline size_t coarse_elem_bytes(const amg_coarse* h) { return h->p.vec_prec == AMG_FP64 ? 16 : 8; }
+
+// Entry points of the translation units, used by the C ABI layer.
+amg_status amg_internal_setup(amg_coarse* h, const double2* U, const double2* tv, cudaStream_t s);
+amg_status amg_internal_restrict(amg_coarse* h, const void* y, void* yc, int nrhs, cudaStream_t s);
+amg_status amg_internal_apply(amg_coarse* h, const void* xc, void* yc, int nrhs, cudaStream_t s);
+amg_status amg_internal_prolong(amg_coarse* h, const void* xc, void* x, int nrhs, cudaStream_t s);
+amg_status amg_internal_solve(amg_coarse* h, const void* b, void* x, int nrhs, double tol,
+                              int restart, int max_applies, cudaStream_t s, double* info);
+amg_status amg_internal_batch(amg_coarse* const* hs, int n, const void* const* y, void* const* x,
+                              const int* nrhs, cudaStream_t s);
+amg_status amg_internal_export_stored(amg_coarse* h, double2* out);
+amg_status amg_internal_tc_prepare(amg_coarse* h, cudaStream_t s);
+void amg_internal_free_tc(amg_coarse* h);
+// Coarse application whose CTAs return at once while *skip != 0 (used inside the solver).
+amg_status amg_internal_apply_ex(amg_coarse* h, const void* xc, void* yc, int nrhs, cudaStream_t s,
+                                 const int* skip);

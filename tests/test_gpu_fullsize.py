@@ -1,0 +1,101 @@
+"""GPU parity at full workload sizes, on sampled outputs the oracle computes one by one.
+
+The inputs are generated on the device (synth.device); the oracle rebuilds the
+inputs of a 3x3x3x3-block box around each sampled block on the host from the
+same counter-based generator and computes that block's R rows and D_c row.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from synth import inputs as si  # noqa: E402
+
+import helpers as H  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def amg():
+    import paper_1512_04506_gb300 as m
+    return m
+
+
+def test_device_generator_matches_host():
+    from synth import device as sd
+    L = (4, 2, 6, 4)
+    sites = si.all_sites(L)
+    U = sd.links(77, 0.4, L).cpu().numpy()
+    assert H.rel(U, si.links(77, 0.4, sites)) < 1e-14
+    tv = sd.test_vectors(77, 5, L).cpu().numpy()
+    assert H.rel(tv, si.test_vectors(77, 5, sites)) < 1e-14
+    y = sd.fine_rhs(77, 3, L, torch.complex128).cpu().numpy()
+    assert H.rel(y, si.fine_rhs(77, 3, sites)) < 1e-14
+    xc = sd.coarse_vector(77, 5, 2, 24, torch.complex128).cpu().numpy()
+    assert H.rel(xc, si.coarse_vector(77, 5, 2, np.arange(24))) < 1e-14
+
+
+def _block_sites(L, B, X):
+    """Global site indices of block X in the library's aggregate order (site in block, x fastest)."""
+    bt, bz, by, bx = np.meshgrid(*(np.arange(B[m]) for m in (3, 2, 1, 0)), indexing="ij")
+    c = np.stack([X[0] * B[0] + bx, X[1] * B[1] + by, X[2] * B[2] + bz, X[3] * B[3] + bt], axis=-1)
+    return si.site_index(L, c.reshape(-1, 4))
+
+
+def test_fp32_workload_32x4_sampled(amg):
+    """32^4, 4^4 blocks (8^4 coarse), Ntv = 20, FP64 setup, FP32 applies: the benchmark's workload."""
+    from synth import device as sd
+    L, B, ntv, eps, off = H.WORKLOADS["fp32_32^4_b4_ntv20"]
+    seed = si.SEED_BASE + off
+    Lc = tuple(L[m] // B[m] for m in range(4))
+    Vc = int(np.prod(Lc))
+    nc = 2 * ntv
+    stream = torch.cuda.current_stream()
+    U = sd.links(seed, eps, L)
+    tv = sd.test_vectors(seed, ntv, L)
+    p = amg.make_params(L, B, ntv, 1, H.M0, H.CSW, amg.AMG_FP32, amg.AMG_FP32, amg.AMG_FP32)
+    h, _ = amg.amg_setup_coarse(p, U, tv, stream)
+    del U, tv
+    torch.cuda.empty_cache()
+    try:
+        Dc = torch.empty((Vc, 9, nc, nc), dtype=torch.complex128, device="cuda")
+        amg.amg_export_Dc(h, Dc)
+        y = sd.fine_rhs(seed, 1, L, torch.complex64)
+        yc = torch.empty((Vc, 2, ntv, 1), dtype=torch.complex64, device="cuda")
+        amg.amg_restrict(h, y, yc, 1, stream)
+        xc = sd.coarse_vector(seed, ntv, 1, Vc, torch.complex64)
+        zc = torch.empty_like(xc)
+        amg.amg_coarse_apply(h, xc, zc, 1, stream)
+        x = torch.empty_like(y)
+        amg.amg_prolong(h, xc, x, 1, stream)
+        torch.cuda.synchronize()
+        assert amg.amg_sync_status(h) == amg.AMG_OK
+        from oracle import lattice as lat
+        nbr = lat.coarse_neighbours(Lc)
+        Rall = torch.empty((Vc, 2, ntv, 6 * 256), dtype=torch.complex128, device="cuda")
+        amg.amg_export_R(h, Rall)
+        for X in [(0, 0, 0, 0), (7, 2, 5, 7)]:
+            i = int(lat.coarse_index(np.array(X), Lc))
+            Q, Dref, _, _ = H.patch_reference(seed, eps, L, B, ntv, X)
+            assert H.rel(Dc[i].cpu().numpy(), Dref) < 1e-12
+            Rg = Rall[i].cpu().numpy()
+            assert H.rel(Rg, np.conj(np.swapaxes(Q, -1, -2))) < 1e-12
+            # restriction of the FP32 right-hand side on this block
+            bs = _block_sites(L, B, X)
+            yb = si.fine_rhs(seed, 1, bs).astype(np.complex64).astype(np.complex128)[..., 0]  # (Vb, 4, 3)
+            ya = yb.reshape(-1, 2, 2, 3).transpose(1, 0, 2, 3).reshape(2, -1)              # (h, n)
+            ref = np.einsum("hnj,hn->hj", Q.conj(), ya)
+            assert H.rel(yc[i, :, :, 0].cpu().numpy(), ref) < 1e-5
+            # coarse operator at this site
+            xh = si.coarse_vector(seed, ntv, 1, nbr[i]).astype(np.complex64).astype(np.complex128)
+            refz = sum(Dref[d] @ xh[d].reshape(nc) for d in range(9))
+            assert H.rel(zc[i].reshape(nc).cpu().numpy(), refz) < 1e-5
+            # prolongation onto this block
+            refx = np.einsum("hnj,hj->hn", Q, xh[0][..., 0])                                # (h, n)
+            refx = refx.reshape(2, -1, 2, 3).transpose(1, 0, 2, 3).reshape(-1, 4, 3)
+            got = x[torch.from_numpy(bs).cuda()].cpu().numpy()[..., 0]
+            assert H.rel(got, refx) < 1e-5
+        del Rall
+    finally:
+        amg.amg_destroy(h)
