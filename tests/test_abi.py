@@ -13,8 +13,8 @@ def built():
     amg = os.path.join(ROOT, "paper_1512_04506_gb300", "libamg.so")
     syn = os.path.join(ROOT, "synth", "libsynth.so")
     if not (os.path.exists(amg) and os.path.exists(syn)):
-        from paper_1512_04506_gb300 import _build
-        _build.build()
+        import __graft_entry__
+        __graft_entry__.build()
     return amg, syn
 
 
