@@ -156,6 +156,8 @@ amg_status amg_sync_status(amg_handle h);
 
 amg_status amg_destroy(amg_handle h);
 const char *amg_status_string(amg_status s);
+/* Text of the last failed CUDA call made by this library on the calling thread ("" if none). */
+const char *amg_last_error(void);
 
 #ifdef __cplusplus
 }

@@ -45,7 +45,8 @@ class amg_params(ctypes.Structure):
 class AmgError(RuntimeError):
     def __init__(self, status, where):
         self.status = status
-        super().__init__("%s: %s (status %d)" % (where, amg_status_string(status), status))
+        detail = amg_last_error() if status in (AMG_ERR_CUDA, AMG_ERR_OOM) else ""
+        super().__init__("%s: %s (status %d) %s" % (where, amg_status_string(status), status, detail))
 
 
 if not os.path.exists(_LIB_PATH):
@@ -79,8 +80,14 @@ for _name, _args in _proto.items():
     _f.restype = ctypes.c_int
 lib.amg_status_string.argtypes = [ctypes.c_int]
 lib.amg_status_string.restype = ctypes.c_char_p
+lib.amg_last_error.argtypes = []
+lib.amg_last_error.restype = ctypes.c_char_p
 
-EXPORTED = sorted(list(_proto) + ["amg_status_string"])
+EXPORTED = sorted(list(_proto) + ["amg_status_string", "amg_last_error"])
+
+
+def amg_last_error():
+    return lib.amg_last_error().decode()
 
 
 def amg_status_string(status):

@@ -122,17 +122,25 @@ struct amg_coarse {
 };
 
 // ---------------------------------------------------------------- shared host helpers
+// Records the failing CUDA call of the calling thread (read back by amg_last_error()).
+void amg_note_cuda_error(const char* file, int line, cudaError_t e);
+
 #define AMG_CUDA_TRY(call)                                \
   do {                                                    \
     cudaError_t e_ = (call);                              \
     if (e_ != cudaSuccess) {                              \
+      amg_note_cuda_error(__FILE__, __LINE__, e_);        \
       return e_ == cudaErrorMemoryAllocation ? AMG_ERR_OOM : AMG_ERR_CUDA; \
     }                                                     \
   } while (0)
 
 #define AMG_LAUNCH_CHECK()                                \
   do {                                                    \
-    if (cudaGetLastError() != cudaSuccess) return AMG_ERR_CUDA; \
+    cudaError_t e_ = cudaGetLastError();                  \
+    if (e_ != cudaSuccess) {                              \
+      amg_note_cuda_error(__FILE__, __LINE__, e_);        \
+      return AMG_ERR_CUDA;                                \
+    }                                                     \
   } while (0)
 
 inline bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }

@@ -2,7 +2,16 @@
 #include "amg_internal.cuh"
 
 #include <new>
+#include <stdio.h>
 #include <vector>
+
+static thread_local char g_last_error[256] = "";
+
+void amg_note_cuda_error(const char* file, int line, cudaError_t e) {
+  const char* base = strrchr(file, '/');
+  snprintf(g_last_error, sizeof(g_last_error), "%s:%d: %s (%s)", base ? base + 1 : file, line,
+           cudaGetErrorString(e), cudaGetErrorName(e));
+}
 
 namespace {
 
@@ -323,6 +332,8 @@ amg_status amg_destroy(amg_handle h) {
   free_handle(h);
   return AMG_OK;
 }
+
+const char* amg_last_error(void) { return g_last_error; }
 
 const char* amg_status_string(amg_status s) {
   switch (s) {

@@ -667,6 +667,9 @@ amg_status amg_internal_setup(amg_coarse* h, const double2* U, const double2* tv
   unsigned e = 0;
   AMG_CUDA_TRY(cudaMemcpy(&e, h->err, sizeof(unsigned), cudaMemcpyDeviceToHost));
   if (e & AMG_EBIT_RANK) return AMG_ERR_RANK_DEFICIENT;
-  if (e) return AMG_ERR_CUDA;
+  if (e) {
+    amg_note_cuda_error(__FILE__, __LINE__, cudaErrorUnknown);
+    return AMG_ERR_CUDA;
+  }
   return AMG_OK;
 }
