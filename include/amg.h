@@ -67,7 +67,7 @@ typedef enum {
 typedef struct {
     int L[4];            /* fine lattice extents, mu = 0..3 = x, y, z, t               */
     int B[4];            /* block extents                                              */
-    int ntv;             /* number of test vectors N_tv, 1..64, ntv <= 6 Vb            */
+    int ntv;             /* number of test vectors N_tv, 1..32, ntv <= 6 Vb            */
     int max_nrhs;        /* largest nrhs later passed to the apply calls (1..64)       */
     double m0;           /* bare mass                                                  */
     double csw;          /* clover coefficient                                         */

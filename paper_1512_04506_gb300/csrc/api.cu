@@ -38,6 +38,7 @@ amg_status validate_params(const amg_params* p) {
     if (p->r_prec != AMG_BF16 || p->link_prec != AMG_BF16) return AMG_ERR_UNSUPPORTED;
   }
   if (p->link_prec == AMG_FP16_SCALED && (p->ntv % 2)) return AMG_ERR_UNSUPPORTED;
+  if (p->ntv > 32) return AMG_ERR_UNSUPPORTED;  // register tiles of the D_c assembly
   return AMG_OK;
 }
 

@@ -330,7 +330,7 @@ __device__ inline double2 bmat(int mu, int a, int b) {
 }
 
 template <int TA, int TC>
-__global__ void assemble_kernel(const double2* __restrict__ R, const double2* __restrict__ U,
+__global__ void __launch_bounds__(256) assemble_kernel(const double2* __restrict__ R, const double2* __restrict__ U,
                                 const double2* __restrict__ clov, double2* __restrict__ part, Geom g,
                                 double m0, int ncp, int sb_max) {
   extern __shared__ double2 smem[];
@@ -614,12 +614,13 @@ amg_status amg_internal_setup(amg_coarse* h, const double2* U, const double2* tv
   const size_t part_elems = (size_t)g.Vc * 5 * 2 * g.nc * g.nc;
   AMG_CUDA_TRY(cudaMallocAsync((void**)&part, part_elems * sizeof(double2), st));
   {
-    const bool big = g.nc > 64;
+    // 2x4 register tiles up to 2 ntv = 40, 4x4 tiles up to 2 ntv = 64; at most 256 threads
+    const bool big = g.nc > 40;
     const int TA = big ? 4 : 2, TC = 4;
     const int ncp = round_up(g.nc, 4);
     const int ntiles = (ncp / TA) * (ncp / TC);
     const int T = round_up(ntiles < 128 ? 128 : ntiles, 32);
-    if (T > 1024) return AMG_ERR_UNSUPPORTED;
+    if (T > 256) return AMG_ERR_UNSUPPORTED;
     int sb = 8;
     while (sb > 1 && (size_t)sb * 12 * ncp * sizeof(double2) > 96 * 1024) sb >>= 1;
     const size_t sm = (size_t)sb * 12 * ncp * sizeof(double2);
