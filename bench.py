@@ -33,6 +33,9 @@ NTV = 20
 EPS, M0, CSW = 0.3, -0.3, 1.0
 SEED = 20151204 + 2
 TOL, RESTART, MAX_APPLIES = 0.05, 30, 200
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the ncu capture
+# summarised under profiles/, for the kernels as they are now; None until captured.
+TRAFFIC = {}
 METRIC = "coarse-grid correction GB/s & % HBM roofline; batched-mixed vs plain speedup"
 WORKLOAD = "fp32_32^4_b4_ntv20: 32^4 Wilson-clover, 4^4 blocks -> 8^4 coarse, Ntv=20, 1 RHS, " \
            "FP64 setup, FP32 R and D_c; step = R y, FGMRES(30) to 0.05 (<=200 applies), P x_c"
@@ -223,8 +226,13 @@ def run_gpu(args):
     value = world * step_bytes * args.steps / t_total / 1e9
     e2e_value = world * step_bytes * args.steps / t_e2e / 1e9
     peaks, src = measured_peaks()
-    apply_bytes = parts["apply"]
-    achieved = apply_bytes / t_apply / 1e9
+    # dominant kernel of the step: largest (launches per step x live launch time)
+    live = {"restrict": (t_restrict, 1, parts["restrict"], "restrict y_c = R y (FP32 R)"),
+            "prolong": (t_prolong, 1, parts["prolong"], "prolong x = P x_c (FP32 R)"),
+            "apply": (t_apply, applies, parts["apply"], "coarse apply y_c = D_c x_c (FP32 links)")}
+    dom = max(live, key=lambda k: live[k][0] * live[k][1])
+    t_dom, _, dom_bytes, dom_name = live[dom]
+    achieved = dom_bytes / t_dom / 1e9
     result = {
         "metric": METRIC,
         "value": round(value, 2),
@@ -244,15 +252,16 @@ def run_gpu(args):
                    "l2": "inputs larger than L2 (R %.2f GB, D_c %.2f GB) and a 256 MB flush before each step"
                          % (parts["restrict"] / 1e9, Vc * 9 * nc * nc * 8 / 1e9),
                    "parallelism": "replicas" if world > 1 else "single"},
-        "roofline": {"bound": "hbm", "kernel": "coarse apply (FP32 links)", "achieved": round(achieved, 1),
+        "roofline": {"bound": "hbm", "kernel": dom_name, "achieved": round(achieved, 1),
                      "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
-                     "peak_source": src, "traffic": None,
-                     "bytes_per_launch": apply_bytes, "avg_launch_us": round(t_apply * 1e6, 2)},
+                     "peak_source": src, "traffic": TRAFFIC.get(dom),
+                     "bytes_per_launch": dom_bytes, "avg_launch_us": round(t_dom * 1e6, 2),
+                     "step_share": round(t_dom * live[dom][1] / (t_total / args.steps), 3)},
         "kernels": {
             "restrict": {"GB/s": round(parts["restrict"] / t_restrict / 1e9, 1), "us": round(t_restrict * 1e6, 1),
                          "frac": round(parts["restrict"] / t_restrict / 1e9 / peaks["hbm_gbs"], 4)},
-            "apply": {"GB/s": round(achieved, 1), "us": round(t_apply * 1e6, 1),
-                      "frac": round(achieved / peaks["hbm_gbs"], 4)},
+            "apply": {"GB/s": round(parts["apply"] / t_apply / 1e9, 1), "us": round(t_apply * 1e6, 1),
+                      "frac": round(parts["apply"] / t_apply / 1e9 / peaks["hbm_gbs"], 4)},
             "prolong": {"GB/s": round(parts["prolong"] / t_prolong / 1e9, 1), "us": round(t_prolong * 1e6, 1),
                         "frac": round(parts["prolong"] / t_prolong / 1e9 / peaks["hbm_gbs"], 4)},
         },

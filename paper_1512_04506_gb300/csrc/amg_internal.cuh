@@ -83,14 +83,14 @@ __host__ __device__ inline void cfmac(float2& acc, float2 a, float2 b) {
 }
 
 // ---------------------------------------------------------------- handle
+// Workspace of the coarse solve: one device buffer (Krylov basis, partial sums, scalars, flags)
+// plus a ring of pinned flags and events through which the host sees convergence.
 struct SolveWork {
-  int nrhs = 0, restart = 0;
-  void* basis = nullptr;     // (restart+1) coarse vectors
-  void* w = nullptr;         // one coarse vector
-  double2* part = nullptr;   // partial sums
-  double* scal = nullptr;    // device scalars (Hessenberg, Givens, g, flags)
-  int* flags = nullptr;
-  size_t part_elems = 0;
+  static constexpr int kRing = 16;
+  void* buf = nullptr;
+  size_t bytes = 0;
+  int* hflag = nullptr;
+  cudaEvent_t ev[kRing] = {};
 };
 
 struct BatchWork {
@@ -157,6 +157,11 @@ amg_status amg_internal_apply(amg_coarse* h, const void* xc, void* yc, int nrhs,
 amg_status amg_internal_prolong(amg_coarse* h, const void* xc, void* x, int nrhs, cudaStream_t s);
 amg_status amg_internal_solve(amg_coarse* h, const void* b, void* x, int nrhs, double tol,
                               int restart, int max_applies, cudaStream_t s, double* info);
+// The solve on a caller-provided workspace of amg_internal_solve_bytes() bytes; poll = false
+// launches the whole budget without host events (kernels after convergence return at once).
+amg_status amg_internal_solve_ws(amg_coarse* h, const void* b, void* x, int nrhs, double tol, int restart,
+                                 int max_applies, cudaStream_t s, double* info, void* ws, bool poll);
+size_t amg_internal_solve_bytes(const amg_coarse* h, int nrhs, int m);
 amg_status amg_internal_batch(amg_coarse* const* hs, int n, const void* const* y, void* const* x,
                               const int* nrhs, cudaStream_t s);
 amg_status amg_internal_export_stored(amg_coarse* h, double2* out);

@@ -69,11 +69,11 @@ void free_handle(amg_coarse* h) {
   cudaFree(h->Dscale);
   cudaFree(h->nbr);
   cudaFree(h->err);
-  cudaFree(h->sw.basis);
-  cudaFree(h->sw.w);
-  cudaFree(h->sw.part);
-  cudaFree(h->sw.scal);
-  cudaFree(h->sw.flags);
+  cudaFree(h->sw.buf);
+  if (h->sw.hflag) {
+    cudaFreeHost(h->sw.hflag);
+    for (int k = 0; k < SolveWork::kRing; ++k) cudaEventDestroy(h->sw.ev[k]);
+  }
   cudaFree(h->bw.buf);
   cudaFree(h->xc_tmp);
   cudaFree(h->yc_tmp);

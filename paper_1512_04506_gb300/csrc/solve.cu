@@ -2,10 +2,14 @@
 // ("BLAS-like linear algebra (mainly Gram-Schmidt)") and Givens rotations, one independent
 // Krylov space per right-hand side.  Vectors stay in the coarse layout [Vc][2][ntv][nrhs]; all
 // scalars (Hessenberg matrix, rotations, residual estimates, convergence flags) live on the
-// device, so the host only launches kernels.  Once every right-hand side has converged the
-// device flag `done` makes all later kernels of the iteration return immediately; the host
-// learns of it through an event two iterations behind the launch front, so the GPU never waits
-// for the host.
+// device, so the host only launches kernels.
+//
+// One Arnoldi step is four launches: D_c V_j, the dots <V_i, w> (whose last CTA reduces the
+// partial sums into column j of H), the update w -= sum H_ij V_i with |w|^2 (whose last CTA does
+// the Givens rotation and the convergence test), and the scaling V_{j+1} = w / h_{j+1,j}.  Once
+// every right-hand side has converged the device flag `done` makes every later kernel return at
+// once.  The host either learns of it through an event two steps behind the launch front (so
+// the GPU never waits for the host) or, without events, launches the whole budget.
 #include "amg_internal.cuh"
 
 #include <algorithm>
@@ -14,14 +18,16 @@ namespace {
 
 constexpr int ST_T = 256;
 constexpr int MAXR = 16;
+constexpr int NBLK = 2 * 152;
 
 struct FState {
   int m, nrhs, nblk;
   long long rows;  // Vc * nc
   double tol;
-  double2 *H, *cs, *sn, *gv, *yv, *part;
+  double2 *H, *cs, *sn, *gv, *part;
   double *bnorm, *relres, *invh;
   int *active, *kcnt, *applies, *done;
+  unsigned* counter;
 };
 
 __device__ inline double2 to_d(float2 v) { return make_double2(v.x, v.y); }
@@ -30,8 +36,10 @@ template <typename CT> __device__ inline CT from_d(double2 v);
 template <> __device__ inline float2 from_d<float2>(double2 v) { return make_float2((float)v.x, (float)v.y); }
 template <> __device__ inline double2 from_d<double2>(double2 v) { return v; }
 
-// CTA-wide sum of nrhs complex values per thread; result written by thread r < nrhs to out[r].
-__device__ inline void cta_sum_store(double2 (&acc)[MAXR], int nrhs, double2* out, int stride) {
+__device__ inline double2 ld_cg(const double2* p) { return __ldcg(p); }
+
+// CTA-wide sum of nrhs complex values per thread; thread r < nrhs writes out[r].
+__device__ inline void cta_sum_store(double2 (&acc)[MAXR], int nrhs, double2* out) {
   __shared__ double2 sm[ST_T / 32][MAXR];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -48,18 +56,73 @@ __device__ inline void cta_sum_store(double2 (&acc)[MAXR], int nrhs, double2* ou
   if (threadIdx.x < nrhs) {
     double2 t = make_double2(0, 0);
     for (int w = 0; w < ST_T / 32; ++w) t = cadd(t, sm[w][threadIdx.x]);
-    out[threadIdx.x * stride] = t;
+    out[threadIdx.x] = t;
   }
 }
 
-// part[(i * nblk + b) * nrhs + r] = partial <V_i, w> (i = blockIdx.y).
+// Last-CTA election: every CTA publishes its partial sums, then counts itself in; the CTA that
+// brings the count to `total` sees every partial (threadfence before the count) and resets it.
+__device__ inline bool last_block(unsigned* counter, unsigned total) {
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned prev = atomicAdd(counter, 1u);
+    last = prev == total - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) *counter = 0;
+  return last;
+}
+
+// Givens rotation and convergence test of Arnoldi step j for right-hand side r, given |w|^2.
+__device__ void arnoldi_step(FState& s, int r, int j, double n2, int* any) {
+  if (!s.active[r]) {
+    s.invh[r] = 0;
+    return;
+  }
+  const double hnext = sqrt(n2);
+  double2* Hc = s.H + (long long)r * (s.m + 1) * s.m;  // Hc[i * m + j]
+  double2* cs = s.cs + (long long)r * s.m;
+  double2* sn = s.sn + (long long)r * s.m;
+  double2* gv = s.gv + (long long)r * (s.m + 1);
+  for (int i = 0; i < j; ++i) {
+    const double2 a = Hc[i * s.m + j], b = Hc[(i + 1) * s.m + j];
+    const double2 t = cadd(cmul(cs[i], a), cmul(sn[i], b));
+    Hc[(i + 1) * s.m + j] = csub(cmul(cconj(cs[i]), b), cmul(cconj(sn[i]), a));
+    Hc[i * s.m + j] = t;
+  }
+  const double2 a = Hc[j * s.m + j];
+  const double den = sqrt(a.x * a.x + a.y * a.y + hnext * hnext);
+  const double2 c = den > 0 ? cscale(cconj(a), 1.0 / den) : make_double2(1, 0);
+  const double2 sv = den > 0 ? make_double2(hnext / den, 0) : make_double2(0, 0);
+  cs[j] = c;
+  sn[j] = sv;
+  Hc[j * s.m + j] = make_double2(den, 0);
+  Hc[(j + 1) * s.m + j] = make_double2(0, 0);
+  const double2 gj = gv[j];
+  gv[j + 1] = cscale(cmul(cconj(sv), gj), -1.0);
+  gv[j] = cmul(c, gj);
+  const double rel = sqrt(gv[j + 1].x * gv[j + 1].x + gv[j + 1].y * gv[j + 1].y) / s.bnorm[r];
+  s.relres[r] = rel;
+  s.kcnt[r] = j + 1;
+  s.applies[r] += 1;
+  if (rel <= s.tol || hnext == 0) {
+    s.active[r] = 0;
+    s.invh[r] = 0;
+  } else {
+    s.invh[r] = 1.0 / hnext;
+    atomicOr(any, 1);
+  }
+}
+
+// part[(i * nblk + b) * nrhs + r] = partial <V_i, w> (i = blockIdx.y); the last CTA writes H[.][i][j].
 template <typename CT>
 __global__ void __launch_bounds__(ST_T) k_dots(FState s, const CT* __restrict__ w, const CT* __restrict__ V,
-                                               long long vstride) {
+                                               long long vstride, int j) {
   if (*s.done) return;
   const int i = blockIdx.y;
   const CT* Vi = V + i * vstride;
-  // per-thread sums in the vector precision, CTA and grid sums in FP64
   CT a[MAXR];
 #pragma unroll
   for (int r = 0; r < MAXR; ++r) a[r] = CT{0, 0};
@@ -74,20 +137,17 @@ __global__ void __launch_bounds__(ST_T) k_dots(FState s, const CT* __restrict__ 
   double2 acc[MAXR];
 #pragma unroll
   for (int r = 0; r < MAXR; ++r) acc[r] = to_d(a[r]);
-  cta_sum_store(acc, s.nrhs, s.part + ((long long)i * s.nblk + blockIdx.x) * s.nrhs, 1);
+  cta_sum_store(acc, s.nrhs, s.part + ((long long)i * s.nblk + blockIdx.x) * s.nrhs);
+  if (!last_block(s.counter, s.nblk * (j + 1))) return;
+  for (int t = threadIdx.x; t < (j + 1) * s.nrhs; t += blockDim.x) {
+    const int ii = t / s.nrhs, r = t % s.nrhs;
+    double2 sum = make_double2(0, 0);
+    for (int b = 0; b < s.nblk; ++b) sum = cadd(sum, ld_cg(s.part + ((long long)ii * s.nblk + b) * s.nrhs + r));
+    s.H[((long long)r * (s.m + 1) + ii) * s.m + j] = s.active[r] ? sum : make_double2(0, 0);
+  }
 }
 
-// H[r][i][j] = sum of the partial dots (zero for converged right-hand sides).
-__global__ void k_finish_dots(FState s, int j) {
-  const int t = threadIdx.x + blockIdx.x * blockDim.x;
-  if (*s.done || t >= (j + 1) * s.nrhs) return;
-  const int i = t / s.nrhs, r = t % s.nrhs;
-  double2 sum = make_double2(0, 0);
-  for (int b = 0; b < s.nblk; ++b) sum = cadd(sum, s.part[((long long)i * s.nblk + b) * s.nrhs + r]);
-  s.H[((long long)r * (s.m + 1) + i) * s.m + j] = s.active[r] ? sum : make_double2(0, 0);
-}
-
-// w -= sum_{i<=j} H[r][i][j] V_i; partial |w|^2 into part slot 0.
+// w -= sum_{i<=j} H[r][i][j] V_i and |w|^2; the last CTA does the Givens step (arnoldi_step).
 template <typename CT>
 __global__ void __launch_bounds__(ST_T) k_update(FState s, CT* __restrict__ w, const CT* __restrict__ V,
                                                  long long vstride, int j) {
@@ -95,7 +155,7 @@ __global__ void __launch_bounds__(ST_T) k_update(FState s, CT* __restrict__ w, c
   __shared__ CT hc[AMG_MAX_NTV + 1][MAXR];
   for (int e = threadIdx.x; e < (j + 1) * s.nrhs; e += ST_T) {
     const int i = e / s.nrhs, r = e % s.nrhs;
-    hc[i][r] = from_d<CT>(s.H[((long long)r * (s.m + 1) + i) * s.m + j]);
+    hc[i][r] = from_d<CT>(ld_cg(s.H + ((long long)r * (s.m + 1) + i) * s.m + j));
   }
   __syncthreads();
   CT a[MAXR];
@@ -120,57 +180,16 @@ __global__ void __launch_bounds__(ST_T) k_update(FState s, CT* __restrict__ w, c
   double2 acc[MAXR];
 #pragma unroll
   for (int r = 0; r < MAXR; ++r) acc[r] = to_d(a[r]);
-  cta_sum_store(acc, s.nrhs, s.part + (long long)blockIdx.x * s.nrhs, 1);
-}
-
-// One thread per right-hand side: h_{j+1,j}, Givens rotations, residual estimate, convergence.
-__global__ void k_arnoldi(FState s, int j) {
+  cta_sum_store(acc, s.nrhs, s.part + (long long)blockIdx.x * s.nrhs);
+  if (!last_block(s.counter, s.nblk)) return;
   __shared__ int any;
-  if (*s.done) return;
   if (threadIdx.x == 0) any = 0;
   __syncthreads();
-  const int r = threadIdx.x;
-  if (r < s.nrhs) {
-    if (s.active[r]) {
-      double n2 = 0;
-      for (int b = 0; b < s.nblk; ++b) n2 += s.part[(long long)b * s.nrhs + r].x;
-      const double hnext = sqrt(n2);
-      double2* Hc = s.H + (long long)r * (s.m + 1) * s.m;  // Hc[i * m + j]
-      double2* cs = s.cs + (long long)r * s.m;
-      double2* sn = s.sn + (long long)r * s.m;
-      double2* gv = s.gv + (long long)r * (s.m + 1);
-      Hc[(j + 1) * s.m + j] = make_double2(hnext, 0);
-      for (int i = 0; i < j; ++i) {
-        const double2 a = Hc[i * s.m + j], b = Hc[(i + 1) * s.m + j];
-        const double2 t = cadd(cmul(cs[i], a), cmul(sn[i], b));
-        Hc[(i + 1) * s.m + j] = csub(cmul(cconj(cs[i]), b), cmul(cconj(sn[i]), a));
-        Hc[i * s.m + j] = t;
-      }
-      const double2 a = Hc[j * s.m + j];
-      const double den = sqrt(a.x * a.x + a.y * a.y + hnext * hnext);
-      const double2 c = den > 0 ? cscale(cconj(a), 1.0 / den) : make_double2(1, 0);
-      const double2 sv = den > 0 ? make_double2(hnext / den, 0) : make_double2(0, 0);
-      cs[j] = c;
-      sn[j] = sv;
-      Hc[j * s.m + j] = make_double2(den, 0);
-      Hc[(j + 1) * s.m + j] = make_double2(0, 0);
-      const double2 gj = gv[j];
-      gv[j + 1] = cscale(cmul(cconj(sv), gj), -1.0);
-      gv[j] = cmul(c, gj);
-      const double rel = sqrt(gv[j + 1].x * gv[j + 1].x + gv[j + 1].y * gv[j + 1].y) / s.bnorm[r];
-      s.relres[r] = rel;
-      s.kcnt[r] = j + 1;
-      s.applies[r] += 1;
-      if (rel <= s.tol || hnext == 0) {
-        s.active[r] = 0;
-        s.invh[r] = 0;
-      } else {
-        s.invh[r] = 1.0 / hnext;
-        atomicOr(&any, 1);
-      }
-    } else {
-      s.invh[r] = 0;
-    }
+  if (threadIdx.x < s.nrhs) {
+    const int r = threadIdx.x;
+    double n2 = 0;
+    for (int b = 0; b < s.nblk; ++b) n2 += ld_cg(s.part + (long long)b * s.nrhs + r).x;
+    arnoldi_step(s, r, j, n2, &any);
   }
   __syncthreads();
   if (threadIdx.x == 0 && !any) *s.done = 1;
@@ -183,59 +202,65 @@ __global__ void k_scale(FState s, CT* __restrict__ out, const CT* __restrict__ w
   const long long n = s.rows * s.nrhs;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
     const CT v = w[e];
-    const auto f = (decltype(v.x))s.invh[e % s.nrhs];
+    const auto f = (decltype(v.x))__ldcg(s.invh + e % s.nrhs);
     out[e] = CT{v.x * f, v.y * f};
   }
 }
 
-// Back substitution of the k x k triangular system per right-hand side.
-__global__ void k_backsolve(FState s) {
-  const int r = threadIdx.x;
-  if (r >= s.nrhs) return;
-  const int k = s.kcnt[r];
-  const double2* Hc = s.H + (long long)r * (s.m + 1) * s.m;
-  const double2* gv = s.gv + (long long)r * (s.m + 1);
-  double2* y = s.yv + (long long)r * s.m;
-  for (int i = k - 1; i >= 0; --i) {
-    double2 t = gv[i];
-    for (int l = i + 1; l < k; ++l) t = csub(t, cmul(Hc[i * s.m + l], y[l]));
-    const double2 d = Hc[i * s.m + i];
-    const double dd = d.x * d.x + d.y * d.y;
-    y[i] = dd > 0 ? cscale(cmulc(d, t), 1.0 / dd) : make_double2(0, 0);
-  }
-  for (int i = k; i < s.m; ++i) y[i] = make_double2(0, 0);
-}
-
-// x += sum_i y[r][i] V_i (over the columns built in this cycle); kcnt is then reset.
+// End of a cycle: every CTA solves the small triangular systems (one thread per right-hand
+// side), then x += sum_i y_i V_i over the columns built in the cycle.  The last CTA resets the
+// column counts, so a repeated call adds nothing.
 template <typename CT>
-__global__ void k_xupdate(FState s, CT* __restrict__ x, const CT* __restrict__ V, long long vstride) {
+__global__ void __launch_bounds__(ST_T) k_xupdate(FState s, CT* __restrict__ x, const CT* __restrict__ V,
+                                                  long long vstride) {
+  __shared__ double2 yd[MAXR][AMG_MAX_NTV];
   __shared__ CT yc[AMG_MAX_NTV][MAXR];
   __shared__ int kmax;
-  if (threadIdx.x == 0) {
-    int k = 0;
-    for (int r = 0; r < s.nrhs; ++r) k = max(k, s.kcnt[r]);
-    kmax = k;
-  }
-  for (int e = threadIdx.x; e < s.m * s.nrhs; e += blockDim.x) {
-    const int i = e / s.nrhs, r = e % s.nrhs;
-    yc[i][r] = from_d<CT>(s.yv[(long long)r * s.m + i]);
+  if (threadIdx.x == 0) kmax = 0;
+  __syncthreads();
+  if (threadIdx.x < s.nrhs) {
+    const int r = threadIdx.x;
+    const int k = __ldcg(s.kcnt + r);
+    const double2* Hc = s.H + (long long)r * (s.m + 1) * s.m;
+    const double2* gv = s.gv + (long long)r * (s.m + 1);
+    for (int i = k - 1; i >= 0; --i) {
+      double2 t = ld_cg(gv + i);
+      for (int l = i + 1; l < k; ++l) t = csub(t, cmul(ld_cg(Hc + i * s.m + l), yd[r][l]));
+      const double2 d = ld_cg(Hc + i * s.m + i);
+      const double dd = d.x * d.x + d.y * d.y;
+      yd[r][i] = dd > 0 ? cscale(cmulc(d, t), 1.0 / dd) : make_double2(0, 0);
+    }
+    for (int i = k; i < s.m; ++i) yd[r][i] = make_double2(0, 0);
+    atomicMax(&kmax, k);
   }
   __syncthreads();
-  const long long n = s.rows * s.nrhs;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-    const int r = (int)(e % s.nrhs);
-    CT v = x[e];
-    for (int i = 0; i < kmax; ++i) {
-      const CT q = V[i * vstride + e];
-      const CT c = yc[i][r];
-      v.x += c.x * q.x - c.y * q.y;
-      v.y += c.x * q.y + c.y * q.x;
-    }
-    x[e] = v;
+  for (int e = threadIdx.x; e < s.m * s.nrhs; e += blockDim.x) {
+    const int i = e / s.nrhs, r = e % s.nrhs;
+    yc[i][r] = from_d<CT>(yd[r][i]);
   }
+  __syncthreads();
+  const int km = kmax;
+  const long long n = s.rows * s.nrhs;
+  if (km > 0) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+         e += (long long)gridDim.x * blockDim.x) {
+      const int r = (int)(e % s.nrhs);
+      CT v = x[e];
+      for (int i = 0; i < km; ++i) {
+        const CT q = V[i * vstride + e];
+        const CT c = yc[i][r];
+        v.x += c.x * q.x - c.y * q.y;
+        v.y += c.x * q.y + c.y * q.x;
+      }
+      x[e] = v;
+    }
+  }
+  if (!last_block(s.counter, gridDim.x)) return;
+  if (threadIdx.x < s.nrhs) s.kcnt[threadIdx.x] = 0;
 }
 
-// w = b - w (restart residual; first = 1: w = b) and partial |w|^2.
+// w = b - w (restart residual; first = 1: w = b) and |w|^2; the last CTA starts the cycle:
+// beta = |r|, convergence test, g = (beta, 0, ...), invh = 1 / beta.
 template <typename CT>
 __global__ void __launch_bounds__(ST_T) k_residual(FState s, CT* __restrict__ w, const CT* __restrict__ b, int first) {
   if (*s.done) return;
@@ -249,9 +274,9 @@ __global__ void __launch_bounds__(ST_T) k_residual(FState s, CT* __restrict__ w,
       if (r >= s.nrhs) break;
       CT v = b[row * s.nrhs + r];
       if (!first) {
-        const CT a = w[row * s.nrhs + r];
-        v.x -= a.x;
-        v.y -= a.y;
+        const CT q = w[row * s.nrhs + r];
+        v.x -= q.x;
+        v.y -= q.y;
       }
       w[row * s.nrhs + r] = v;
       a[r].x += v.x * v.x + v.y * v.y;
@@ -260,19 +285,15 @@ __global__ void __launch_bounds__(ST_T) k_residual(FState s, CT* __restrict__ w,
   double2 acc[MAXR];
 #pragma unroll
   for (int r = 0; r < MAXR; ++r) acc[r] = to_d(a[r]);
-  cta_sum_store(acc, s.nrhs, s.part + (long long)blockIdx.x * s.nrhs, 1);
-}
-
-// Start of a restart cycle: beta = |r|, convergence check, g = (beta, 0, ...), invh = 1/beta.
-__global__ void k_start(FState s, int first) {
+  cta_sum_store(acc, s.nrhs, s.part + (long long)blockIdx.x * s.nrhs);
+  if (!last_block(s.counter, s.nblk)) return;
   __shared__ int any;
-  if (*s.done) return;
   if (threadIdx.x == 0) any = 0;
   __syncthreads();
-  const int r = threadIdx.x;
-  if (r < s.nrhs) {
+  if (threadIdx.x < s.nrhs) {
+    const int r = threadIdx.x;
     double n2 = 0;
-    for (int b = 0; b < s.nblk; ++b) n2 += s.part[(long long)b * s.nrhs + r].x;
+    for (int bb = 0; bb < s.nblk; ++bb) n2 += ld_cg(s.part + (long long)bb * s.nrhs + r).x;
     const double beta = sqrt(n2);
     if (first) {
       s.bnorm[r] = beta;
@@ -299,135 +320,103 @@ __global__ void k_start(FState s, int first) {
   if (threadIdx.x == 0 && !any) *s.done = 1;
 }
 
+size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+size_t scal_doubles(int nrhs, int m) { return (size_t)nrhs * ((m + 1) * m + 3 * m + 1) * 2 + 3 * (size_t)nrhs; }
+
 template <typename CT>
 amg_status solve_impl(amg_coarse* h, const CT* b, CT* x, int nrhs, double tol, int m, int max_applies,
-                      cudaStream_t st, double* info) {
+                      cudaStream_t st, double* info, unsigned char* ws, bool poll) {
   const Geom& g = h->g;
   const long long rows = g.Vc * g.nc;
   const long long vstride = rows * nrhs;
-  SolveWork& sw = h->sw;
-  const int nblk = 2 * 152;
-  if (sw.nrhs != nrhs || sw.restart != m) {
-    cudaStreamSynchronize(st);
-    cudaFree(sw.basis);
-    cudaFree(sw.w);
-    cudaFree(sw.part);
-    cudaFree(sw.scal);
-    cudaFree(sw.flags);
-    sw = SolveWork();
-    AMG_CUDA_TRY(cudaMalloc(&sw.basis, (size_t)(m + 1) * vstride * sizeof(CT)));
-    AMG_CUDA_TRY(cudaMalloc(&sw.w, (size_t)vstride * sizeof(CT)));
-    AMG_CUDA_TRY(cudaMalloc(&sw.part, (size_t)(m + 1) * nblk * nrhs * sizeof(double2)));
-    const size_t nscal = (size_t)nrhs * ((m + 1) * m + 2 * m + (m + 1) + m) * 2 + 4 * nrhs;
-    AMG_CUDA_TRY(cudaMalloc(&sw.scal, nscal * sizeof(double)));
-    AMG_CUDA_TRY(cudaMalloc(&sw.flags, (size_t)(3 * nrhs + 1) * sizeof(int)));
-    sw.nrhs = nrhs;
-    sw.restart = m;
-  }
   FState s;
   s.m = m;
   s.nrhs = nrhs;
-  s.nblk = nblk;
+  s.nblk = NBLK;
   s.rows = rows;
   s.tol = tol;
-  double2* p = (double2*)sw.scal;
-  s.H = p;
-  p += (size_t)nrhs * (m + 1) * m;
-  s.cs = p;
-  p += (size_t)nrhs * m;
-  s.sn = p;
-  p += (size_t)nrhs * m;
-  s.gv = p;
-  p += (size_t)nrhs * (m + 1);
-  s.yv = p;
-  p += (size_t)nrhs * m;
-  double* q = (double*)p;
+  unsigned char* p = ws;
+  CT* V = (CT*)p;
+  CT* w = V + (size_t)(m + 1) * vstride;
+  p += align256((size_t)(m + 2) * vstride * sizeof(CT));
+  s.part = (double2*)p;
+  p += align256((size_t)(m + 1) * NBLK * nrhs * sizeof(double2));
+  double2* d2 = (double2*)p;
+  s.H = d2;
+  d2 += (size_t)nrhs * (m + 1) * m;
+  s.cs = d2;
+  d2 += (size_t)nrhs * m;
+  s.sn = d2;
+  d2 += (size_t)nrhs * m;
+  s.gv = d2;
+  d2 += (size_t)nrhs * (m + 1);
+  double* q = (double*)d2;
   s.bnorm = q;
   s.relres = q + nrhs;
   s.invh = q + 2 * nrhs;
-  s.part = sw.part;
-  s.active = sw.flags;
-  s.kcnt = sw.flags + nrhs;
-  s.applies = sw.flags + 2 * nrhs;
-  s.done = sw.flags + 3 * nrhs;
-  CT* V = (CT*)sw.basis;
-  CT* w = (CT*)sw.w;
+  p += align256(scal_doubles(nrhs, m) * sizeof(double));
+  int* fl = (int*)p;
+  s.active = fl;
+  s.kcnt = fl + nrhs;
+  s.applies = fl + 2 * nrhs;
+  s.done = fl + 3 * nrhs;
+  s.counter = (unsigned*)(fl + 3 * nrhs + 4);
   const unsigned egrid = 4 * 152;
-  AMG_CUDA_TRY(cudaMemsetAsync(s.done, 0, sizeof(int), st));
+  AMG_CUDA_TRY(cudaMemsetAsync(fl, 0, (4 * (size_t)nrhs + 8) * sizeof(int), st));
   AMG_CUDA_TRY(cudaMemsetAsync(x, 0, (size_t)vstride * sizeof(CT), st));
-  k_residual<CT><<<nblk, ST_T, 0, st>>>(s, w, b, 1);
-  h->launches++;
-  k_start<<<1, 64, 0, st>>>(s, 1);
-  h->launches++;
+  k_residual<CT><<<NBLK, ST_T, 0, st>>>(s, w, b, 1);
   k_scale<CT><<<egrid, 256, 0, st>>>(s, V, w);
-  h->launches++;
   AMG_LAUNCH_CHECK();
-  // host-side view of `done`, two iterations behind the launch front
-  int* hflag = nullptr;
-  AMG_CUDA_TRY(cudaHostAlloc((void**)&hflag, 64 * sizeof(int), cudaHostAllocDefault));
-  cudaEvent_t ev[64];
-  for (int k = 0; k < 64; ++k) cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming);
-  int launched = 0, polled = 0, issued = 0;
+  h->launches += 2;
+  SolveWork& sw = h->sw;
+  int issued = 0, polled = 0;
   bool stop = false;
-  auto poll_point = [&]() -> void {
-    const int slot = issued % 64;
-    cudaMemcpyAsync(hflag + slot, s.done, sizeof(int), cudaMemcpyDeviceToHost, st);
-    cudaEventRecord(ev[slot], st);
+  auto poll_point = [&]() {
+    if (!poll) return;
+    const int slot = issued % SolveWork::kRing;
+    cudaMemcpyAsync(sw.hflag + slot, s.done, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaEventRecord(sw.ev[slot], st);
     ++issued;
     while (issued - polled > 2) {
-      const int ps = polled % 64;
-      cudaEventSynchronize(ev[ps]);
-      if (hflag[ps]) stop = true;
+      const int ps = polled % SolveWork::kRing;
+      cudaEventSynchronize(sw.ev[ps]);
+      if (sw.hflag[ps]) stop = true;
       ++polled;
     }
   };
-  amg_status status = AMG_OK;
+  int launched = 0;
   while (launched < max_applies && !stop) {
     const int mc = std::min(m, max_applies - launched);
     for (int j = 0; j < mc && !stop; ++j) {
-      status = amg_internal_apply_ex(h, V + j * vstride, w, nrhs, st, s.done);
-      if (status != AMG_OK) break;
-      k_dots<CT><<<dim3(nblk, j + 1), ST_T, 0, st>>>(s, w, V, vstride);
-      h->launches++;
-      k_finish_dots<<<((j + 1) * nrhs + 127) / 128, 128, 0, st>>>(s, j);
-      h->launches++;
-      k_update<CT><<<nblk, ST_T, 0, st>>>(s, w, V, vstride, j);
-      h->launches++;
-      k_arnoldi<<<1, 64, 0, st>>>(s, j);
-      h->launches++;
+      amg_status status = amg_internal_apply_ex(h, V + j * vstride, w, nrhs, st, s.done);
+      if (status != AMG_OK) return status;
+      k_dots<CT><<<dim3(NBLK, j + 1), ST_T, 0, st>>>(s, w, V, vstride, j);
+      k_update<CT><<<NBLK, ST_T, 0, st>>>(s, w, V, vstride, j);
       k_scale<CT><<<egrid, 256, 0, st>>>(s, V + (j + 1) * vstride, w);
-      h->launches++;
+      AMG_LAUNCH_CHECK();
+      h->launches += 3;
       ++launched;
       poll_point();
     }
-    if (status != AMG_OK) break;
-    k_backsolve<<<1, 64, 0, st>>>(s);
-    h->launches++;
-    k_xupdate<CT><<<egrid, 256, 0, st>>>(s, x, V, vstride);
-    h->launches++;
+    k_xupdate<CT><<<egrid, ST_T, 0, st>>>(s, x, V, vstride);
+    AMG_LAUNCH_CHECK();
+    h->launches += 1;
     if (launched >= max_applies || stop) break;
-    status = amg_internal_apply_ex(h, x, w, nrhs, st, s.done);
-    if (status != AMG_OK) break;
+    amg_status status = amg_internal_apply_ex(h, x, w, nrhs, st, s.done);
+    if (status != AMG_OK) return status;
     ++launched;
-    k_residual<CT><<<nblk, ST_T, 0, st>>>(s, w, b, 0);
-    h->launches++;
-    k_start<<<1, 64, 0, st>>>(s, 0);
-    h->launches++;
+    k_residual<CT><<<NBLK, ST_T, 0, st>>>(s, w, b, 0);
     k_scale<CT><<<egrid, 256, 0, st>>>(s, V, w);
-    h->launches++;
+    AMG_LAUNCH_CHECK();
+    h->launches += 2;
     poll_point();
   }
-  cudaError_t le = cudaGetLastError();
-  cudaStreamSynchronize(st);
-  for (int k = 0; k < 64; ++k) cudaEventDestroy(ev[k]);
-  cudaFreeHost(hflag);
-  if (status != AMG_OK) return status;
-  if (le != cudaSuccess) return AMG_ERR_CUDA;
   if (info) {
     int applies[MAXR];
     double rel[MAXR];
-    AMG_CUDA_TRY(cudaMemcpy(applies, s.applies, nrhs * sizeof(int), cudaMemcpyDeviceToHost));
-    AMG_CUDA_TRY(cudaMemcpy(rel, s.relres, nrhs * sizeof(double), cudaMemcpyDeviceToHost));
+    AMG_CUDA_TRY(cudaMemcpyAsync(applies, s.applies, nrhs * sizeof(int), cudaMemcpyDeviceToHost, st));
+    AMG_CUDA_TRY(cudaMemcpyAsync(rel, s.relres, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
+    AMG_CUDA_TRY(cudaStreamSynchronize(st));
     for (int r = 0; r < nrhs; ++r) {
       info[2 * r] = applies[r];
       info[2 * r + 1] = rel[r];
@@ -438,10 +427,39 @@ amg_status solve_impl(amg_coarse* h, const CT* b, CT* x, int nrhs, double tol, i
 
 }  // namespace
 
+size_t amg_internal_solve_bytes(const amg_coarse* h, int nrhs, int m) {
+  const size_t N = (size_t)h->g.Vc * h->g.nc * nrhs * coarse_elem_bytes(h);
+  return align256((size_t)(m + 2) * N) + align256((size_t)(m + 1) * NBLK * nrhs * sizeof(double2)) +
+         align256(scal_doubles(nrhs, m) * sizeof(double)) + align256((4 * (size_t)nrhs + 8) * sizeof(int));
+}
+
+amg_status amg_internal_solve_ws(amg_coarse* h, const void* b, void* x, int nrhs, double tol, int restart,
+                                 int max_applies, cudaStream_t s, double* info, void* ws, bool poll) {
+  if (nrhs > MAXR || restart < 1 || restart > AMG_MAX_NTV || max_applies < 1) return AMG_ERR_INVALID_ARG;
+  if (h->p.vec_prec == AMG_FP64)
+    return solve_impl<double2>(h, (const double2*)b, (double2*)x, nrhs, tol, restart, max_applies, s, info,
+                               (unsigned char*)ws, poll);
+  return solve_impl<float2>(h, (const float2*)b, (float2*)x, nrhs, tol, restart, max_applies, s, info,
+                            (unsigned char*)ws, poll);
+}
+
 amg_status amg_internal_solve(amg_coarse* h, const void* b, void* x, int nrhs, double tol, int restart,
                               int max_applies, cudaStream_t s, double* info) {
   if (nrhs > MAXR || restart < 1 || restart > AMG_MAX_NTV || max_applies < 1) return AMG_ERR_INVALID_ARG;
-  if (h->p.vec_prec == AMG_FP64)
-    return solve_impl<double2>(h, (const double2*)b, (double2*)x, nrhs, tol, restart, max_applies, s, info);
-  return solve_impl<float2>(h, (const float2*)b, (float2*)x, nrhs, tol, restart, max_applies, s, info);
+  SolveWork& sw = h->sw;
+  const size_t need = amg_internal_solve_bytes(h, nrhs, restart);
+  if (need > sw.bytes) {
+    AMG_CUDA_TRY(cudaStreamSynchronize(s));
+    cudaFree(sw.buf);
+    sw.buf = nullptr;
+    sw.bytes = 0;
+    AMG_CUDA_TRY(cudaMalloc(&sw.buf, need));
+    sw.bytes = need;
+  }
+  if (!sw.hflag) {
+    AMG_CUDA_TRY(cudaHostAlloc((void**)&sw.hflag, SolveWork::kRing * sizeof(int), cudaHostAllocDefault));
+    for (int k = 0; k < SolveWork::kRing; ++k)
+      AMG_CUDA_TRY(cudaEventCreateWithFlags(&sw.ev[k], cudaEventDisableTiming));
+  }
+  return amg_internal_solve_ws(h, b, x, nrhs, tol, restart, max_applies, s, info, sw.buf, true);
 }
