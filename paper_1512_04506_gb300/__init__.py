@@ -45,7 +45,7 @@ class amg_params(ctypes.Structure):
 class AmgError(RuntimeError):
     def __init__(self, status, where):
         self.status = status
-        detail = amg_last_error() if status in (AMG_ERR_CUDA, AMG_ERR_OOM) else ""
+        detail = amg_last_error() if status in (AMG_ERR_CUDA, AMG_ERR_OOM, AMG_ERR_INVALID_ARG) else ""
         super().__init__("%s: %s (status %d) %s" % (where, amg_status_string(status), status, detail))
 
 

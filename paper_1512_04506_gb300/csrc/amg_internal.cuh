@@ -124,6 +124,8 @@ struct amg_coarse {
 // ---------------------------------------------------------------- shared host helpers
 // Records the failing CUDA call of the calling thread (read back by amg_last_error()).
 void amg_note_cuda_error(const char* file, int line, cudaError_t e);
+// Records a printf-style message as the calling thread's last error.
+void amg_note_error(const char* fmt, ...);
 
 #define AMG_CUDA_TRY(call)                                \
   do {                                                    \

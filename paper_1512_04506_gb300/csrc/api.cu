@@ -2,10 +2,18 @@
 #include "amg_internal.cuh"
 
 #include <new>
+#include <stdarg.h>
 #include <stdio.h>
 #include <vector>
 
 static thread_local char g_last_error[256] = "";
+
+void amg_note_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+  va_end(ap);
+}
 
 void amg_note_cuda_error(const char* file, int line, cudaError_t e) {
   const char* base = strrchr(file, '/');

@@ -8,7 +8,7 @@
 // partial sums into column j of H), the update w -= sum H_ij V_i with |w|^2 (whose last CTA does
 // the Givens rotation and the convergence test), and the scaling V_{j+1} = w / h_{j+1,j}.  Once
 // every right-hand side has converged the device flag `done` makes every later kernel return at
-// once.  The host either learns of it through an event two steps behind the launch front (so
+// once.  The host either learns of it through an event one step behind the launch front (so
 // the GPU never waits for the host) or, without events, launches the whole budget.
 #include "amg_internal.cuh"
 
@@ -75,6 +75,21 @@ __device__ inline bool last_block(unsigned* counter, unsigned total) {
   return last;
 }
 
+// Sum over the nblk partials of pair t (layout part[(i * nblk + b) * nrhs + r], t = i * nrhs + r)
+// by one warp: lanes stride over the partials, then a shuffle sum; valid in lane 0.
+__device__ inline double2 warp_sum_partials(const double2* part, int nblk, int nrhs, int t) {
+  const int lane = threadIdx.x & 31;
+  const int i = t / nrhs, r = t % nrhs;
+  double2 sum = make_double2(0, 0);
+  for (int b = lane; b < nblk; b += 32) sum = cadd(sum, ld_cg(part + ((long long)i * nblk + b) * nrhs + r));
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    sum.x += __shfl_xor_sync(0xffffffffu, sum.x, o);
+    sum.y += __shfl_xor_sync(0xffffffffu, sum.y, o);
+  }
+  return sum;
+}
+
 // Givens rotation and convergence test of Arnoldi step j for right-hand side r, given |w|^2.
 __device__ void arnoldi_step(FState& s, int r, int j, double n2, int* any) {
   if (!s.active[r]) {
@@ -139,11 +154,11 @@ __global__ void __launch_bounds__(ST_T) k_dots(FState s, const CT* __restrict__ 
   for (int r = 0; r < MAXR; ++r) acc[r] = to_d(a[r]);
   cta_sum_store(acc, s.nrhs, s.part + ((long long)i * s.nblk + blockIdx.x) * s.nrhs);
   if (!last_block(s.counter, s.nblk * (j + 1))) return;
-  for (int t = threadIdx.x; t < (j + 1) * s.nrhs; t += blockDim.x) {
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int t = warp; t < (j + 1) * s.nrhs; t += nw) {
+    const double2 sum = warp_sum_partials(s.part, s.nblk, s.nrhs, t);
     const int ii = t / s.nrhs, r = t % s.nrhs;
-    double2 sum = make_double2(0, 0);
-    for (int b = 0; b < s.nblk; ++b) sum = cadd(sum, ld_cg(s.part + ((long long)ii * s.nblk + b) * s.nrhs + r));
-    s.H[((long long)r * (s.m + 1) + ii) * s.m + j] = s.active[r] ? sum : make_double2(0, 0);
+    if ((threadIdx.x & 31) == 0) s.H[((long long)r * (s.m + 1) + ii) * s.m + j] = s.active[r] ? sum : make_double2(0, 0);
   }
 }
 
@@ -183,14 +198,14 @@ __global__ void __launch_bounds__(ST_T) k_update(FState s, CT* __restrict__ w, c
   cta_sum_store(acc, s.nrhs, s.part + (long long)blockIdx.x * s.nrhs);
   if (!last_block(s.counter, s.nblk)) return;
   __shared__ int any;
+  __shared__ double n2s[MAXR];
   if (threadIdx.x == 0) any = 0;
-  __syncthreads();
-  if (threadIdx.x < s.nrhs) {
-    const int r = threadIdx.x;
-    double n2 = 0;
-    for (int b = 0; b < s.nblk; ++b) n2 += ld_cg(s.part + (long long)b * s.nrhs + r).x;
-    arnoldi_step(s, r, j, n2, &any);
+  for (int r = threadIdx.x >> 5; r < s.nrhs; r += blockDim.x >> 5) {
+    const double2 v = warp_sum_partials(s.part, s.nblk, s.nrhs, r);
+    if ((threadIdx.x & 31) == 0) n2s[r] = v.x;
   }
+  __syncthreads();
+  if (threadIdx.x < s.nrhs) arnoldi_step(s, threadIdx.x, j, n2s[threadIdx.x], &any);
   __syncthreads();
   if (threadIdx.x == 0 && !any) *s.done = 1;
 }
@@ -288,13 +303,16 @@ __global__ void __launch_bounds__(ST_T) k_residual(FState s, CT* __restrict__ w,
   cta_sum_store(acc, s.nrhs, s.part + (long long)blockIdx.x * s.nrhs);
   if (!last_block(s.counter, s.nblk)) return;
   __shared__ int any;
+  __shared__ double n2s[MAXR];
   if (threadIdx.x == 0) any = 0;
+  for (int r = threadIdx.x >> 5; r < s.nrhs; r += blockDim.x >> 5) {
+    const double2 v = warp_sum_partials(s.part, s.nblk, s.nrhs, r);
+    if ((threadIdx.x & 31) == 0) n2s[r] = v.x;
+  }
   __syncthreads();
   if (threadIdx.x < s.nrhs) {
     const int r = threadIdx.x;
-    double n2 = 0;
-    for (int bb = 0; bb < s.nblk; ++bb) n2 += ld_cg(s.part + (long long)bb * s.nrhs + r).x;
-    const double beta = sqrt(n2);
+    const double beta = sqrt(n2s[r]);
     if (first) {
       s.bnorm[r] = beta;
       s.active[r] = beta > 0;
@@ -377,7 +395,7 @@ amg_status solve_impl(amg_coarse* h, const CT* b, CT* x, int nrhs, double tol, i
     cudaMemcpyAsync(sw.hflag + slot, s.done, sizeof(int), cudaMemcpyDeviceToHost, st);
     cudaEventRecord(sw.ev[slot], st);
     ++issued;
-    while (issued - polled > 2) {
+    while (issued - polled > 1) {
       const int ps = polled % SolveWork::kRing;
       cudaEventSynchronize(sw.ev[ps]);
       if (sw.hflag[ps]) stop = true;
