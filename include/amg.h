@@ -118,6 +118,25 @@ amg_status amg_coarse_solve(amg_handle h, const void *d_b, void *d_x, int nrhs, 
                             int restart, int max_applies, void *stream, double *info);
 
 /*
+ * amg_coarse_solve_noalloc -- amg_coarse_solve for callers that may not allocate device
+ * memory when they solve (a memory manager that forbids allocations outside its pool, a
+ * latency path that cannot take cudaMalloc's implicit synchronisation).  The paper has no
+ * counterpart; it is a property of this library's interface.  Same arguments and results as
+ * amg_coarse_solve, but the Krylov workspace lives in a scratch array compiled into the library
+ * (amg_noalloc_scratch_bytes(), 16 MiB, held by every GPU that loads the library until the
+ * process exits) and nothing is allocated.  A request whose workspace does not fit is rejected
+ * with AMG_ERR_INVALID_ARG (amg_last_error() says by how much).  All calls share the array:
+ * calls whose kernels overlap on the GPU race and must be serialised by the caller.  The first
+ * call on a device looks up the array's device address (with that device current) and should
+ * come before any stream capture.  Without info the call does not synchronise; it then
+ * launches the whole max_applies budget, kernels after convergence returning at once.
+ */
+amg_status amg_coarse_solve_noalloc(amg_handle h, const void *d_b, void *d_x, int nrhs, double tol,
+                                    int restart, int max_applies, void *stream, double *info);
+/* Size in bytes of the scratch array used by amg_coarse_solve_noalloc. */
+size_t amg_noalloc_scratch_bytes(void);
+
+/*
  * amg_cgc -- one coarse-grid correction, Alg. 2: x = P FGMRES(D_c, R y).
  * Same arguments as amg_coarse_solve for the solve.
  */

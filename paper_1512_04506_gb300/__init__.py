@@ -62,6 +62,7 @@ _proto = {
     "amg_coarse_apply": [_vp, _vp, _vp, _i, _vp],
     "amg_prolong": [_vp, _vp, _vp, _i, _vp],
     "amg_coarse_solve": [_vp, _vp, _vp, _i, _d, _i, _i, _vp, ctypes.POINTER(_d)],
+    "amg_coarse_solve_noalloc": [_vp, _vp, _vp, _i, _d, _i, _i, _vp, ctypes.POINTER(_d)],
     "amg_cgc": [_vp, _vp, _vp, _i, _d, _i, _i, _vp, ctypes.POINTER(_d)],
     "amg_batch_cgc": [ctypes.POINTER(_vp), _i, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                       ctypes.POINTER(_i), _vp],
@@ -82,8 +83,14 @@ lib.amg_status_string.argtypes = [ctypes.c_int]
 lib.amg_status_string.restype = ctypes.c_char_p
 lib.amg_last_error.argtypes = []
 lib.amg_last_error.restype = ctypes.c_char_p
+lib.amg_noalloc_scratch_bytes.argtypes = []
+lib.amg_noalloc_scratch_bytes.restype = ctypes.c_size_t
 
-EXPORTED = sorted(list(_proto) + ["amg_status_string", "amg_last_error"])
+EXPORTED = sorted(list(_proto) + ["amg_status_string", "amg_last_error", "amg_noalloc_scratch_bytes"])
+
+
+def amg_noalloc_scratch_bytes():
+    return lib.amg_noalloc_scratch_bytes()
 
 
 def amg_last_error():
@@ -172,6 +179,14 @@ def amg_coarse_solve(h, b, x, nrhs=1, tol=0.05, restart=30, max_applies=200, str
     buf = _info(nrhs, info)
     _check(lib.amg_coarse_solve(h, ptr(b), ptr(x), nrhs, tol, restart, max_applies, stream_ptr(stream), buf),
            "amg_coarse_solve")
+    return _info_out(buf, nrhs)
+
+
+def amg_coarse_solve_noalloc(h, b, x, nrhs=1, tol=0.05, restart=30, max_applies=200, stream=None, info=True):
+    """amg_coarse_solve on the library's fixed scratch array: allocates no device memory."""
+    buf = _info(nrhs, info)
+    _check(lib.amg_coarse_solve_noalloc(h, ptr(b), ptr(x), nrhs, tol, restart, max_applies,
+                                        stream_ptr(stream), buf), "amg_coarse_solve_noalloc")
     return _info_out(buf, nrhs)
 
 
