@@ -373,7 +373,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--lattice", default=None,
+                    help="Lx,Ly,Lz,Lt override of the 32^4 lattice (smaller cases for ncu captures)")
     args = ap.parse_args()
+    if args.lattice:
+        global L, WORKLOAD
+        L = tuple(int(v) for v in args.lattice.split(","))
+        WORKLOAD = "%dx%dx%dx%d variant of %s" % (L + (WORKLOAD,))
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
