@@ -169,6 +169,7 @@ amg_status amg_internal_batch(amg_coarse* const* hs, int n, const void* const* y
 amg_status amg_internal_export_stored(amg_coarse* h, double2* out);
 amg_status amg_internal_tc_prepare(amg_coarse* h, cudaStream_t s);
 void amg_internal_free_tc(amg_coarse* h);
-// Coarse application whose CTAs return at once while *skip != 0 (used inside the solver).
+// Coarse application for the solver: CTAs return at once while *skip != 0; with xscale the input
+// is xc * xscale[r] and that scaled input is also stored to vout (both may be null).
 amg_status amg_internal_apply_ex(amg_coarse* h, const void* xc, void* yc, int nrhs, cudaStream_t s,
-                                 const int* skip);
+                                 const int* skip, const double* xscale, void* vout);

@@ -4,9 +4,10 @@
 // scalars (Hessenberg matrix, rotations, residual estimates, convergence flags) live on the
 // device, so the host only launches kernels.
 //
-// One Arnoldi step is four launches: D_c V_j, the dots <V_i, w> (whose last CTA reduces the
-// partial sums into column j of H), the update w -= sum H_ij V_i with |w|^2 (whose last CTA does
-// the Givens rotation and the convergence test), and the scaling V_{j+1} = w / h_{j+1,j}.  Once
+// One Arnoldi step is three launches: w = D_c V_j (the application reads the unnormalised
+// vector times 1/h_{j,j-1} and stores V_j on the way), the dots <V_i, w> (whose last CTA reduces
+// the partial sums into column j of H), and the update w -= sum H_ij V_i with |w|^2 (whose last
+// CTA does the Givens rotation and the convergence test).  Once
 // every right-hand side has converged the device flag `done` makes every later kernel return at
 // once.  The host either learns of it through an event one step behind the launch front (so
 // the GPU never waits for the host) or, without events, launches the whole budget.
@@ -101,21 +102,29 @@ __device__ void arnoldi_step(FState& s, int r, int j, double n2, int* any) {
   double2* cs = s.cs + (long long)r * s.m;
   double2* sn = s.sn + (long long)r * s.m;
   double2* gv = s.gv + (long long)r * (s.m + 1);
+  // gather the column and the earlier rotations first (independent loads), rotate locally
+  double2 col[AMG_MAX_NTV + 1], c_[AMG_MAX_NTV], s_[AMG_MAX_NTV];
+  for (int i = 0; i <= j; ++i) col[i] = __ldcg(Hc + i * s.m + j);
   for (int i = 0; i < j; ++i) {
-    const double2 a = Hc[i * s.m + j], b = Hc[(i + 1) * s.m + j];
-    const double2 t = cadd(cmul(cs[i], a), cmul(sn[i], b));
-    Hc[(i + 1) * s.m + j] = csub(cmul(cconj(cs[i]), b), cmul(cconj(sn[i]), a));
-    Hc[i * s.m + j] = t;
+    c_[i] = __ldcg(cs + i);
+    s_[i] = __ldcg(sn + i);
   }
-  const double2 a = Hc[j * s.m + j];
+  const double2 gj = __ldcg(gv + j);
+  col[j + 1] = make_double2(hnext, 0);
+  for (int i = 0; i < j; ++i) {
+    const double2 a = col[i], b = col[i + 1];
+    col[i] = cadd(cmul(c_[i], a), cmul(s_[i], b));
+    col[i + 1] = csub(cmul(cconj(c_[i]), b), cmul(cconj(s_[i]), a));
+  }
+  const double2 a = col[j];
   const double den = sqrt(a.x * a.x + a.y * a.y + hnext * hnext);
   const double2 c = den > 0 ? cscale(cconj(a), 1.0 / den) : make_double2(1, 0);
   const double2 sv = den > 0 ? make_double2(hnext / den, 0) : make_double2(0, 0);
+  col[j] = make_double2(den, 0);
+  col[j + 1] = make_double2(0, 0);
+  for (int i = 0; i <= j + 1; ++i) Hc[i * s.m + j] = col[i];
   cs[j] = c;
   sn[j] = sv;
-  Hc[j * s.m + j] = make_double2(den, 0);
-  Hc[(j + 1) * s.m + j] = make_double2(0, 0);
-  const double2 gj = gv[j];
   gv[j + 1] = cscale(cmul(cconj(sv), gj), -1.0);
   gv[j] = cmul(c, gj);
   const double rel = sqrt(gv[j + 1].x * gv[j + 1].x + gv[j + 1].y * gv[j + 1].y) / s.bnorm[r];
@@ -208,18 +217,6 @@ __global__ void __launch_bounds__(ST_T) k_update(FState s, CT* __restrict__ w, c
   if (threadIdx.x < s.nrhs) arnoldi_step(s, threadIdx.x, j, n2s[threadIdx.x], &any);
   __syncthreads();
   if (threadIdx.x == 0 && !any) *s.done = 1;
-}
-
-// out = w * invh[r]
-template <typename CT>
-__global__ void k_scale(FState s, CT* __restrict__ out, const CT* __restrict__ w) {
-  if (*s.done) return;
-  const long long n = s.rows * s.nrhs;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-    const CT v = w[e];
-    const auto f = (decltype(v.x))__ldcg(s.invh + e % s.nrhs);
-    out[e] = CT{v.x * f, v.y * f};
-  }
 }
 
 // End of a cycle: every CTA solves the small triangular systems (one thread per right-hand
@@ -354,9 +351,10 @@ amg_status solve_impl(amg_coarse* h, const CT* b, CT* x, int nrhs, double tol, i
   s.rows = rows;
   s.tol = tol;
   unsigned char* p = ws;
-  CT* V = (CT*)p;
-  CT* w = V + (size_t)(m + 1) * vstride;
-  p += align256((size_t)(m + 2) * vstride * sizeof(CT));
+  CT* V = (CT*)p;                       // V_0 .. V_m
+  CT* cur = V + (size_t)(m + 1) * vstride;  // unnormalised next basis vector (V_j = cur * invh)
+  CT* nxt = cur + vstride;                  // D_c V_j, orthogonalised in place
+  p += align256((size_t)(m + 3) * vstride * sizeof(CT));
   s.part = (double2*)p;
   p += align256((size_t)(m + 1) * NBLK * nrhs * sizeof(double2));
   double2* d2 = (double2*)p;
@@ -382,10 +380,9 @@ amg_status solve_impl(amg_coarse* h, const CT* b, CT* x, int nrhs, double tol, i
   const unsigned egrid = 4 * 152;
   AMG_CUDA_TRY(cudaMemsetAsync(fl, 0, (4 * (size_t)nrhs + 8) * sizeof(int), st));
   AMG_CUDA_TRY(cudaMemsetAsync(x, 0, (size_t)vstride * sizeof(CT), st));
-  k_residual<CT><<<NBLK, ST_T, 0, st>>>(s, w, b, 1);
-  k_scale<CT><<<egrid, 256, 0, st>>>(s, V, w);
+  k_residual<CT><<<NBLK, ST_T, 0, st>>>(s, cur, b, 1);
   AMG_LAUNCH_CHECK();
-  h->launches += 2;
+  h->launches += 1;
   SolveWork& sw = h->sw;
   int issued = 0, polled = 0;
   bool stop = false;
@@ -406,13 +403,14 @@ amg_status solve_impl(amg_coarse* h, const CT* b, CT* x, int nrhs, double tol, i
   while (launched < max_applies && !stop) {
     const int mc = std::min(m, max_applies - launched);
     for (int j = 0; j < mc && !stop; ++j) {
-      amg_status status = amg_internal_apply_ex(h, V + j * vstride, w, nrhs, st, s.done);
+      // V_j = cur / h_{j,j-1} is written by the application itself, which reads cur scaled
+      amg_status status = amg_internal_apply_ex(h, cur, nxt, nrhs, st, s.done, s.invh, V + j * vstride);
       if (status != AMG_OK) return status;
-      k_dots<CT><<<dim3(NBLK, j + 1), ST_T, 0, st>>>(s, w, V, vstride, j);
-      k_update<CT><<<NBLK, ST_T, 0, st>>>(s, w, V, vstride, j);
-      k_scale<CT><<<egrid, 256, 0, st>>>(s, V + (j + 1) * vstride, w);
+      k_dots<CT><<<dim3(NBLK, j + 1), ST_T, 0, st>>>(s, nxt, V, vstride, j);
+      k_update<CT><<<NBLK, ST_T, 0, st>>>(s, nxt, V, vstride, j);
       AMG_LAUNCH_CHECK();
-      h->launches += 3;
+      h->launches += 2;
+      std::swap(cur, nxt);
       ++launched;
       poll_point();
     }
@@ -420,13 +418,12 @@ amg_status solve_impl(amg_coarse* h, const CT* b, CT* x, int nrhs, double tol, i
     AMG_LAUNCH_CHECK();
     h->launches += 1;
     if (launched >= max_applies || stop) break;
-    amg_status status = amg_internal_apply_ex(h, x, w, nrhs, st, s.done);
+    amg_status status = amg_internal_apply_ex(h, x, cur, nrhs, st, s.done, nullptr, nullptr);
     if (status != AMG_OK) return status;
     ++launched;
-    k_residual<CT><<<NBLK, ST_T, 0, st>>>(s, w, b, 0);
-    k_scale<CT><<<egrid, 256, 0, st>>>(s, V, w);
+    k_residual<CT><<<NBLK, ST_T, 0, st>>>(s, cur, b, 0);
     AMG_LAUNCH_CHECK();
-    h->launches += 2;
+    h->launches += 1;
     poll_point();
   }
   if (info) {
@@ -447,7 +444,7 @@ amg_status solve_impl(amg_coarse* h, const CT* b, CT* x, int nrhs, double tol, i
 
 size_t amg_internal_solve_bytes(const amg_coarse* h, int nrhs, int m) {
   const size_t N = (size_t)h->g.Vc * h->g.nc * nrhs * coarse_elem_bytes(h);
-  return align256((size_t)(m + 2) * N) + align256((size_t)(m + 1) * NBLK * nrhs * sizeof(double2)) +
+  return align256((size_t)(m + 3) * N) + align256((size_t)(m + 1) * NBLK * nrhs * sizeof(double2)) +
          align256(scal_doubles(nrhs, m) * sizeof(double)) + align256((4 * (size_t)nrhs + 8) * sizeof(int));
 }
 

@@ -1,0 +1,650 @@
+// Persistent, TMA-fed streaming kernels for the three HBM-bound steps of the coarse-grid
+// correction (Alg. 2): restriction y_c = R y (Eq. R, Alg. 6), coarse operator y_c = D_c x_c and
+// prolongation x = P x_c with P = R^dagger.
+//
+// Each CTA is persistent over work items (blocks for R / P, coarse sites for D_c).  Warp 0 is
+// the producer: one lane streams the item's matrix into a ring of shared-memory stages with
+// cp.async.bulk, each stage guarded by a "full" mbarrier (transaction bytes) and an "empty"
+// mbarrier (consumer release).  The other warps consume the stages from shared memory.  The
+// producer runs ahead across item boundaries, so the stream never stops while the consumers
+// stage the small vectors of the next item.  Every wait is bounded (about one second of clock
+// cycles); a wait that runs out sets AMG_EBIT_TIMEOUT, makes the CTA skip the rest of its work,
+// and the producer still waits (bounded) for the copies it has issued before the CTA exits.
+#include "amg_internal.cuh"
+
+namespace {
+
+// ------------------------------------------------------------------ PTX helpers
+__device__ inline unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ inline void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ inline void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ inline void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ inline void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ inline bool mbar_test(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// global -> shared bulk copy completing on `bar`; dst, src 16-byte aligned, bytes % 16 == 0
+__device__ inline void bulk_load(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+__device__ inline void consumer_sync(int nthreads) { asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory"); }
+
+constexpr long long kWaitCycles = 2000000000LL;  // about one second at GB300 clocks
+constexpr int kMaxStages = 8;
+
+struct Pipe {
+  uint64_t full[kMaxStages];
+  uint64_t empty[kMaxStages];
+  volatile int abort;
+};
+constexpr int kPipeBytes = 256;
+static_assert(sizeof(Pipe) <= kPipeBytes, "pipe header");
+
+// Waits for phase `parity` of `bar`; false when the CTA aborted or the wait ran out.
+__device__ inline bool wait_phase(uint64_t* bar, unsigned parity, Pipe* pp) {
+  if (mbar_test(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_test(bar, parity)) {
+    if (pp->abort) return false;
+    if (clock64() - t0 > kWaitCycles) return false;
+  }
+  return true;
+}
+__device__ inline void abort_cta(Pipe* pp, unsigned* err) {
+  if (!pp->abort) {
+    pp->abort = 1;
+    atomicOr(err, AMG_EBIT_TIMEOUT);
+  }
+}
+// Producer epilogue: every copy issued must have landed before the CTA may exit.
+__device__ inline void drain(Pipe* pp, long long issued, int ns) {
+  for (long long k = issued > ns ? issued - ns : 0; k < issued; ++k) {
+    uint64_t* bar = &pp->full[k % ns];
+    const unsigned par = (unsigned)((k / ns) & 1);
+    const long long t0 = clock64();
+    while (!mbar_test(bar, par) && clock64() - t0 < kWaitCycles) {
+    }
+  }
+}
+
+template <typename T> struct Acc;
+template <> struct Acc<double2> { using type = double2; };
+template <> struct Acc<float2> { using type = float2; };
+template <> struct Acc<__half2> { using type = float2; };
+
+// 16 bytes of shared memory as CPL complex values of the accumulation type.
+template <typename T> struct Vec16;
+template <> struct Vec16<double2> {
+  static constexpr int CPL = 1;
+  __device__ static void ld(const double2* p, double2 (&v)[1]) { v[0] = *p; }
+};
+template <> struct Vec16<float2> {
+  static constexpr int CPL = 2;
+  __device__ static void ld(const float2* p, float2 (&v)[2]) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = make_float2(t.x, t.y);
+    v[1] = make_float2(t.z, t.w);
+  }
+};
+template <> struct Vec16<__half2> {
+  static constexpr int CPL = 4;
+  __device__ static void ld(const __half2* p, float2 (&v)[4]) {
+    const uint4 t = *reinterpret_cast<const uint4*>(p);
+    const unsigned u[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      __half2 hv;
+      memcpy(&hv, &u[k], 4);
+      v[k] = __half22float2(hv);
+    }
+  }
+};
+
+template <typename T>
+__device__ inline T warp_csum(T v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+  }
+  return v;
+}
+
+template <typename AT>
+__device__ inline AT scaled(AT v, double f) {
+  using RT = decltype(v.x);
+  return AT{v.x * (RT)f, v.y * (RT)f};
+}
+
+// ------------------------------------------------------------------ coarse operator
+// Item = coarse site i; chunk d (0..8) = stencil block D_c[i][d], column-major, nc*nc entries.
+// Consumers stage X[d][b] = s_d * x(nbr(i, d))[b] (s_d the FP16 block scale; x optionally times
+// xscale[r], in which case the consumers of direction 0 also store the scaled own vector to
+// vout), then thread (rc, grp) accumulates rows rc*CPL.. over columns b = grp, grp + G, ...
+template <typename LT, int NR>
+struct ApplyArgs {
+  using AT = typename Acc<LT>::type;
+  const LT* D;
+  const float* dscale;
+  const int* nbr;
+  const AT* x;
+  AT* y;
+  AT* vout;
+  const double* xscale;
+  const int* skip;
+  unsigned* err;
+  Geom g;
+  int ld, r0, ns, G;
+};
+
+template <typename LT, int NR>
+__global__ void __launch_bounds__(288) apply_tma_kernel(const ApplyArgs<LT, NR> a) {
+  using AT = typename Acc<LT>::type;
+  constexpr int CPL = Vec16<LT>::CPL;
+  if (a.skip && *a.skip) return;
+  extern __shared__ __align__(128) unsigned char sm[];
+  Pipe* pp = reinterpret_cast<Pipe*>(sm);
+  const int nc = a.g.nc, K = 9 * nc, ns = a.ns;
+  const unsigned chunk = (unsigned)(nc * nc * sizeof(LT));
+  unsigned char* stages = sm + kPipeBytes;
+  AT* xs = reinterpret_cast<AT*>(stages + (size_t)ns * chunk);
+  AT* red = xs + (size_t)K * NR;
+  const int ncw = (blockDim.x - 32) >> 5;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < ns; ++s) {
+      mbar_init(&pp->full[s], 1);
+      mbar_init(&pp->empty[s], ncw);
+    }
+    pp->abort = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const long long Vc = a.g.Vc;
+  if (threadIdx.x < 32) {
+    if (threadIdx.x == 0) {
+      long long c = 0;
+      for (long long i = blockIdx.x; i < Vc && !pp->abort; i += gridDim.x) {
+        for (int d = 0; d < 9; ++d, ++c) {
+          const int s = (int)(c % ns);
+          const long long q = c / ns;
+          if (c >= ns && !wait_phase(&pp->empty[s], (unsigned)((q - 1) & 1), pp)) {
+            abort_cta(pp, a.err);
+            break;
+          }
+          mbar_expect_tx(&pp->full[s], chunk);
+          bulk_load(stages + (size_t)s * chunk, a.D + (i * 9 + d) * (long long)nc * nc, chunk, &pp->full[s]);
+        }
+      }
+      drain(pp, c, ns);
+    }
+    return;
+  }
+  const int t = threadIdx.x - 32, nct = blockDim.x - 32;
+  const int Gc = nc / CPL, rc = t % Gc, grp = t / Gc;
+  long long c = 0;
+  for (long long i = blockIdx.x; i < Vc; i += gridDim.x) {
+    for (int e = t; e < K * NR; e += nct) {
+      const int k = e / NR, r = e % NR, d = k / nc, b = k % nc;
+      const long long j = a.nbr[i * 9 + d];
+      AT v = a.x[(j * nc + b) * a.ld + a.r0 + r];
+      if (a.xscale) {
+        v = scaled(v, a.xscale[a.r0 + r]);
+        if (d == 0 && a.vout) a.vout[(i * nc + b) * a.ld + a.r0 + r] = v;
+      }
+      if (a.dscale) v = scaled(v, (double)a.dscale[i * 9 + d]);
+      xs[e] = v;
+    }
+    consumer_sync(nct);
+    AT acc[CPL][NR];
+#pragma unroll
+    for (int q = 0; q < CPL; ++q)
+#pragma unroll
+      for (int r = 0; r < NR; ++r) acc[q][r] = AT{0, 0};
+    for (int d = 0; d < 9; ++d, ++c) {
+      const int s = (int)(c % ns);
+      bool ok = !pp->abort;
+      if (ok && !wait_phase(&pp->full[s], (unsigned)((c / ns) & 1), pp)) {
+        abort_cta(pp, a.err);
+        ok = false;
+      }
+      if (ok && grp < a.G) {
+        const LT* blk = reinterpret_cast<const LT*>(stages + (size_t)s * chunk) + rc * CPL;
+        const AT* xd = xs + (size_t)d * nc * NR;
+#pragma unroll 4
+        for (int b = grp; b < nc; b += a.G) {
+          AT v[CPL];
+          Vec16<LT>::ld(blk + (size_t)b * nc, v);
+#pragma unroll
+          for (int q = 0; q < CPL; ++q)
+#pragma unroll
+            for (int r = 0; r < NR; ++r) cfma(acc[q][r], v[q], xd[b * NR + r]);
+        }
+      }
+      __syncwarp();
+      if ((t & 31) == 0) mbar_arrive(&pp->empty[s]);
+    }
+    if (grp < a.G)
+#pragma unroll
+      for (int q = 0; q < CPL; ++q)
+#pragma unroll
+        for (int r = 0; r < NR; ++r) red[((size_t)grp * nc + rc * CPL + q) * NR + r] = acc[q][r];
+    consumer_sync(nct);
+    for (int e = t; e < nc * NR; e += nct) {
+      AT sum = AT{0, 0};
+      for (int gg = 0; gg < a.G; ++gg) {
+        const AT v = red[(size_t)gg * nc * NR + e];
+        sum.x += v.x;
+        sum.y += v.y;
+      }
+      a.y[(i * nc + e / NR) * a.ld + a.r0 + e % NR] = sum;
+    }
+    consumer_sync(nct);
+  }
+}
+
+// ------------------------------------------------------------------ restriction
+// Item = block; chunk = one row (h, j) of R_i^h (6 Vb entries; a block's 2 ntv rows are one
+// contiguous run).  Consumer warp w owns stage w and the chunks c = w (mod #warps); y of the
+// block is staged as ys[h][n][r] by all consumers at the start of the block.
+template <typename ST, int NR>
+struct RestrictArgs {
+  using AT = typename Acc<ST>::type;
+  const ST* R;
+  const ST* y;
+  ST* yc;
+  unsigned* err;
+  Geom g;
+  int ld, r0;
+};
+
+template <typename ST, int NR>
+__global__ void __launch_bounds__(224) restrict_tma_kernel(const RestrictArgs<ST, NR> a) {
+  using AT = typename Acc<ST>::type;
+  constexpr int CPL = Vec16<ST>::CPL;
+  extern __shared__ __align__(128) unsigned char sm[];
+  Pipe* pp = reinterpret_cast<Pipe*>(sm);
+  const int ncw = (blockDim.x - 32) >> 5, ns = ncw;
+  const int nagg = a.g.nagg, ntv = a.g.ntv, Vb = (int)a.g.Vb, rows = 2 * ntv;
+  const unsigned chunk = (unsigned)(nagg * sizeof(ST));
+  unsigned char* stages = sm + kPipeBytes;
+  AT* ys = reinterpret_cast<AT*>(stages + (size_t)ns * chunk);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < ns; ++s) {
+      mbar_init(&pp->full[s], 1);
+      mbar_init(&pp->empty[s], 1);
+    }
+    pp->abort = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const long long nblk = a.g.Vc;
+  if (threadIdx.x < 32) {
+    if (threadIdx.x == 0) {
+      long long c = 0;
+      for (long long blk = blockIdx.x; blk < nblk && !pp->abort; blk += gridDim.x) {
+        for (int row = 0; row < rows; ++row, ++c) {
+          const int s = (int)(c % ns);
+          const long long q = c / ns;
+          if (c >= ns && !wait_phase(&pp->empty[s], (unsigned)((q - 1) & 1), pp)) {
+            abort_cta(pp, a.err);
+            break;
+          }
+          mbar_expect_tx(&pp->full[s], chunk);
+          bulk_load(stages + (size_t)s * chunk, a.R + (blk * rows + row) * (long long)nagg, chunk, &pp->full[s]);
+        }
+      }
+      drain(pp, c, ns);
+    }
+    return;
+  }
+  const int t = threadIdx.x - 32, nct = blockDim.x - 32, w = t >> 5, lane = t & 31;
+  long long c = 0;
+  for (long long blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+    consumer_sync(nct);
+    for (int e = t; e < Vb * 12 * NR; e += nct) {
+      const int sl = e / (12 * NR), rem = e % (12 * NR), dof = rem / NR, r = rem % NR;
+      const long long site = block_site(a.g, blk, sl);
+      const int hh = dof / 6, n = sl * 6 + dof % 6;
+      ys[((size_t)hh * nagg + n) * NR + r] = a.y[(site * 12 + dof) * a.ld + a.r0 + r];
+    }
+    consumer_sync(nct);
+    for (int row = 0; row < rows; ++row, ++c) {
+      if ((int)(c % ncw) != w) continue;
+      const int s = (int)(c % ns);
+      bool ok = !pp->abort;
+      if (ok && !wait_phase(&pp->full[s], (unsigned)((c / ns) & 1), pp)) {
+        abort_cta(pp, a.err);
+        ok = false;
+      }
+      AT acc[NR];
+#pragma unroll
+      for (int r = 0; r < NR; ++r) acc[r] = AT{0, 0};
+      if (ok) {
+        const int hh = row / ntv;
+        const ST* Rrow = reinterpret_cast<const ST*>(stages + (size_t)s * chunk);
+        const AT* yh = ys + (size_t)hh * nagg * NR;
+#pragma unroll 4
+        for (int qv = lane; qv < nagg / CPL; qv += 32) {
+          AT v[CPL];
+          Vec16<ST>::ld(Rrow + qv * CPL, v);
+#pragma unroll
+          for (int k = 0; k < CPL; ++k)
+#pragma unroll
+            for (int r = 0; r < NR; ++r) cfma(acc[r], v[k], yh[(qv * CPL + k) * NR + r]);
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&pp->empty[s]);
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        const AT sum = warp_csum(acc[r]);
+        if (lane == 0) a.yc[(blk * rows + row) * a.ld + a.r0 + r] = sum;
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ prolongation
+// Item = block; chunk = (h, n0): rows j = 0..ntv-1 of R_i^h restricted to n0 .. n0+nch-1, one bulk
+// copy per row into stage [j][nch].  Consumer warp w owns stage w; lane l computes
+// x[n] = sum_j conj(R[j][n]) x_c[h][j] for n = n0 + l, n0 + l + 32, ...
+template <typename ST, int NR>
+struct ProlongArgs {
+  using AT = typename Acc<ST>::type;
+  const ST* R;
+  const ST* xc;
+  ST* x;
+  unsigned* err;
+  Geom g;
+  int ld, r0, nch;
+};
+
+template <typename ST, int NR>
+__global__ void __launch_bounds__(160) prolong_tma_kernel(const ProlongArgs<ST, NR> a) {
+  using AT = typename Acc<ST>::type;
+  extern __shared__ __align__(128) unsigned char sm[];
+  Pipe* pp = reinterpret_cast<Pipe*>(sm);
+  const int ncw = (blockDim.x - 32) >> 5, ns = ncw;
+  const int nagg = a.g.nagg, ntv = a.g.ntv, nch = a.nch, cpa = nagg / nch;  // chunks per aggregate
+  const unsigned rowb = (unsigned)(nch * sizeof(ST)), chunk = rowb * ntv;
+  unsigned char* stages = sm + kPipeBytes;
+  AT* xs = reinterpret_cast<AT*>(stages + (size_t)ns * chunk);  // [2][ntv][NR]
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < ns; ++s) {
+      mbar_init(&pp->full[s], 1);
+      mbar_init(&pp->empty[s], 1);
+    }
+    pp->abort = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const long long nblk = a.g.Vc;
+  if (threadIdx.x < 32) {
+    long long c = 0;
+    for (long long blk = blockIdx.x; blk < nblk && !pp->abort; blk += gridDim.x) {
+      for (int k = 0; k < 2 * cpa; ++k, ++c) {
+        const int s = (int)(c % ns);
+        const long long q = c / ns;
+        const int hh = k / cpa, n0 = (k % cpa) * nch;
+        bool ok = true;
+        if (threadIdx.x == 0) {
+          if (c >= ns && !wait_phase(&pp->empty[s], (unsigned)((q - 1) & 1), pp)) {
+            abort_cta(pp, a.err);
+            ok = false;
+          } else {
+            mbar_expect_tx(&pp->full[s], chunk);
+          }
+        }
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) break;
+        // lanes issue the ntv row copies; all complete on the stage's full barrier
+        for (int j = threadIdx.x; j < ntv; j += 32)
+          bulk_load(stages + (size_t)s * chunk + (size_t)j * rowb,
+                    a.R + ((blk * 2 + hh) * ntv + j) * (long long)nagg + n0, rowb, &pp->full[s]);
+        __syncwarp();
+      }
+    }
+    if (threadIdx.x == 0) drain(pp, c, ns);
+    return;
+  }
+  const int t = threadIdx.x - 32, nct = blockDim.x - 32, w = t >> 5, lane = t & 31;
+  long long c = 0;
+  for (long long blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+    consumer_sync(nct);
+    for (int e = t; e < 2 * ntv * NR; e += nct) xs[e] = a.xc[(blk * 2 * ntv + e / NR) * a.ld + a.r0 + e % NR];
+    consumer_sync(nct);
+    for (int k = 0; k < 2 * cpa; ++k, ++c) {
+      if ((int)(c % ncw) != w) continue;
+      const int s = (int)(c % ns);
+      bool ok = !pp->abort;
+      if (ok && !wait_phase(&pp->full[s], (unsigned)((c / ns) & 1), pp)) {
+        abort_cta(pp, a.err);
+        ok = false;
+      }
+      const int hh = k / cpa, n0 = (k % cpa) * nch;
+      const ST* st = reinterpret_cast<const ST*>(stages + (size_t)s * chunk);
+      const AT* xh = xs + (size_t)hh * ntv * NR;
+      for (int nl = lane; nl < nch; nl += 32) {
+        AT acc[NR];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) acc[r] = AT{0, 0};
+        if (ok) {
+#pragma unroll 4
+          for (int j = 0; j < ntv; ++j) {
+            const ST v = st[(size_t)j * nch + nl];
+#pragma unroll
+            for (int r = 0; r < NR; ++r) cfmac(acc[r], v, xh[j * NR + r]);
+          }
+        }
+        const int n = n0 + nl, sl = n / 6, dof = hh * 6 + n % 6;
+        const long long site = block_site(a.g, blk, sl);
+#pragma unroll
+        for (int r = 0; r < NR; ++r) a.x[(site * 12 + dof) * a.ld + a.r0 + r] = acc[r];
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&pp->empty[s]);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ launch helpers
+int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 152;
+  }
+  return n;
+}
+
+template <typename K>
+amg_status grid_for(K kernel, int threads, size_t smem, long long items, int* grid) {
+  AMG_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  AMG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem));
+  if (per_sm < 1) return AMG_ERR_UNSUPPORTED;
+  const long long g = (long long)per_sm * sm_count();
+  *grid = (int)(items < g ? items : g);
+  return AMG_OK;
+}
+
+template <typename LT, int NR>
+amg_status launch_apply_tma(amg_coarse* h, const LT* D, const float* dscale, const void* x, void* y, int ld, int r0,
+                            cudaStream_t st, const int* skip, const double* xscale, void* vout) {
+  using AT = typename Acc<LT>::type;
+  constexpr int CPL = Vec16<LT>::CPL;
+  const int nc = h->g.nc;
+  if (nc % CPL) return AMG_ERR_UNSUPPORTED;
+  const int threads = 288;
+  const int Gc = nc / CPL;
+  int G = (threads - 32) / Gc;
+  if (G < 1) return AMG_ERR_UNSUPPORTED;
+  if (G > nc) G = nc;
+  const size_t chunk = (size_t)nc * nc * sizeof(LT);
+  int ns = (int)((64 * 1024) / chunk);
+  ns = ns < 2 ? 2 : (ns > 6 ? 6 : ns);
+  const size_t smem = kPipeBytes + ns * chunk + (size_t)9 * nc * NR * sizeof(AT) + (size_t)G * nc * NR * sizeof(AT);
+  if (smem > 227 * 1024) return AMG_ERR_UNSUPPORTED;
+  int grid = 0;
+  amg_status s = grid_for(apply_tma_kernel<LT, NR>, threads, smem, h->g.Vc, &grid);
+  if (s != AMG_OK) return s;
+  ApplyArgs<LT, NR> a{D, dscale, h->nbr, (const AT*)x, (AT*)y, (AT*)vout, xscale, skip, h->err, h->g, ld, r0, ns, G};
+  apply_tma_kernel<LT, NR><<<grid, threads, smem, st>>>(a);
+  AMG_LAUNCH_CHECK();
+  h->launches++;
+  return AMG_OK;
+}
+
+template <typename ST, int NR>
+amg_status launch_restrict_tma(amg_coarse* h, const ST* R, const ST* y, ST* yc, int ld, int r0, cudaStream_t st) {
+  using AT = typename Acc<ST>::type;
+  const size_t chunk = (size_t)h->g.nagg * sizeof(ST);
+  const size_t ybytes = (size_t)2 * h->g.nagg * NR * sizeof(AT);
+  if (chunk % 16 || kPipeBytes + chunk + ybytes > 220 * 1024) return AMG_ERR_UNSUPPORTED;
+  int ns = (int)((200 * 1024 - ybytes) / chunk);
+  ns = ns < 1 ? 1 : (ns > 6 ? 6 : ns);
+  const int threads = 32 + 32 * ns;  // one consumer warp per stage
+  const size_t smem = kPipeBytes + ns * chunk + ybytes;
+  int grid = 0;
+  amg_status s = grid_for(restrict_tma_kernel<ST, NR>, threads, smem, h->g.Vc, &grid);
+  if (s != AMG_OK) return s;
+  RestrictArgs<ST, NR> a{R, y, yc, h->err, h->g, ld, r0};
+  restrict_tma_kernel<ST, NR><<<grid, threads, smem, st>>>(a);
+  AMG_LAUNCH_CHECK();
+  h->launches++;
+  return AMG_OK;
+}
+
+// Largest nch dividing 6 Vb, a multiple of 6 (whole sites), with ntv * nch * sizeof(ST) <= 24 KB.
+template <typename ST>
+int prolong_chunk(const Geom& g) {
+  int best = 0;
+  for (int nch = 6; nch <= g.nagg; nch += 6)
+    if (g.nagg % nch == 0 && (size_t)g.ntv * nch * sizeof(ST) <= 24 * 1024 && (nch * sizeof(ST)) % 16 == 0)
+      best = nch;
+  return best;
+}
+
+template <typename ST, int NR>
+amg_status launch_prolong_tma(amg_coarse* h, const ST* R, const ST* xc, ST* x, int ld, int r0, cudaStream_t st) {
+  using AT = typename Acc<ST>::type;
+  const int threads = 32 + 4 * 32;
+  const int ns = 4;
+  const int nch = prolong_chunk<ST>(h->g);
+  if (nch == 0) return AMG_ERR_UNSUPPORTED;
+  const size_t chunk = (size_t)h->g.ntv * nch * sizeof(ST);
+  const size_t smem = kPipeBytes + ns * chunk + (size_t)2 * h->g.ntv * NR * sizeof(AT);
+  int grid = 0;
+  amg_status s = grid_for(prolong_tma_kernel<ST, NR>, threads, smem, h->g.Vc, &grid);
+  if (s != AMG_OK) return s;
+  ProlongArgs<ST, NR> a{R, xc, x, h->err, h->g, ld, r0, nch};
+  prolong_tma_kernel<ST, NR><<<grid, threads, smem, st>>>(a);
+  AMG_LAUNCH_CHECK();
+  h->launches++;
+  return AMG_OK;
+}
+
+template <typename F>
+amg_status for_rhs_chunks(int nrhs, F&& f) {
+  int r0 = 0;
+  while (r0 < nrhs) {
+    const int left = nrhs - r0;
+    const int nr = left >= 4 ? 4 : (left >= 2 ? 2 : 1);
+    amg_status st = f(r0, nr);
+    if (st != AMG_OK) return st;
+    r0 += nr;
+  }
+  return AMG_OK;
+}
+
+template <typename LT>
+amg_status apply_prec(amg_coarse* h, const LT* D, const float* dscale, const void* x, void* y, int nrhs,
+                      cudaStream_t s, const int* skip, const double* xscale, void* vout) {
+  return for_rhs_chunks(nrhs, [&](int r0, int nr) {
+    if (nr == 4) return launch_apply_tma<LT, 4>(h, D, dscale, x, y, nrhs, r0, s, skip, xscale, vout);
+    if (nr == 2) return launch_apply_tma<LT, 2>(h, D, dscale, x, y, nrhs, r0, s, skip, xscale, vout);
+    return launch_apply_tma<LT, 1>(h, D, dscale, x, y, nrhs, r0, s, skip, xscale, vout);
+  });
+}
+
+}  // namespace
+
+amg_status amg_internal_restrict(amg_coarse* h, const void* y, void* yc, int nrhs, cudaStream_t s) {
+  if (h->p.vec_prec == AMG_FP64) {
+    const double2* R = h->R64;
+    return for_rhs_chunks(nrhs, [&](int r0, int nr) {
+      if (nr == 4) return launch_restrict_tma<double2, 4>(h, R, (const double2*)y, (double2*)yc, nrhs, r0, s);
+      if (nr == 2) return launch_restrict_tma<double2, 2>(h, R, (const double2*)y, (double2*)yc, nrhs, r0, s);
+      return launch_restrict_tma<double2, 1>(h, R, (const double2*)y, (double2*)yc, nrhs, r0, s);
+    });
+  }
+  if (h->p.vec_prec == AMG_FP32 && h->p.r_prec == AMG_FP32) {
+    const float2* R = (const float2*)h->Rq;
+    return for_rhs_chunks(nrhs, [&](int r0, int nr) {
+      if (nr == 4) return launch_restrict_tma<float2, 4>(h, R, (const float2*)y, (float2*)yc, nrhs, r0, s);
+      if (nr == 2) return launch_restrict_tma<float2, 2>(h, R, (const float2*)y, (float2*)yc, nrhs, r0, s);
+      return launch_restrict_tma<float2, 1>(h, R, (const float2*)y, (float2*)yc, nrhs, r0, s);
+    });
+  }
+  return AMG_ERR_UNSUPPORTED;
+}
+
+amg_status amg_internal_prolong(amg_coarse* h, const void* xc, void* x, int nrhs, cudaStream_t s) {
+  if (h->p.vec_prec == AMG_FP64) {
+    const double2* R = h->R64;
+    return for_rhs_chunks(nrhs, [&](int r0, int nr) {
+      if (nr == 4) return launch_prolong_tma<double2, 4>(h, R, (const double2*)xc, (double2*)x, nrhs, r0, s);
+      if (nr == 2) return launch_prolong_tma<double2, 2>(h, R, (const double2*)xc, (double2*)x, nrhs, r0, s);
+      return launch_prolong_tma<double2, 1>(h, R, (const double2*)xc, (double2*)x, nrhs, r0, s);
+    });
+  }
+  if (h->p.vec_prec == AMG_FP32 && h->p.r_prec == AMG_FP32) {
+    const float2* R = (const float2*)h->Rq;
+    return for_rhs_chunks(nrhs, [&](int r0, int nr) {
+      if (nr == 4) return launch_prolong_tma<float2, 4>(h, R, (const float2*)xc, (float2*)x, nrhs, r0, s);
+      if (nr == 2) return launch_prolong_tma<float2, 2>(h, R, (const float2*)xc, (float2*)x, nrhs, r0, s);
+      return launch_prolong_tma<float2, 1>(h, R, (const float2*)xc, (float2*)x, nrhs, r0, s);
+    });
+  }
+  return AMG_ERR_UNSUPPORTED;
+}
+
+amg_status amg_internal_apply(amg_coarse* h, const void* xc, void* yc, int nrhs, cudaStream_t s) {
+  return amg_internal_apply_ex(h, xc, yc, nrhs, s, nullptr, nullptr, nullptr);
+}
+
+amg_status amg_internal_apply_ex(amg_coarse* h, const void* xc, void* yc, int nrhs, cudaStream_t s,
+                                 const int* skip, const double* xscale, void* vout) {
+  switch (h->p.link_prec) {
+    case AMG_FP64:
+      if (h->p.vec_prec != AMG_FP64) return AMG_ERR_UNSUPPORTED;
+      return apply_prec<double2>(h, (const double2*)h->Dq, nullptr, xc, yc, nrhs, s, skip, xscale, vout);
+    case AMG_FP32:
+      if (h->p.vec_prec == AMG_FP64) return AMG_ERR_UNSUPPORTED;
+      return apply_prec<float2>(h, (const float2*)h->Dq, nullptr, xc, yc, nrhs, s, skip, xscale, vout);
+    case AMG_FP16_SCALED:
+      if (h->p.vec_prec == AMG_FP64) return AMG_ERR_UNSUPPORTED;
+      return apply_prec<__half2>(h, (const __half2*)h->Dq, h->Dscale, xc, yc, nrhs, s, skip, xscale, vout);
+    default:
+      return AMG_ERR_UNSUPPORTED;
+  }
+}
