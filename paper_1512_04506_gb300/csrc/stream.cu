@@ -1,8 +1,11 @@
-// Persistent, TMA-fed streaming kernels for the three HBM-bound steps of the coarse-grid
-// correction (Alg. 2): restriction y_c = R y (Eq. R, Alg. 6), coarse operator y_c = D_c x_c and
-// prolongation x = P x_c with P = R^dagger.
+// Streaming kernels for the three HBM-bound steps of the coarse-grid correction (Alg. 2):
+// restriction y_c = R y (Eq. R, Alg. 6), coarse operator y_c = D_c x_c and prolongation
+// x = P x_c with P = R^dagger.
 //
-// Each CTA is persistent over work items (blocks for R / P, coarse sites for D_c).  Warp 0 is
+// The coarse operator and the prolongation are persistent and TMA-fed; the restriction is a
+// plain one-CTA-per-block kernel (measured faster for its access pattern, see restrict_kernel).
+// In the TMA-fed kernels each CTA is persistent over work items (blocks for P, coarse sites for
+// D_c), taken in strided order so that the CTAs in flight read neighbouring items.  Warp 0 is
 // the producer: one lane streams the item's matrix into a ring of shared-memory stages with
 // cp.async.bulk, each stage guarded by a "full" mbarrier (transaction bytes) and an "empty"
 // mbarrier (consumer release).  The other warps consume the stages from shared memory.  The
@@ -114,6 +117,35 @@ template <> struct Vec16<__half2> {
       memcpy(&hv, &u[k], 4);
       v[k] = __half22float2(hv);
     }
+  }
+};
+
+// n consecutive complex values from 16-byte aligned shared memory, with 16-byte loads.
+template <typename AT, int n>
+__device__ inline void load_run(const AT* p, AT (&v)[n]) {
+  if constexpr (sizeof(AT) == 8 && n % 2 == 0) {
+#pragma unroll
+    for (int u = 0; u < n / 2; ++u) {
+      const float4 t = reinterpret_cast<const float4*>(p)[u];
+      v[2 * u] = AT{t.x, t.y};
+      v[2 * u + 1] = AT{t.z, t.w};
+    }
+  } else {
+#pragma unroll
+    for (int u = 0; u < n; ++u) v[u] = p[u];
+  }
+}
+
+// 16 bytes of global memory (read once, not kept in L1) as CPL complex values.
+template <typename T> struct Ld16;
+template <> struct Ld16<double2> {
+  __device__ static void ld(const double2* p, double2 (&v)[1]) { v[0] = __ldcs(p); }
+};
+template <> struct Ld16<float2> {
+  __device__ static void ld(const float2* p, float2 (&v)[2]) {
+    const float4 t = __ldcs(reinterpret_cast<const float4*>(p));
+    v[0] = make_float2(t.x, t.y);
+    v[1] = make_float2(t.z, t.w);
   }
 };
 
@@ -260,103 +292,48 @@ __global__ void __launch_bounds__(288) apply_tma_kernel(const ApplyArgs<LT, NR> 
 }
 
 // ------------------------------------------------------------------ restriction
-// Item = block; chunk = one row (h, j) of R_i^h (6 Vb entries; a block's 2 ntv rows are one
-// contiguous run).  Consumer warp w owns stage w and the chunks c = w (mod #warps); y of the
-// block is staged as ys[h][n][r] by all consumers at the start of the block.
+// One CTA per block, launched in block order, so the CTAs resident at any time read neighbouring
+// blocks.  y on the block is staged as ys[h][n][r]; warp w computes rows (h, j) of R_i^h y_i^h,
+// the lanes striding over n with 16-byte streaming loads of the row and 16-byte shared loads of
+// y, then a shuffle sum.  Many small CTAs (8 per SM) keep enough loads in flight.
 template <typename ST, int NR>
-struct RestrictArgs {
-  using AT = typename Acc<ST>::type;
-  const ST* R;
-  const ST* y;
-  ST* yc;
-  unsigned* err;
-  Geom g;
-  int ld, r0;
-};
-
-template <typename ST, int NR>
-__global__ void __launch_bounds__(224) restrict_tma_kernel(const RestrictArgs<ST, NR> a) {
+__global__ void __launch_bounds__(256) restrict_kernel(const ST* __restrict__ R, const ST* __restrict__ y,
+                                                       ST* __restrict__ yc, Geom g, int ld, int r0) {
   using AT = typename Acc<ST>::type;
   constexpr int CPL = Vec16<ST>::CPL;
-  extern __shared__ __align__(128) unsigned char sm[];
-  Pipe* pp = reinterpret_cast<Pipe*>(sm);
-  const int ncw = (blockDim.x - 32) >> 5, ns = ncw;
-  const int nagg = a.g.nagg, ntv = a.g.ntv, Vb = (int)a.g.Vb, rows = 2 * ntv;
-  const unsigned chunk = (unsigned)(nagg * sizeof(ST));
-  unsigned char* stages = sm + kPipeBytes;
-  AT* ys = reinterpret_cast<AT*>(stages + (size_t)ns * chunk);
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < ns; ++s) {
-      mbar_init(&pp->full[s], 1);
-      mbar_init(&pp->empty[s], 1);
-    }
-    pp->abort = 0;
-    fence_mbar_init();
+  extern __shared__ __align__(16) unsigned char smraw[];
+  AT* ys = reinterpret_cast<AT*>(smraw);
+  const long long blk = blockIdx.x;
+  const int nagg = g.nagg, ntv = g.ntv, Vb = (int)g.Vb;
+  for (int e = threadIdx.x; e < Vb * 12 * NR; e += blockDim.x) {
+    const int sl = e / (12 * NR), rem = e % (12 * NR), dof = rem / NR, r = rem % NR;
+    const long long site = block_site(g, blk, sl);
+    const int hh = dof / 6, n = sl * 6 + dof % 6;
+    ys[((size_t)hh * nagg + n) * NR + r] = y[(site * 12 + dof) * ld + r0 + r];
   }
   __syncthreads();
-  const long long nblk = a.g.Vc;
-  if (threadIdx.x < 32) {
-    if (threadIdx.x == 0) {
-      long long c = 0;
-      for (long long blk = blockIdx.x; blk < nblk && !pp->abort; blk += gridDim.x) {
-        for (int row = 0; row < rows; ++row, ++c) {
-          const int s = (int)(c % ns);
-          const long long q = c / ns;
-          if (c >= ns && !wait_phase(&pp->empty[s], (unsigned)((q - 1) & 1), pp)) {
-            abort_cta(pp, a.err);
-            break;
-          }
-          mbar_expect_tx(&pp->full[s], chunk);
-          bulk_load(stages + (size_t)s * chunk, a.R + (blk * rows + row) * (long long)nagg, chunk, &pp->full[s]);
-        }
-      }
-      drain(pp, c, ns);
-    }
-    return;
-  }
-  const int t = threadIdx.x - 32, nct = blockDim.x - 32, w = t >> 5, lane = t & 31;
-  long long c = 0;
-  for (long long blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
-    consumer_sync(nct);
-    for (int e = t; e < Vb * 12 * NR; e += nct) {
-      const int sl = e / (12 * NR), rem = e % (12 * NR), dof = rem / NR, r = rem % NR;
-      const long long site = block_site(a.g, blk, sl);
-      const int hh = dof / 6, n = sl * 6 + dof % 6;
-      ys[((size_t)hh * nagg + n) * NR + r] = a.y[(site * 12 + dof) * a.ld + a.r0 + r];
-    }
-    consumer_sync(nct);
-    for (int row = 0; row < rows; ++row, ++c) {
-      if ((int)(c % ncw) != w) continue;
-      const int s = (int)(c % ns);
-      bool ok = !pp->abort;
-      if (ok && !wait_phase(&pp->full[s], (unsigned)((c / ns) & 1), pp)) {
-        abort_cta(pp, a.err);
-        ok = false;
-      }
-      AT acc[NR];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int row = warp; row < 2 * ntv; row += nw) {
+    const int hh = row / ntv;
+    const ST* Rrow = R + (blk * 2 * ntv + row) * (long long)nagg;
+    const AT* yh = ys + (size_t)hh * nagg * NR;
+    AT acc[NR];
 #pragma unroll
-      for (int r = 0; r < NR; ++r) acc[r] = AT{0, 0};
-      if (ok) {
-        const int hh = row / ntv;
-        const ST* Rrow = reinterpret_cast<const ST*>(stages + (size_t)s * chunk);
-        const AT* yh = ys + (size_t)hh * nagg * NR;
+    for (int r = 0; r < NR; ++r) acc[r] = AT{0, 0};
 #pragma unroll 4
-        for (int qv = lane; qv < nagg / CPL; qv += 32) {
-          AT v[CPL];
-          Vec16<ST>::ld(Rrow + qv * CPL, v);
+    for (int q = lane; q < nagg / CPL; q += 32) {
+      AT v[CPL], yv[CPL * NR];
+      Ld16<ST>::ld(Rrow + q * CPL, v);
+      load_run<AT, CPL * NR>(yh + (size_t)q * CPL * NR, yv);
 #pragma unroll
-          for (int k = 0; k < CPL; ++k)
+      for (int k = 0; k < CPL; ++k)
 #pragma unroll
-            for (int r = 0; r < NR; ++r) cfma(acc[r], v[k], yh[(qv * CPL + k) * NR + r]);
-        }
-      }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&pp->empty[s]);
+        for (int r = 0; r < NR; ++r) cfma(acc[r], v[k], yv[k * NR + r]);
+    }
 #pragma unroll
-      for (int r = 0; r < NR; ++r) {
-        const AT sum = warp_csum(acc[r]);
-        if (lane == 0) a.yc[(blk * rows + row) * a.ld + a.r0 + r] = sum;
-      }
+    for (int r = 0; r < NR; ++r) {
+      const AT sum = warp_csum(acc[r]);
+      if (lane == 0) yc[(blk * 2 * ntv + row) * ld + r0 + r] = sum;
     }
   }
 }
@@ -515,20 +492,13 @@ amg_status launch_apply_tma(amg_coarse* h, const LT* D, const float* dscale, con
 }
 
 template <typename ST, int NR>
-amg_status launch_restrict_tma(amg_coarse* h, const ST* R, const ST* y, ST* yc, int ld, int r0, cudaStream_t st) {
+amg_status launch_restrict(amg_coarse* h, const ST* R, const ST* y, ST* yc, int ld, int r0, cudaStream_t st) {
   using AT = typename Acc<ST>::type;
-  const size_t chunk = (size_t)h->g.nagg * sizeof(ST);
-  const size_t ybytes = (size_t)2 * h->g.nagg * NR * sizeof(AT);
-  if (chunk % 16 || kPipeBytes + chunk + ybytes > 220 * 1024) return AMG_ERR_UNSUPPORTED;
-  int ns = (int)((200 * 1024 - ybytes) / chunk);
-  ns = ns < 1 ? 1 : (ns > 6 ? 6 : ns);
-  const int threads = 32 + 32 * ns;  // one consumer warp per stage
-  const size_t smem = kPipeBytes + ns * chunk + ybytes;
-  int grid = 0;
-  amg_status s = grid_for(restrict_tma_kernel<ST, NR>, threads, smem, h->g.Vc, &grid);
-  if (s != AMG_OK) return s;
-  RestrictArgs<ST, NR> a{R, y, yc, h->err, h->g, ld, r0};
-  restrict_tma_kernel<ST, NR><<<grid, threads, smem, st>>>(a);
+  const size_t smem = (size_t)2 * h->g.nagg * NR * sizeof(AT);
+  if (smem > 227 * 1024) return AMG_ERR_UNSUPPORTED;
+  if (smem > 48 * 1024)
+    AMG_CUDA_TRY(cudaFuncSetAttribute(restrict_kernel<ST, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  restrict_kernel<ST, NR><<<(unsigned)h->g.Vc, 256, smem, st>>>(R, y, yc, h->g, ld, r0);
   AMG_LAUNCH_CHECK();
   h->launches++;
   return AMG_OK;
@@ -592,17 +562,17 @@ amg_status amg_internal_restrict(amg_coarse* h, const void* y, void* yc, int nrh
   if (h->p.vec_prec == AMG_FP64) {
     const double2* R = h->R64;
     return for_rhs_chunks(nrhs, [&](int r0, int nr) {
-      if (nr == 4) return launch_restrict_tma<double2, 4>(h, R, (const double2*)y, (double2*)yc, nrhs, r0, s);
-      if (nr == 2) return launch_restrict_tma<double2, 2>(h, R, (const double2*)y, (double2*)yc, nrhs, r0, s);
-      return launch_restrict_tma<double2, 1>(h, R, (const double2*)y, (double2*)yc, nrhs, r0, s);
+      if (nr == 4) return launch_restrict<double2, 4>(h, R, (const double2*)y, (double2*)yc, nrhs, r0, s);
+      if (nr == 2) return launch_restrict<double2, 2>(h, R, (const double2*)y, (double2*)yc, nrhs, r0, s);
+      return launch_restrict<double2, 1>(h, R, (const double2*)y, (double2*)yc, nrhs, r0, s);
     });
   }
   if (h->p.vec_prec == AMG_FP32 && h->p.r_prec == AMG_FP32) {
     const float2* R = (const float2*)h->Rq;
     return for_rhs_chunks(nrhs, [&](int r0, int nr) {
-      if (nr == 4) return launch_restrict_tma<float2, 4>(h, R, (const float2*)y, (float2*)yc, nrhs, r0, s);
-      if (nr == 2) return launch_restrict_tma<float2, 2>(h, R, (const float2*)y, (float2*)yc, nrhs, r0, s);
-      return launch_restrict_tma<float2, 1>(h, R, (const float2*)y, (float2*)yc, nrhs, r0, s);
+      if (nr == 4) return launch_restrict<float2, 4>(h, R, (const float2*)y, (float2*)yc, nrhs, r0, s);
+      if (nr == 2) return launch_restrict<float2, 2>(h, R, (const float2*)y, (float2*)yc, nrhs, r0, s);
+      return launch_restrict<float2, 1>(h, R, (const float2*)y, (float2*)yc, nrhs, r0, s);
     });
   }
   return AMG_ERR_UNSUPPORTED;
