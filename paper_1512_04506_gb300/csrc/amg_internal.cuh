@@ -173,3 +173,8 @@ void amg_internal_free_tc(amg_coarse* h);
 // is xc * xscale[r] and that scaled input is also stored to vout (both may be null).
 amg_status amg_internal_apply_ex(amg_coarse* h, const void* xc, void* yc, int nrhs, cudaStream_t s,
                                  const int* skip, const double* xscale, void* vout);
+// Tensor-core (BF16) forms for nrhs = 4, 8, 12, 16.
+amg_status amg_internal_apply_tc(amg_coarse* h, const void* xc, void* yc, int nrhs, cudaStream_t s,
+                                 const int* skip, const double* xscale, void* vout);
+amg_status amg_internal_restrict_tc(amg_coarse* h, const void* y, void* yc, int nrhs, cudaStream_t s);
+amg_status amg_internal_prolong_tc(amg_coarse* h, const void* xc, void* x, int nrhs, cudaStream_t s);

@@ -14,78 +14,10 @@
 // cycles); a wait that runs out sets AMG_EBIT_TIMEOUT, makes the CTA skip the rest of its work,
 // and the producer still waits (bounded) for the copies it has issued before the CTA exits.
 #include "amg_internal.cuh"
+#include "pipe.cuh"
 
 namespace {
-
-// ------------------------------------------------------------------ PTX helpers
-__device__ inline unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ inline void mbar_init(uint64_t* bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-__device__ inline void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-__device__ inline void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-               : "memory");
-}
-__device__ inline void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-__device__ inline bool mbar_test(uint64_t* bar, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// global -> shared bulk copy completing on `bar`; dst, src 16-byte aligned, bytes % 16 == 0
-__device__ inline void bulk_load(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_addr(dst)),
-               "l"(src), "r"(bytes), "r"(smem_addr(bar))
-               : "memory");
-}
-__device__ inline void consumer_sync(int nthreads) { asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory"); }
-
-constexpr long long kWaitCycles = 2000000000LL;  // about one second at GB300 clocks
-constexpr int kMaxStages = 8;
-
-struct Pipe {
-  uint64_t full[kMaxStages];
-  uint64_t empty[kMaxStages];
-  volatile int abort;
-};
-constexpr int kPipeBytes = 256;
-static_assert(sizeof(Pipe) <= kPipeBytes, "pipe header");
-
-// Waits for phase `parity` of `bar`; false when the CTA aborted or the wait ran out.
-__device__ inline bool wait_phase(uint64_t* bar, unsigned parity, Pipe* pp) {
-  if (mbar_test(bar, parity)) return true;
-  const long long t0 = clock64();
-  while (!mbar_test(bar, parity)) {
-    if (pp->abort) return false;
-    if (clock64() - t0 > kWaitCycles) return false;
-  }
-  return true;
-}
-__device__ inline void abort_cta(Pipe* pp, unsigned* err) {
-  if (!pp->abort) {
-    pp->abort = 1;
-    atomicOr(err, AMG_EBIT_TIMEOUT);
-  }
-}
-// Producer epilogue: every copy issued must have landed before the CTA may exit.
-__device__ inline void drain(Pipe* pp, long long issued, int ns) {
-  for (long long k = issued > ns ? issued - ns : 0; k < issued; ++k) {
-    uint64_t* bar = &pp->full[k % ns];
-    const unsigned par = (unsigned)((k / ns) & 1);
-    const long long t0 = clock64();
-    while (!mbar_test(bar, par) && clock64() - t0 < kWaitCycles) {
-    }
-  }
-}
+using namespace amgpipe;
 
 template <typename T> struct Acc;
 template <> struct Acc<double2> { using type = double2; };
@@ -559,6 +491,7 @@ amg_status apply_prec(amg_coarse* h, const LT* D, const float* dscale, const voi
 }  // namespace
 
 amg_status amg_internal_restrict(amg_coarse* h, const void* y, void* yc, int nrhs, cudaStream_t s) {
+  if (h->p.vec_prec == AMG_BF16) return amg_internal_restrict_tc(h, y, yc, nrhs, s);
   if (h->p.vec_prec == AMG_FP64) {
     const double2* R = h->R64;
     return for_rhs_chunks(nrhs, [&](int r0, int nr) {
@@ -579,6 +512,7 @@ amg_status amg_internal_restrict(amg_coarse* h, const void* y, void* yc, int nrh
 }
 
 amg_status amg_internal_prolong(amg_coarse* h, const void* xc, void* x, int nrhs, cudaStream_t s) {
+  if (h->p.vec_prec == AMG_BF16) return amg_internal_prolong_tc(h, xc, x, nrhs, s);
   if (h->p.vec_prec == AMG_FP64) {
     const double2* R = h->R64;
     return for_rhs_chunks(nrhs, [&](int r0, int nr) {
@@ -614,6 +548,8 @@ amg_status amg_internal_apply_ex(amg_coarse* h, const void* xc, void* yc, int nr
     case AMG_FP16_SCALED:
       if (h->p.vec_prec == AMG_FP64) return AMG_ERR_UNSUPPORTED;
       return apply_prec<__half2>(h, (const __half2*)h->Dq, h->Dscale, xc, yc, nrhs, s, skip, xscale, vout);
+    case AMG_BF16:
+      return amg_internal_apply_tc(h, xc, yc, nrhs, s, skip, xscale, vout);
     default:
       return AMG_ERR_UNSUPPORTED;
   }
