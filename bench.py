@@ -274,9 +274,82 @@ def run_gpu(args):
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(applies)
+    if not args.no_speedup:
+        result["batched_mixed_vs_plain"] = speedup_mixed()
     if dist:
         dist.destroy_process_group()
     return result, rank
+
+
+def speedup_mixed(seed=20151204 + 3):
+    """Batched mixed precision against plain FP32, per right-hand side, at coarse accuracy 1e-4.
+
+    Workload: 32^3 x 64 lattice, 4^4 blocks (8^3 x 16 coarse), Ntv = 24, 16 right-hand sides.
+    Plain: FP32 D_c, single-RHS FGMRES(30) to relative residual 1e-4, one right-hand side after
+    the other.  Batched mixed: all 16 right-hand sides at once, FGMRES(30) to 0.05 on the BF16
+    (tensor-core) or FP16 D_c, refined with the FP32 D_c until the true residual is <= 1e-4.
+    """
+    import torch
+    import paper_1512_04506_gb300 as amg
+    from synth import device as sd
+    L3, ntv, nrhs = (32, 32, 32, 64), 24, 16
+    st = torch.cuda.current_stream()
+    U = sd.links(seed, EPS, L3)
+    tv = sd.test_vectors(seed, ntv, L3)
+    hs = {}
+    for name, link in (("fp32", amg.AMG_FP32), ("fp16", amg.AMG_FP16_SCALED), ("bf16", amg.AMG_BF16)):
+        p = amg.make_params(L3, B, ntv, nrhs, M0, CSW, link, amg.AMG_FP32, amg.AMG_FP32)
+        hs[name], _ = amg.amg_setup_coarse(p, U, tv, st)
+    del U, tv
+    Vc = int(np.prod(L3)) // int(np.prod(B))
+    b = sd.coarse_vector(seed, ntv, nrhs, Vc, torch.complex64)
+    cols = [b[..., r:r + 1].contiguous() for r in range(nrhs)]
+    x1 = torch.empty_like(cols[0])
+    x = torch.empty_like(b)
+    res = {}
+    try:
+        def plain():
+            out = []
+            for r in range(nrhs):
+                out.append(amg.amg_coarse_solve(hs["fp32"], cols[r], x1, 1, 1e-4, 30, 2000, st, info=True)[0])
+            return out
+        def mixed(name):
+            return amg.amg_coarse_solve_mixed(hs["fp32"], hs[name], b, x, nrhs, 1e-4, 0.05, 30, 400, 30, st)
+        for fn in (plain, lambda: mixed("bf16"), lambda: mixed("fp16")):
+            fn()  # warm-up
+        def timed(fn, reps=3):
+            best_t, best_info = None, None
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(st)
+                info = fn()
+                e1.record(st)
+                torch.cuda.synchronize()
+                el = e0.elapsed_time(e1) / 1000.0
+                if best_t is None or el < best_t:
+                    best_t, best_info = el, info
+            return best_t, best_info
+        tp, ip = timed(plain)
+        tb, ib = timed(lambda: mixed("bf16"))
+        th, ih = timed(lambda: mixed("fp16"))
+        res = {
+            "workload": "32^3x64, 4^4 blocks, Ntv=24, 16 RHS; coarse relative residual <= 1e-4",
+            "plain_fp32_ms_per_rhs": round(1000 * tp / nrhs, 3),
+            "plain_applies_per_rhs": float(np.mean([a for a, _ in ip])),
+            "mixed_bf16_tc_ms_per_rhs": round(1000 * tb / nrhs, 3),
+            "mixed_bf16_inner_applies": float(np.mean([a for a, _, _ in ib])),
+            "mixed_bf16_max_true_residual": max(r for _, _, r in ib),
+            "mixed_fp16_ms_per_rhs": round(1000 * th / nrhs, 3),
+            "mixed_fp16_max_true_residual": max(r for _, _, r in ih),
+            "speedup_bf16": round(tp / tb, 2),
+            "speedup_fp16": round(tp / th, 2),
+            "timing": "CUDA events around the whole solve (host synchronisations included), best of 3",
+        }
+    finally:
+        for h in hs.values():
+            amg.amg_destroy(h)
+    return res
 
 
 def cpu_sample(applies, target_s=15.0):
@@ -373,6 +446,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-speedup", action="store_true",
+                    help="skip the batched-mixed vs plain FP32 coarse-solve comparison")
     ap.add_argument("--lattice", default=None,
                     help="Lx,Ly,Lz,Lt override of the 32^4 lattice (smaller cases for ncu captures)")
     args = ap.parse_args()

@@ -137,6 +137,20 @@ amg_status amg_coarse_solve_noalloc(amg_handle h, const void *d_b, void *d_x, in
 size_t amg_noalloc_scratch_bytes(void);
 
 /*
+ * amg_coarse_solve_mixed -- the coarse solve to a tight tolerance with a cheap operator, by
+ * iterative refinement [Alg. 2's low-precision coarse solve; Sec. 3, half-precision D_c]: each
+ * pass solves D_c e = r with FGMRES on h_inner's D_c (FP16 / BF16 storage) to inner_tol, adds e
+ * to x_c and recomputes the true residual r = b - D_c x_c with h_outer's D_c (FP32), until
+ * |r| <= tol |b| per right-hand side or max_outer passes.  h_outer and h_inner must come from the
+ * same lattice, blocks, ntv, links and test vectors; both with FP32 coarse vectors.  info (host,
+ * may be NULL) receives per RHS {inner D_c applications, outer passes, final true relative
+ * residual} at info[3 r .. 3 r + 2].  Synchronises the stream once per pass.
+ */
+amg_status amg_coarse_solve_mixed(amg_handle h_outer, amg_handle h_inner, const void *d_b, void *d_x,
+                                  int nrhs, double tol, double inner_tol, int restart,
+                                  int max_inner_applies, int max_outer, void *stream, double *info);
+
+/*
  * amg_cgc -- one coarse-grid correction, Alg. 2: x = P FGMRES(D_c, R y).
  * Same arguments as amg_coarse_solve for the solve.
  */

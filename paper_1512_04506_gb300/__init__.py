@@ -63,6 +63,7 @@ _proto = {
     "amg_prolong": [_vp, _vp, _vp, _i, _vp],
     "amg_coarse_solve": [_vp, _vp, _vp, _i, _d, _i, _i, _vp, ctypes.POINTER(_d)],
     "amg_coarse_solve_noalloc": [_vp, _vp, _vp, _i, _d, _i, _i, _vp, ctypes.POINTER(_d)],
+    "amg_coarse_solve_mixed": [_vp, _vp, _vp, _vp, _i, _d, _d, _i, _i, _i, _vp, ctypes.POINTER(_d)],
     "amg_cgc": [_vp, _vp, _vp, _i, _d, _i, _i, _vp, ctypes.POINTER(_d)],
     "amg_batch_cgc": [ctypes.POINTER(_vp), _i, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                       ctypes.POINTER(_i), _vp],
@@ -188,6 +189,18 @@ def amg_coarse_solve_noalloc(h, b, x, nrhs=1, tol=0.05, restart=30, max_applies=
     _check(lib.amg_coarse_solve_noalloc(h, ptr(b), ptr(x), nrhs, tol, restart, max_applies,
                                         stream_ptr(stream), buf), "amg_coarse_solve_noalloc")
     return _info_out(buf, nrhs)
+
+
+def amg_coarse_solve_mixed(h_outer, h_inner, b, x, nrhs=1, tol=1e-4, inner_tol=0.05, restart=30,
+                           max_inner_applies=200, max_outer=20, stream=None, info=True):
+    """Returns [(inner applications, outer passes, true relative residual)] per right-hand side."""
+    buf = (ctypes.c_double * (3 * nrhs))() if info else None
+    _check(lib.amg_coarse_solve_mixed(h_outer, h_inner, ptr(b), ptr(x), nrhs, tol, inner_tol, restart,
+                                      max_inner_applies, max_outer, stream_ptr(stream), buf),
+           "amg_coarse_solve_mixed")
+    if buf is None:
+        return None
+    return [(int(buf[3 * r]), int(buf[3 * r + 1]), float(buf[3 * r + 2])) for r in range(nrhs)]
 
 
 def amg_cgc(h, y, x, nrhs=1, tol=0.05, restart=30, max_applies=200, stream=None, info=True):

@@ -1,0 +1,138 @@
+// Mixed-precision coarse solve: iterative refinement around the low-precision FGMRES of Alg. 2.
+//
+// The paper keeps D_c in half precision inside a coarse solve that only needs a residual of about
+// 0.05 (Sec. 3).  To reach a tighter coarse tolerance with the cheap operator, each pass solves the
+// correction equation D_c e = r with FGMRES on the FP16 / BF16 operator (handle h_inner) to
+// inner_tol, adds e to x, and recomputes the true residual r = b - D_c x with the accurate FP32
+// operator (handle h_outer); right-hand sides that have reached tol drop out (their r is zeroed,
+// so the inner solver leaves them alone).
+#include "amg_internal.cuh"
+
+#include <cmath>
+#include <vector>
+
+namespace {
+
+// per right-hand side |v_r|^2 of a coarse FP32 vector with nrhs columns: one CTA per column
+__global__ void __launch_bounds__(1024) k_colnorm2(const float2* __restrict__ v, long long rows, int nrhs,
+                                                   double* __restrict__ out) {
+  __shared__ double red[32];
+  const int r = blockIdx.x;
+  double s = 0;
+  for (long long e = threadIdx.x; e < rows; e += blockDim.x) {
+    const float2 a = v[e * nrhs + r];
+    s += (double)a.x * a.x + (double)a.y * a.y;
+  }
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    out[r] = t;
+  }
+}
+
+// x += e; r = b - w (w = D_c x from the accurate operator), columns with keep[r] == 0 zeroed in r
+__global__ void k_axpy(float2* __restrict__ x, const float2* __restrict__ e, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float2 a = x[i], b = e[i];
+    x[i] = make_float2(a.x + b.x, a.y + b.y);
+  }
+}
+__global__ void k_resid(float2* __restrict__ r, const float2* __restrict__ b, const float2* __restrict__ w,
+                        const int* __restrict__ keep, long long n, int nrhs) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float2 u = b[i], v = w[i];
+    r[i] = keep[i % nrhs] ? make_float2(u.x - v.x, u.y - v.y) : make_float2(0.f, 0.f);
+  }
+}
+
+}  // namespace
+
+extern "C" amg_status amg_coarse_solve_mixed(amg_handle ho, amg_handle hi, const void* d_b, void* d_x, int nrhs,
+                                             double tol, double inner_tol, int restart, int max_inner_applies,
+                                             int max_outer, void* stream, double* info) {
+  if (!ho || !hi || !d_b || !d_x || d_b == d_x || !aligned16(d_b) || !aligned16(d_x)) return AMG_ERR_INVALID_ARG;
+  if (nrhs < 1 || nrhs > 16 || nrhs > ho->p.max_nrhs || nrhs > hi->p.max_nrhs) return AMG_ERR_INVALID_ARG;
+  if (!(tol > 0) || !(inner_tol > 0) || max_outer < 1 || max_inner_applies < 1) return AMG_ERR_INVALID_ARG;
+  if (ho->p.vec_prec == AMG_FP64 || hi->p.vec_prec == AMG_FP64) return AMG_ERR_UNSUPPORTED;
+  for (int mu = 0; mu < 4; ++mu)
+    if (ho->g.L[mu] != hi->g.L[mu] || ho->g.B[mu] != hi->g.B[mu]) return AMG_ERR_INVALID_ARG;
+  if (ho->g.ntv != hi->g.ntv) return AMG_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  ho->last_stream = hi->last_stream = st;
+  const long long rows = ho->g.Vc * ho->g.nc, n = rows * nrhs;
+  const size_t bytes = (size_t)n * sizeof(float2);
+  // workspace: r, e, w (3 coarse vectors) + norms + keep flags, owned by the outer handle
+  const size_t need = 3 * bytes + 64 * sizeof(double) + 64 * sizeof(int);
+  if (need > ho->tmp_bytes) {
+    AMG_CUDA_TRY(cudaStreamSynchronize(st));
+    cudaFree(ho->xc_tmp);
+    cudaFree(ho->yc_tmp);
+    ho->xc_tmp = ho->yc_tmp = nullptr;
+    ho->tmp_bytes = 0;
+    AMG_CUDA_TRY(cudaMalloc(&ho->xc_tmp, need));
+    AMG_CUDA_TRY(cudaMalloc(&ho->yc_tmp, need));
+    ho->tmp_bytes = need;
+  }
+  float2* r = (float2*)ho->xc_tmp;
+  float2* e = r + n;
+  float2* w = e + n;
+  double* nrm = (double*)(w + n);
+  int* keep = (int*)(nrm + 64);
+  const float2* b = (const float2*)d_b;
+  float2* x = (float2*)d_x;
+  AMG_CUDA_TRY(cudaMemsetAsync(x, 0, bytes, st));
+  AMG_CUDA_TRY(cudaMemcpyAsync(r, b, bytes, cudaMemcpyDeviceToDevice, st));
+  std::vector<double> bn(nrhs), rn(nrhs), inner(nrhs, 0.0), outer(nrhs, 0.0);
+  std::vector<int> kp(nrhs, 1);
+  std::vector<double> sub(2 * nrhs);
+  k_colnorm2<<<nrhs, 1024, 0, st>>>(b, rows, nrhs, nrm);
+  AMG_LAUNCH_CHECK();
+  ho->launches++;
+  AMG_CUDA_TRY(cudaMemcpyAsync(bn.data(), nrm, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
+  AMG_CUDA_TRY(cudaStreamSynchronize(st));
+  for (int q = 0; q < nrhs; ++q) rn[q] = 1.0;
+  for (int it = 0; it < max_outer; ++it) {
+    bool all = true;
+    for (int q = 0; q < nrhs; ++q) {
+      kp[q] = bn[q] > 0 && rn[q] > tol;
+      all = all && !kp[q];
+    }
+    if (all) break;
+    if (it > 0) {  // zero the columns that have converged so the inner solve skips them
+      AMG_CUDA_TRY(cudaMemcpyAsync(keep, kp.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, st));
+      k_resid<<<4 * 152, 256, 0, st>>>(r, b, w, keep, n, nrhs);
+      AMG_LAUNCH_CHECK();
+      ho->launches++;
+    }
+    amg_status s = amg_internal_solve(hi, r, e, nrhs, inner_tol, restart, max_inner_applies, st, sub.data());
+    if (s != AMG_OK) return s;
+    for (int q = 0; q < nrhs; ++q) inner[q] += kp[q] ? sub[2 * q] : 0;
+    k_axpy<<<4 * 152, 256, 0, st>>>(x, e, n);
+    AMG_LAUNCH_CHECK();
+    ho->launches++;
+    s = amg_internal_apply(ho, x, w, nrhs, st);
+    if (s != AMG_OK) return s;
+    for (int q = 0; q < nrhs; ++q) kp[q] = 1;
+    AMG_CUDA_TRY(cudaMemcpyAsync(keep, kp.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, st));
+    k_resid<<<4 * 152, 256, 0, st>>>(r, b, w, keep, n, nrhs);
+    k_colnorm2<<<nrhs, 1024, 0, st>>>(r, rows, nrhs, nrm);
+    AMG_LAUNCH_CHECK();
+    ho->launches += 2;
+    AMG_CUDA_TRY(cudaMemcpyAsync(rn.data(), nrm, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
+    AMG_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int q = 0; q < nrhs; ++q) {
+      rn[q] = bn[q] > 0 ? std::sqrt(rn[q] / bn[q]) : 0.0;
+      outer[q] += 1;
+    }
+  }
+  if (info)
+    for (int q = 0; q < nrhs; ++q) {
+      info[3 * q] = inner[q];
+      info[3 * q + 1] = outer[q];
+      info[3 * q + 2] = rn[q];
+    }
+  return AMG_OK;
+}
