@@ -167,7 +167,23 @@ amg_status amg_cgc(amg_handle h, const void *d_y, void *d_x, int nrhs, double to
  * owned by hs[0]; later calls reuse it.
  */
 amg_status amg_batch_cgc(const amg_handle *hs, int n, const void *const *d_y, void *const *d_x,
-                         const int *nrhs, void *stream);
+                         const int *nrhs, void *stream);   /* n <= 8; FP32 R, D_c and vectors */
+
+/*
+ * amg_batch_autotune -- times the fused batch launch for each candidate shape (128, 256 or 512
+ * threads per CTA x 1, 2 or 4 CTAs per SM) on the given buffers (which it overwrites like
+ * amg_batch_cgc) and keeps the fastest in hs[0] for later amg_batch_cgc calls.  best_ms (may be
+ * NULL) receives its time in milliseconds.  Synchronises the stream.
+ */
+amg_status amg_batch_autotune(const amg_handle *hs, int n, const void *const *d_y, void *const *d_x,
+                              const int *nrhs, void *stream, double *best_ms);
+/*
+ * amg_batch_test_hook -- test hook for the bounded waits of amg_batch_cgc: the next launches whose
+ * first handle is h0 expect extra_need more phase-1 jobs for lattice 0 than exist, so its
+ * coarse-operator jobs wait until their limit (about one second) runs out; the launch then ends
+ * early and amg_sync_status reports AMG_ERR_TIMEOUT.  extra_need = 0 restores normal operation.
+ */
+amg_status amg_batch_test_hook(amg_handle h0, int extra_need);
 
 /* R as [Nblock][2][ntv][6 Vb] complex double (row j of R_i^h = v_j^dagger on A_i^h), device or host out. */
 amg_status amg_export_R(amg_handle h, void *out);
@@ -184,7 +200,7 @@ amg_status amg_setup_timings(amg_handle h, double out_ms[4]);
 /* Number of kernels this handle has launched so far (a host-side count, for benchmarks). */
 amg_status amg_kernel_launches(amg_handle h, unsigned long long *out);
 
-/* Waits for the handle's last stream and reports device-detected errors. */
+/* Waits for the handle's last stream and reports device-detected errors, then clears them. */
 amg_status amg_sync_status(amg_handle h);
 
 amg_status amg_destroy(amg_handle h);

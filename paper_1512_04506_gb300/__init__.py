@@ -67,6 +67,9 @@ _proto = {
     "amg_cgc": [_vp, _vp, _vp, _i, _d, _i, _i, _vp, ctypes.POINTER(_d)],
     "amg_batch_cgc": [ctypes.POINTER(_vp), _i, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                       ctypes.POINTER(_i), _vp],
+    "amg_batch_autotune": [ctypes.POINTER(_vp), _i, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                           ctypes.POINTER(_i), _vp, ctypes.POINTER(_d)],
+    "amg_batch_test_hook": [_vp, _i],
     "amg_export_R": [_vp, _vp],
     "amg_export_Dc": [_vp, _vp],
     "amg_export_clover": [_vp, _vp],
@@ -216,6 +219,20 @@ def amg_batch_cgc(hs, ys, xs, nrhs, stream=None):
     X = (_vp * n)(*[ptr(x) for x in xs])
     R = (_i * n)(*nrhs)
     return _check(lib.amg_batch_cgc(H, n, Y, X, R, stream_ptr(stream)), "amg_batch_cgc")
+
+
+def amg_batch_autotune(hs, ys, xs, nrhs, stream=None):
+    """Returns the time in ms of the fastest launch shape, which hs[0] keeps."""
+    n = len(hs)
+    best = ctypes.c_double()
+    _check(lib.amg_batch_autotune((_vp * n)(*hs), n, (_vp * n)(*[ptr(y) for y in ys]),
+                                  (_vp * n)(*[ptr(x) for x in xs]), (_i * n)(*nrhs), stream_ptr(stream),
+                                  ctypes.byref(best)), "amg_batch_autotune")
+    return best.value
+
+
+def amg_batch_test_hook(h0, extra_need):
+    return _check(lib.amg_batch_test_hook(h0, extra_need), "amg_batch_test_hook")
 
 
 def amg_export_R(h, out):

@@ -328,6 +328,7 @@ amg_status amg_sync_status(amg_handle h) {
   if (cudaStreamSynchronize(h->last_stream) != cudaSuccess) return AMG_ERR_CUDA;
   unsigned e = 0;
   if (cudaMemcpy(&e, h->err, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess) return AMG_ERR_CUDA;
+  if (e && cudaMemset(h->err, 0, sizeof(unsigned)) != cudaSuccess) return AMG_ERR_CUDA;  // reported once
   if (e & AMG_EBIT_TIMEOUT) return AMG_ERR_TIMEOUT;
   if (e & AMG_EBIT_RANK) return AMG_ERR_RANK_DEFICIENT;
   if (e & AMG_EBIT_NONFINITE) return AMG_ERR_NONFINITE;
