@@ -439,6 +439,217 @@ def run_reference(args):
     return res, rank
 
 
+def _kernel_time(fn, n, stream):
+    import torch
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+    for _ in range(3):
+        fn()
+    for a, b in evs:
+        a.record(stream)
+        fn()
+        b.record(stream)
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in evs) / n / 1000.0
+
+
+def _timed_steps(step, steps, warmup, stream, flush=None):
+    import torch
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    with Clocks(torch.cuda.current_device()) as clk:
+        for a, b in ev:
+            if flush is not None:
+                flush.zero_()
+            a.record(stream)
+            step()
+            b.record(stream)
+        torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in ev) / 1000.0, clk.summary()
+
+
+def run_tc16(args):
+    """48^3 x 96, 4^4 blocks (12^3 x 24 coarse), Ntv = 24, 16 right-hand sides, BF16 tensor cores.
+
+    Step: restriction of 16 BF16 right-hand sides, FGMRES(30) to 0.05 on the BF16 D_c (all 16
+    right-hand sides), prolongation to BF16; the same byte accounting as the default workload
+    (BF16 R and D_c: 4 B per complex entry; fine vectors BF16, coarse vectors FP32)."""
+    import torch
+    import paper_1512_04506_gb300 as amg
+    from synth import device as sd
+    Lt, ntv, nrhs, seed = (48, 48, 48, 96), 24, 16, 20151204 + 4
+    V = int(np.prod(Lt))
+    Vb = int(np.prod(B))
+    Vc = V // Vb
+    nc = 2 * ntv
+    st = torch.cuda.current_stream()
+    U = sd.links(seed, EPS, Lt)
+    tv = sd.test_vectors(seed, ntv, Lt)
+    p = amg.make_params(Lt, B, ntv, nrhs, M0, CSW, amg.AMG_BF16, amg.AMG_BF16, amg.AMG_BF16)
+    h, _ = amg.amg_setup_coarse(p, U, tv, st)
+    setup_ms = amg.amg_setup_timings(h)
+    del U, tv
+    torch.cuda.empty_cache()
+    y32 = sd.fine_rhs(seed, nrhs, Lt, torch.complex64)
+    y = torch.view_as_real(y32).to(torch.bfloat16)
+    del y32
+    torch.cuda.empty_cache()
+    x = torch.empty_like(y)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    info = amg.amg_cgc(h, y, x, nrhs, TOL, RESTART, MAX_APPLIES, st, info=True)
+    applies = max(a for a, _ in info)
+    t, clk = _timed_steps(lambda: amg.amg_cgc(h, y, x, nrhs, TOL, RESTART, MAX_APPLIES, st, info=False),
+                          args.steps, args.warmup, st, flush)
+    Rb = Vc * 2 * ntv * 6 * Vb * 4
+    vf = V * 12 * nrhs * 4
+    vc = Vc * nc * nrhs * 8
+    parts = {"restrict": Rb + vf + vc, "prolong": Rb + vc + vf, "apply": Vc * 9 * nc * nc * 4 + 2 * vc}
+    flops = {"restrict": 8.0 * Vc * 2 * ntv * 6 * Vb * nrhs, "prolong": 8.0 * Vc * 2 * ntv * 6 * Vb * nrhs,
+             "apply": 8.0 * Vc * 9 * nc * nc * nrhs}
+    gs = sum((2 * (j + 1) + 4) * vc for j in arnoldi_iterations(applies))
+    step_bytes = parts["restrict"] + parts["prolong"] + applies * parts["apply"] + gs
+    yc = torch.empty((Vc, 2, ntv, nrhs), dtype=torch.complex64, device="cuda")
+    zc = torch.empty_like(yc)
+    amg.amg_restrict(h, y, yc, nrhs, st)
+    tk = {"restrict": _kernel_time(lambda: amg.amg_restrict(h, y, yc, nrhs, st), 5, st),
+          "apply": _kernel_time(lambda: amg.amg_coarse_apply(h, yc, zc, nrhs, st), 20, st),
+          "prolong": _kernel_time(lambda: amg.amg_prolong(h, yc, x, nrhs, st), 5, st)}
+    status = amg.amg_sync_status(h)
+    amg.amg_destroy(h)
+    if status != amg.AMG_OK:
+        raise RuntimeError(amg.amg_status_string(status))
+    peaks, src = measured_peaks()
+    counts = {"restrict": 1, "prolong": 1, "apply": applies}
+    dom = max(tk, key=lambda k: tk[k] * counts[k])
+    kern = {k: {"us": round(tk[k] * 1e6, 1), "GB/s": round(parts[k] / tk[k] / 1e9, 1),
+                "frac": round(parts[k] / tk[k] / 1e9 / peaks["hbm_gbs"], 4),
+                "TFLOP/s": round(flops[k] / tk[k] / 1e12, 1),
+                "tensor_frac": round(flops[k] / tk[k] / 1e12 / peaks["bf16_tflops"], 4)} for k in tk}
+    return {
+        "metric": METRIC, "value": round(step_bytes * args.steps / t / 1e9, 2), "unit": "GB/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1000 * t / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": "tc16_48^3x96_b4_ntv24: 48^3x96 Wilson-clover, 4^4 blocks -> 12^3x24 coarse, "
+                               "Ntv=24, 16 RHS, BF16 R / D_c / fine vectors on the tensor cores, FP32 "
+                               "accumulation and coarse vectors; step = R Y, FGMRES(30) to 0.05, P X_c",
+                   "applies_per_step": applies, "bytes_per_step": step_bytes},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["GB/s"], "peak": peaks["hbm_gbs"],
+                     "unit": "GB/s", "frac": kern[dom]["frac"], "peak_source": src, "traffic": None},
+        "kernels": kern, "setup_ms": [round(v, 1) for v in setup_ms], "clocks": clk,
+    }
+
+
+def run_fp16(args):
+    """32^3 x 64, 4^4 blocks (8^3 x 16 coarse), Ntv = 24, FP16 D_c with per-block FP32 scales, one
+    right-hand side: 200 D_c applications of FGMRES(30) (tolerance 0 so the budget is spent);
+    error of one FP16 application against the FP64 application of the same D_c."""
+    import torch
+    import paper_1512_04506_gb300 as amg
+    from synth import device as sd
+    Lt, ntv, seed = (32, 32, 32, 64), 24, 20151204 + 3
+    Vc = int(np.prod(Lt)) // int(np.prod(B))
+    nc = 2 * ntv
+    st = torch.cuda.current_stream()
+    U = sd.links(seed, EPS, Lt)
+    tv = sd.test_vectors(seed, ntv, Lt)
+    h16, _ = amg.amg_setup_coarse(amg.make_params(Lt, B, ntv, 1, M0, CSW, amg.AMG_FP16_SCALED, amg.AMG_FP32,
+                                                  amg.AMG_FP32), U, tv, st)
+    h64, _ = amg.amg_setup_coarse(amg.make_params(Lt, B, ntv, 1, M0, CSW, amg.AMG_FP64, amg.AMG_FP64,
+                                                  amg.AMG_FP64), U, tv, st)
+    del U, tv
+    b = sd.coarse_vector(seed, ntv, 1, Vc, torch.complex64)
+    x = torch.empty_like(b)
+    y16 = torch.empty_like(b)
+    y64 = torch.empty((Vc, 2, ntv, 1), dtype=torch.complex128, device="cuda")
+    amg.amg_coarse_apply(h16, b, y16, 1, st)
+    amg.amg_coarse_apply(h64, b.to(torch.complex128), y64, 1, st)
+    torch.cuda.synchronize()
+    err = float((y16.to(torch.complex128) - y64).norm() / y64.norm())
+    t, clk = _timed_steps(lambda: amg.amg_coarse_solve(h16, b, x, 1, 0.0, RESTART, 200, st, info=False),
+                          args.steps, args.warmup, st)
+    apply_bytes = Vc * 9 * nc * nc * 4 + Vc * 9 * 4 + 2 * Vc * nc * 8
+    ta = _kernel_time(lambda: amg.amg_coarse_apply(h16, b, y16, 1, st), 50, st)
+    gs = sum((2 * (j + 1) + 4) * Vc * nc * 8 for j in arnoldi_iterations(200))
+    step_bytes = 200 * apply_bytes + gs
+    amg.amg_destroy(h16)
+    amg.amg_destroy(h64)
+    peaks, src = measured_peaks()
+    return {
+        "metric": METRIC, "value": round(step_bytes * args.steps / t / 1e9, 2), "unit": "GB/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1000 * t / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f16", "data": "synthetic",
+        "config": {"workload": "fp16_32^3x64_b4_ntv24: 8^3x16 coarse, Ntv=24, FP16 D_c + FP32 scale per "
+                               "block, 1 RHS; step = 200 D_c applications of FGMRES(30)",
+                   "bytes_per_step": step_bytes, "fp16_apply_rel_error_vs_fp64": err},
+        "roofline": {"bound": "hbm", "kernel": "coarse apply (FP16 links)",
+                     "achieved": round(apply_bytes / ta / 1e9, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": round(apply_bytes / ta / 1e9 / peaks["hbm_gbs"], 4), "peak_source": src,
+                     "traffic": None, "avg_launch_us": round(ta * 1e6, 2)},
+        "clocks": clk,
+    }
+
+
+def run_batch(args):
+    """The uneven batch in one persistent launch, captured in a CUDA graph: lattices 16^4 (Ntv=16,
+    1 RHS), 24^3 x 48 (Ntv=20, 4 RHS), 32^3 x 64 (Ntv=24, 12 RHS), 4^4 blocks, eps 0.2 / 0.3 / 0.4,
+    FP32 storage; step = x_k = P_k D_ck R_k y_k for all three; launch shape from the autotuner."""
+    import torch
+    import paper_1512_04506_gb300 as amg
+    from synth import device as sd
+    spec = [((16, 16, 16, 16), 16, 1, 0.2), ((24, 24, 24, 48), 20, 4, 0.3), ((32, 32, 32, 64), 24, 12, 0.4)]
+    st = torch.cuda.current_stream()
+    hs, ys, xs, nr = [], [], [], []
+    step_bytes = 0
+    for k, (Lk, ntv, nrhs, eps) in enumerate(spec):
+        seed = 20151204 + 5 + 10 * k
+        U = sd.links(seed, eps, Lk)
+        tv = sd.test_vectors(seed, ntv, Lk)
+        h, _ = amg.amg_setup_coarse(amg.make_params(Lk, B, ntv, nrhs, M0, CSW, amg.AMG_FP32, amg.AMG_FP32,
+                                                    amg.AMG_FP32), U, tv, st)
+        del U, tv
+        y = sd.fine_rhs(seed, nrhs, Lk, torch.complex64)
+        hs.append(h)
+        ys.append(y)
+        xs.append(torch.empty_like(y))
+        nr.append(nrhs)
+        V = int(np.prod(Lk))
+        Vc = V // int(np.prod(B))
+        nc = 2 * ntv
+        step_bytes += 2 * Vc * 2 * ntv * 6 * int(np.prod(B)) * 8 + 2 * V * 12 * nrhs * 8 \
+            + Vc * 9 * nc * nc * 8 + 4 * Vc * nc * nrhs * 8
+    torch.cuda.empty_cache()
+    amg.amg_batch_cgc(hs, ys, xs, nr, st)
+    best = amg.amg_batch_autotune(hs, ys, xs, nr, st)
+    g = torch.cuda.CUDAGraph()
+    s2 = torch.cuda.Stream()
+    s2.wait_stream(st)
+    with torch.cuda.stream(s2):
+        with torch.cuda.graph(g, stream=s2):
+            amg.amg_batch_cgc(hs, ys, xs, nr, s2)
+    st.wait_stream(s2)
+    t, clk = _timed_steps(g.replay, args.steps, args.warmup, st)
+    status = amg.amg_sync_status(hs[0])
+    for h in hs:
+        amg.amg_destroy(h)
+    if status != amg.AMG_OK:
+        raise RuntimeError(amg.amg_status_string(status))
+    peaks, src = measured_peaks()
+    gbs = step_bytes * args.steps / t / 1e9
+    return {
+        "metric": METRIC, "value": round(gbs, 2), "unit": "GB/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(1000 * t / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "batch: 16^4 (Ntv 16, 1 RHS) + 24^3x48 (Ntv 20, 4 RHS) + 32^3x64 (Ntv 24, "
+                               "12 RHS), 4^4 blocks, FP32; one persistent launch per step, CUDA graph",
+                   "bytes_per_step": step_bytes, "autotuned_ms": round(best, 4)},
+        "roofline": {"bound": "hbm", "kernel": "fused batch (whole launch)", "achieved": round(gbs, 1),
+                     "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(gbs / peaks["hbm_gbs"], 4),
+                     "peak_source": src, "traffic": None},
+        "clocks": clk,
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -448,6 +659,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-speedup", action="store_true",
                     help="skip the batched-mixed vs plain FP32 coarse-solve comparison")
+    ap.add_argument("--workload", default="fp32", choices=["fp32", "tc16", "fp16", "batch"],
+                    help="fp32: the default 32^4 workload; tc16: 48^3x96 with 16 RHS on the tensor cores; "
+                         "fp16: 200 FP16 coarse applications at 32^3x64; batch: the uneven batch")
     ap.add_argument("--lattice", default=None,
                     help="Lx,Ly,Lz,Lt override of the 32^4 lattice (smaller cases for ncu captures)")
     args = ap.parse_args()
@@ -459,6 +673,12 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         res, rank = run_reference(args)
+    elif args.workload == "tc16":
+        res, rank = run_tc16(args), 0
+    elif args.workload == "fp16":
+        res, rank = run_fp16(args), 0
+    elif args.workload == "batch":
+        res, rank = run_batch(args), 0
     else:
         res, rank = run_gpu(args)
     if rank == 0 and res is not None:
