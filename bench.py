@@ -33,9 +33,10 @@ NTV = 20
 EPS, M0, CSW = 0.3, -0.3, 1.0
 SEED = 20151204 + 2
 TOL, RESTART, MAX_APPLIES = 0.05, 30, 200
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from the ncu capture
-# summarised under profiles/, for the kernels as they are now; None until captured.
-TRAFFIC = {}
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the 32^4 workload, from
+# the ncu captures of the 24^4 case summarised under profiles/ scaled by the number of blocks /
+# coarse sites (the per-unit work is the same); valid for the kernels as captured.
+TRAFFIC = {"restrict": 2125495915, "prolong": 2160730820, "apply": 483984978}
 METRIC = "coarse-grid correction GB/s & % HBM roofline; batched-mixed vs plain speedup"
 WORKLOAD = "fp32_32^4_b4_ntv20: 32^4 Wilson-clover, 4^4 blocks -> 8^4 coarse, Ntv=20, 1 RHS, " \
            "FP64 setup, FP32 R and D_c; step = R y, FGMRES(30) to 0.05 (<=200 applies), P x_c"
