@@ -22,7 +22,8 @@
 struct Geom {
   int L[4], B[4], Lc[4];
   long long V, Vb, Vc;
-  int ntv, nc, nagg;  // nc = 2 ntv, nagg = 6 Vb (dof per aggregate)
+  int ntv, nc, nagg;        // nc = 2 ntv, nagg = 6 Vb (dof per aggregate)
+  const int* soff = nullptr;  // device: lattice offset of block-local site s from the block origin
 };
 
 __host__ __device__ inline long long site_index(const int* L, int x, int y, int z, int t) {
@@ -45,6 +46,20 @@ __host__ __device__ inline long long block_site(const Geom& g, long long blk, in
   int bt = q / g.B[2];
   return site_index(g.L, X * g.B[0] + bx, Y * g.B[1] + by, Z * g.B[2] + bz, T * g.B[3] + bt);
 }
+
+// Fine site of the first site (local coordinates 0) of block blk.
+__host__ __device__ inline long long block_origin(const Geom& g, long long blk) {
+  const int X = (int)(blk % g.Lc[0]);
+  long long r = blk / g.Lc[0];
+  const int Y = (int)(r % g.Lc[1]);
+  r /= g.Lc[1];
+  const int Z = (int)(r % g.Lc[2]);
+  const int T = (int)(r / g.Lc[2]);
+  return site_index(g.L, X * g.B[0], Y * g.B[1], Z * g.B[2], T * g.B[3]);
+}
+
+// block_site through the precomputed offsets: origin + soff[s] (device code; g.soff set).
+__device__ inline long long block_site_fast(const Geom& g, long long origin, int s) { return origin + __ldg(g.soff + s); }
 
 // ---------------------------------------------------------------- complex helpers
 __host__ __device__ inline double2 cmul(double2 a, double2 b) {
@@ -114,6 +129,7 @@ struct amg_coarse {
   void* Dtc = nullptr;        // BF16 tensor-core layout (when link_prec == BF16)
   void* Rtc = nullptr;        // BF16 tensor-core layout of R (when r_prec == BF16)
   int* nbr = nullptr;         // [Vc][9]
+  int* soff = nullptr;        // [Vb] site offsets inside a block (g.soff points here)
   unsigned int* err = nullptr;  // device error word
   float setup_ms[4] = {0, 0, 0, 0};
   cudaStream_t last_stream = 0;

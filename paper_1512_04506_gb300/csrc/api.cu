@@ -76,6 +76,7 @@ void free_handle(amg_coarse* h) {
   cudaFree(h->Dq);
   cudaFree(h->Dscale);
   cudaFree(h->nbr);
+  cudaFree(h->soff);
   cudaFree(h->err);
   cudaFree(h->sw.buf);
   if (h->sw.hflag) {
@@ -178,6 +179,20 @@ amg_status amg_setup_coarse(const amg_params* p, const void* d_U, const void* d_
     AMG_TRY_H(dmalloc(&h->Dscale, (size_t)g.Vc * 9 * sizeof(float)));
   }
   AMG_TRY_H(dmalloc(&h->nbr, (size_t)g.Vc * 9 * sizeof(int)));
+  AMG_TRY_H(dmalloc(&h->soff, (size_t)g.Vb * sizeof(int)));
+  {
+    std::vector<int> so((size_t)g.Vb);
+    for (int s = 0; s < (int)g.Vb; ++s) {
+      const int bx = s % g.B[0], by = (s / g.B[0]) % g.B[1], bz = (s / (g.B[0] * g.B[1])) % g.B[2];
+      const int bt = s / (g.B[0] * g.B[1] * g.B[2]);
+      so[s] = (int)site_index(g.L, bx, by, bz, bt);
+    }
+    if (cudaMemcpy(h->soff, so.data(), so.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) {
+      free_handle(h);
+      return AMG_ERR_CUDA;
+    }
+    h->g.soff = h->soff;
+  }
   AMG_TRY_H(dmalloc(&h->err, sizeof(unsigned)));
   {
     std::vector<int> nb((size_t)g.Vc * 9);

@@ -57,9 +57,10 @@ __device__ void restrict_job(const LatDesc& L, long long blk, int r0, float2* sm
   const Geom& g = L.g;
   const int nagg = g.nagg, ntv = g.ntv, Vb = (int)g.Vb, ld = L.nrhs;
   float2* ys = sm;  // [2][nagg][NR]
+  const long long origin = block_origin(g, blk);
   for (int e = threadIdx.x; e < Vb * 12 * NR; e += blockDim.x) {
     const int sl = e / (12 * NR), rem = e % (12 * NR), dof = rem / NR, r = rem % NR;
-    const long long site = block_site(g, blk, sl);
+    const long long site = block_site_fast(g, origin, sl);
     ys[((size_t)(dof / 6) * nagg + sl * 6 + dof % 6) * NR + r] = L.y[(site * 12 + dof) * ld + r0 + r];
   }
   __syncthreads();
@@ -152,6 +153,7 @@ __device__ void prolong_job(const LatDesc& L, long long blk, int r0, float2* sm)
   const Geom& g = L.g;
   const int nagg = g.nagg, ntv = g.ntv, tpa = nagg / 2, ld = L.nrhs;
   float2* xs = sm;  // [2 ntv][NR]
+  const long long origin = block_origin(g, blk);
   for (int e = threadIdx.x; e < 2 * ntv * NR; e += blockDim.x)
     xs[e] = L.zc[(blk * 2 * ntv + e / NR) * ld + r0 + e % NR];
   __syncthreads();
@@ -177,7 +179,7 @@ __device__ void prolong_job(const LatDesc& L, long long blk, int r0, float2* sm)
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       const int n = n0 + q, sl = n / 6;
-      const long long site = block_site(g, blk, sl);
+      const long long site = block_site_fast(g, origin, sl);
 #pragma unroll
       for (int r = 0; r < NR; ++r) L.x[(site * 12 + hh * 6 + n % 6) * ld + r0 + r] = acc[q][r];
     }

@@ -91,6 +91,16 @@ __device__ inline T warp_csum(T v) {
   return v;
 }
 
+// One complex value global -> shared without a register round trip (cp.async, 8 or 16 bytes).
+__device__ inline void cp_async_elem(float2* dst, const float2* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ inline void cp_async_elem(double2* dst, const double2* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ inline void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 template <typename AT>
 __device__ inline AT scaled(AT v, double f) {
   using RT = decltype(v.x);
@@ -128,8 +138,8 @@ __global__ void __launch_bounds__(288) apply_tma_kernel(const ApplyArgs<LT, NR> 
   const int nc = a.g.nc, K = 9 * nc, ns = a.ns;
   const unsigned chunk = (unsigned)(nc * nc * sizeof(LT));
   unsigned char* stages = sm + kPipeBytes;
-  AT* xs = reinterpret_cast<AT*>(stages + (size_t)ns * chunk);
-  AT* red = xs + (size_t)K * NR;
+  AT* xs = reinterpret_cast<AT*>(stages + (size_t)ns * chunk);  // [2][K][NR]
+  AT* red = xs + (size_t)2 * K * NR;
   const int ncw = (blockDim.x - 32) >> 5;
   if (threadIdx.x == 0) {
     for (int s = 0; s < ns; ++s) {
@@ -162,20 +172,42 @@ __global__ void __launch_bounds__(288) apply_tma_kernel(const ApplyArgs<LT, NR> 
   }
   const int t = threadIdx.x - 32, nct = blockDim.x - 32;
   const int Gc = nc / CPL, rc = t % Gc, grp = t / Gc;
-  long long c = 0;
-  for (long long i = blockIdx.x; i < Vc; i += gridDim.x) {
+  // Neighbour vectors of site i, gathered asynchronously one site ahead into the other buffer;
+  // each thread later scales exactly the elements it gathered (no barrier needed in between).
+  auto gather = [&](long long i, AT* buf) {
     for (int e = t; e < K * NR; e += nct) {
       const int k = e / NR, r = e % NR, d = k / nc, b = k % nc;
       const long long j = a.nbr[i * 9 + d];
-      AT v = a.x[(j * nc + b) * a.ld + a.r0 + r];
+      cp_async_elem(buf + e, a.x + (j * nc + b) * a.ld + a.r0 + r);
+    }
+    cp_async_commit();
+  };
+  auto finish = [&](long long i, AT* buf) {
+    cp_async_wait_all();
+    if (!a.xscale && !a.dscale) return;
+    for (int e = t; e < K * NR; e += nct) {
+      const int k = e / NR, r = e % NR, d = k / nc, b = k % nc;
+      AT v = buf[e];
       if (a.xscale) {
         v = scaled(v, a.xscale[a.r0 + r]);
         if (d == 0 && a.vout) a.vout[(i * nc + b) * a.ld + a.r0 + r] = v;
       }
       if (a.dscale) v = scaled(v, (double)a.dscale[i * 9 + d]);
-      xs[e] = v;
+      buf[e] = v;
     }
-    consumer_sync(nct);
+  };
+  long long c = 0;
+  int it = 0;
+  if (blockIdx.x < Vc) {
+    gather(blockIdx.x, xs);
+    finish(blockIdx.x, xs);
+  }
+  consumer_sync(nct);
+  for (long long i = blockIdx.x; i < Vc; i += gridDim.x, ++it) {
+    AT* xcur = xs + (size_t)(it & 1) * K * NR;
+    AT* xnext = xs + (size_t)((it + 1) & 1) * K * NR;
+    const long long inext = i + gridDim.x;
+    if (inext < Vc) gather(inext, xnext);
     AT acc[CPL][NR];
 #pragma unroll
     for (int q = 0; q < CPL; ++q)
@@ -190,7 +222,7 @@ __global__ void __launch_bounds__(288) apply_tma_kernel(const ApplyArgs<LT, NR> 
       }
       if (ok && grp < a.G) {
         const LT* blk = reinterpret_cast<const LT*>(stages + (size_t)s * chunk) + rc * CPL;
-        const AT* xd = xs + (size_t)d * nc * NR;
+        const AT* xd = xcur + (size_t)d * nc * NR;
 #pragma unroll 4
         for (int b = grp; b < nc; b += a.G) {
           AT v[CPL];
@@ -219,6 +251,7 @@ __global__ void __launch_bounds__(288) apply_tma_kernel(const ApplyArgs<LT, NR> 
       }
       a.y[(i * nc + e / NR) * a.ld + a.r0 + e % NR] = sum;
     }
+    if (inext < Vc) finish(inext, xnext);
     consumer_sync(nct);
   }
 }
@@ -237,9 +270,10 @@ __global__ void __launch_bounds__(256) restrict_kernel(const ST* __restrict__ R,
   AT* ys = reinterpret_cast<AT*>(smraw);
   const long long blk = blockIdx.x;
   const int nagg = g.nagg, ntv = g.ntv, Vb = (int)g.Vb;
+  const long long origin = block_origin(g, blk);
   for (int e = threadIdx.x; e < Vb * 12 * NR; e += blockDim.x) {
     const int sl = e / (12 * NR), rem = e % (12 * NR), dof = rem / NR, r = rem % NR;
-    const long long site = block_site(g, blk, sl);
+    const long long site = block_site_fast(g, origin, sl);
     const int hh = dof / 6, n = sl * 6 + dof % 6;
     ys[((size_t)hh * nagg + n) * NR + r] = y[(site * 12 + dof) * ld + r0 + r];
   }
@@ -350,6 +384,7 @@ __global__ void __launch_bounds__(160) prolong_tma_kernel(const ProlongArgs<ST, 
       const int hh = k / cpa, n0 = (k % cpa) * nch;
       const ST* st = reinterpret_cast<const ST*>(stages + (size_t)s * chunk);
       const AT* xh = xs + (size_t)hh * ntv * NR;
+      const long long origin = block_origin(a.g, blk);
       for (int nl = lane; nl < nch; nl += 32) {
         AT acc[NR];
 #pragma unroll
@@ -363,7 +398,7 @@ __global__ void __launch_bounds__(160) prolong_tma_kernel(const ProlongArgs<ST, 
           }
         }
         const int n = n0 + nl, sl = n / 6, dof = hh * 6 + n % 6;
-        const long long site = block_site(a.g, blk, sl);
+        const long long site = block_site_fast(a.g, origin, sl);
 #pragma unroll
         for (int r = 0; r < NR; ++r) a.x[(site * 12 + dof) * a.ld + a.r0 + r] = acc[r];
       }
@@ -411,7 +446,7 @@ amg_status launch_apply_tma(amg_coarse* h, const LT* D, const float* dscale, con
   const size_t chunk = (size_t)nc * nc * sizeof(LT);
   int ns = (int)((64 * 1024) / chunk);
   ns = ns < 2 ? 2 : (ns > 6 ? 6 : ns);
-  const size_t smem = kPipeBytes + ns * chunk + (size_t)9 * nc * NR * sizeof(AT) + (size_t)G * nc * NR * sizeof(AT);
+  const size_t smem = kPipeBytes + ns * chunk + (size_t)2 * 9 * nc * NR * sizeof(AT) + (size_t)G * nc * NR * sizeof(AT);
   if (smem > 227 * 1024) return AMG_ERR_UNSUPPORTED;
   int grid = 0;
   amg_status s = grid_for(apply_tma_kernel<LT, NR>, threads, smem, h->g.Vc, &grid);

@@ -201,7 +201,7 @@ struct TcRPArgs {
 
 // Block-local sites 8c .. 8c+7 as (8 / run) runs of `run` lattice-consecutive sites.
 __device__ inline long long chunk_site(const Geom& g, long long blk, int c, int u, int run) {
-  return block_site(g, blk, 8 * c + u * run);
+  return block_site_fast(g, block_origin(g, blk), 8 * c + u * run);
 }
 
 template <int NRHS>
@@ -399,6 +399,7 @@ __global__ void __launch_bounds__(224) prolong_tc_kernel(const TcRPArgs a) {
       }
       if (ok && hw < 2) {
         const bf16* Rb = reinterpret_cast<const bf16*>(stages + (size_t)s * chunk);
+        const long long origin = block_origin(a.g, blk);
         float acc[NT][4];
 #pragma unroll
         for (int q = 0; q < NT; ++q)
@@ -446,7 +447,7 @@ __global__ void __launch_bounds__(224) prolong_tc_kernel(const TcRPArgs a) {
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
               const int n = mt * 16 + g + 8 * u, sl = n / 6, dof = hw * 6 + n % 6;
-              const long long site = chunk_site(a.g, blk, cc, sl / run, run) + sl % run;
+              const long long site = block_site_fast(a.g, origin, 8 * cc + sl);
               __nv_bfloat162 v0 = __floats2bfloat162_rn(u ? acc[q][2] : acc[q][0], u ? i2 : i0);
               __nv_bfloat162 v1 = __floats2bfloat162_rn(u ? acc[q][3] : acc[q][1], u ? i3 : i1);
               uint2 pk;
