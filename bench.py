@@ -480,6 +480,8 @@ def run_tc16(args):
     import paper_1512_04506_gb300 as amg
     from synth import device as sd
     Lt, ntv, nrhs, seed = (48, 48, 48, 96), 24, 16, 20151204 + 4
+    if args.lattice:
+        Lt = tuple(int(v) for v in args.lattice.split(","))
     V = int(np.prod(Lt))
     Vb = int(np.prod(B))
     Vc = V // Vb
@@ -531,9 +533,10 @@ def run_tc16(args):
         "metric": METRIC, "value": round(step_bytes * args.steps / t / 1e9, 2), "unit": "GB/s", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1000 * t / args.steps, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-        "config": {"workload": "tc16_48^3x96_b4_ntv24: 48^3x96 Wilson-clover, 4^4 blocks -> 12^3x24 coarse, "
-                               "Ntv=24, 16 RHS, BF16 R / D_c / fine vectors on the tensor cores, FP32 "
-                               "accumulation and coarse vectors; step = R Y, FGMRES(30) to 0.05, P X_c",
+        "config": {"workload": ("tc16_48^3x96_b4_ntv24: 48^3x96 Wilson-clover, 4^4 blocks -> 12^3x24 coarse, "
+                                "Ntv=24, 16 RHS, BF16 R / D_c / fine vectors on the tensor cores, FP32 "
+                                "accumulation and coarse vectors; step = R Y, FGMRES(30) to 0.05, P X_c")
+                               if Lt == (48, 48, 48, 96) else "%dx%dx%dx%d variant of tc16" % Lt,
                    "applies_per_step": applies, "bytes_per_step": step_bytes},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["GB/s"], "peak": peaks["hbm_gbs"],
                      "unit": "GB/s", "frac": kern[dom]["frac"], "peak_source": src, "traffic": None},

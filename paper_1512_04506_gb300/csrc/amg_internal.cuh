@@ -128,6 +128,8 @@ struct amg_coarse {
   float* Dscale = nullptr;    // [Vc][9] (FP16 scaled)
   void* Dtc = nullptr;        // BF16 tensor-core layout (when link_prec == BF16)
   void* Rtc = nullptr;        // BF16 tensor-core layout of R (when r_prec == BF16)
+  void* tc_x = nullptr;       // BF16 planes of the coarse input of the tensor-core apply
+  size_t tc_xbytes = 0;
   int* nbr = nullptr;         // [Vc][9]
   int* soff = nullptr;        // [Vb] site offsets inside a block (g.soff points here)
   unsigned int* err = nullptr;  // device error word

@@ -8,8 +8,10 @@
 // N = 2 nrhs.  The N axis is ordered in groups of 8 columns (Re of 4 right-hand sides, then Im of
 // the same 4), so each 16x8 accumulator tile holds complete complex outputs.  A comes from the
 // D_c stream (cp.async.bulk into an mbarrier ring, as in stream.cu); X is converted to BF16 once
-// per site into padded planes [2][9][nrhs][nc + 8] so that the B-fragment loads hit distinct banks.
-// Warp w of the consumers owns rows 16 w .. 16 w + 15 of the site's output and all N columns.
+// per call into padded BF16 planes (xc_to_planes_kernel), and the producer warp copies, next to
+// each stencil block D_c[i][d], the planes of the neighbour nbr(i, d) into the same stage, so the
+// consumers only issue tensor-core instructions.  Warp w of the consumers owns rows 16 w .. 16 w + 15
+// of the site's output and all N columns.
 #include "amg_internal.cuh"
 #include "pipe.cuh"
 
@@ -28,17 +30,44 @@ __device__ inline void mma_bf16(float (&c)[4], const unsigned (&a)[4], unsigned 
 __device__ inline unsigned lds32(const bf16* p) { return *reinterpret_cast<const unsigned*>(p); }
 
 struct TcApplyArgs {
-  const bf16* D;  // [Vc][9][2][nc][nc]: Re plane then Im plane, row-major (row a, column b)
+  const bf16* D;   // [Vc][9][2][nc][nc]: Re plane then Im plane, row-major (row a, column b)
+  const bf16* X;   // [Vc][xpitch]: the coarse vector in BF16 planes, see xc_to_planes_kernel
   const int* nbr;
-  const float2* x;
   float2* y;
-  float2* vout;
-  const double* xscale;
   const int* skip;
   unsigned* err;
   Geom g;
-  int ns;
+  int ns, xpitch;
 };
+
+// Coarse vector (FP32, [Vc][nc][nrhs], optionally times xscale[r]; the (scaled) FP32 vector is also
+// stored to vout when given) -> BF16 planes per site: plane p (0 Re, 1 Im) at offset p * (nrhs (nc + 8) + 32),
+// row r of length nc + 8 (8 pad); the paddings put the two planes and consecutive rows on
+// different shared-memory banks once a site's block is copied to shared memory.
+template <int NRHS>
+__global__ void xc_to_planes_kernel(const float2* __restrict__ x, bf16* __restrict__ X, int nc, long long Vc,
+                                    int xpitch, const double* __restrict__ xscale, float2* __restrict__ vout,
+                                    const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  const int prow = nc + 8, pplane = NRHS * prow + 32;
+  const long long total = Vc * nc * NRHS;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(e % NRHS);
+    const long long ib = e / NRHS;
+    const int b = (int)(ib % nc);
+    const long long i = ib / nc;
+    float2 v = x[e];
+    if (xscale) {
+      const float f = (float)xscale[r];
+      v.x *= f;
+      v.y *= f;
+    }
+    if (vout) vout[e] = v;
+    bf16* site = X + i * xpitch;
+    site[r * prow + b] = __float2bfloat16_rn(v.x);
+    site[pplane + r * prow + b] = __float2bfloat16_rn(v.y);
+  }
+}
 
 template <int NRHS>
 __global__ void __launch_bounds__(160) apply_tc_kernel(const TcApplyArgs a) {
@@ -47,11 +76,11 @@ __global__ void __launch_bounds__(160) apply_tc_kernel(const TcApplyArgs a) {
   extern __shared__ __align__(128) unsigned char sm[];
   Pipe* pp = reinterpret_cast<Pipe*>(sm);
   const int nc = a.g.nc, ns = a.ns, mt_count = nc / 16;
-  const unsigned chunk = (unsigned)(2 * nc * nc * sizeof(bf16));
+  const unsigned dbytes = (unsigned)(2 * nc * nc * sizeof(bf16));
+  const unsigned xbytes = (unsigned)(a.xpitch * sizeof(bf16));
+  const unsigned chunk = dbytes + xbytes;  // stencil block d of D_c and the neighbour's planes
   unsigned char* stages = sm + kPipeBytes;
-  const int xrow = nc + 8;                            // padded row of an X plane
-  const int xplane = 9 * NRHS * xrow + 32;            // padded plane (bank offset 16 words)
-  bf16* xs = reinterpret_cast<bf16*>(stages + (size_t)ns * chunk);
+  const int xrow = nc + 8, xplane = NRHS * xrow + 32;
   const int ncw = (blockDim.x - 32) >> 5;
   if (threadIdx.x == 0) {
     for (int s = 0; s < ns; ++s) {
@@ -75,32 +104,19 @@ __global__ void __launch_bounds__(160) apply_tc_kernel(const TcApplyArgs a) {
             break;
           }
           mbar_expect_tx(&pp->full[s], chunk);
-          bulk_load(stages + (size_t)s * chunk, a.D + (i * 9 + d) * 2LL * nc * nc, chunk, &pp->full[s]);
+          unsigned char* st = stages + (size_t)s * chunk;
+          bulk_load(st, a.D + (i * 9 + d) * 2LL * nc * nc, dbytes, &pp->full[s]);
+          bulk_load(st + dbytes, a.X + (long long)a.nbr[i * 9 + d] * a.xpitch, xbytes, &pp->full[s]);
         }
       }
       drain(pp, c, ns);
     }
     return;
   }
-  const int t = threadIdx.x - 32, nct = blockDim.x - 32, w = t >> 5, lane = t & 31;
+  const int t = threadIdx.x - 32, w = t >> 5, lane = t & 31;
   const int g = lane >> 2, tq = lane & 3;
   long long c = 0;
   for (long long i = blockIdx.x; i < Vc; i += gridDim.x) {
-    // X planes of the nine neighbours in BF16: xs[plane][d][r][b]
-    for (int e = t; e < 9 * nc * NRHS; e += nct) {
-      const int r = e % NRHS, k = e / NRHS, d = k / nc, b = k % nc;
-      const long long j = a.nbr[i * 9 + d];
-      float2 v = a.x[(j * nc + b) * NRHS + r];
-      if (a.xscale) {
-        const float f = (float)a.xscale[r];
-        v.x *= f;
-        v.y *= f;
-        if (d == 0 && a.vout) a.vout[(i * nc + b) * NRHS + r] = v;
-      }
-      xs[((size_t)d * NRHS + r) * xrow + b] = __float2bfloat16_rn(v.x);
-      xs[xplane + ((size_t)d * NRHS + r) * xrow + b] = __float2bfloat16_rn(v.y);
-    }
-    consumer_sync(nct);
     float acc[NT][4];
 #pragma unroll
     for (int q = 0; q < NT; ++q)
@@ -115,6 +131,7 @@ __global__ void __launch_bounds__(160) apply_tc_kernel(const TcApplyArgs a) {
       }
       if (ok && w < mt_count) {
         const bf16* Ablk = reinterpret_cast<const bf16*>(stages + (size_t)s * chunk);
+        const bf16* xs = reinterpret_cast<const bf16*>(stages + (size_t)s * chunk + dbytes);
         const int row0 = w * 16 + g;
         for (int kk = 0; kk < 2 * (nc / 16); ++kk) {
           const int p = kk / (nc / 16), k0 = (kk % (nc / 16)) * 16;  // p = 0: A_re, 1: A_im
@@ -129,7 +146,7 @@ __global__ void __launch_bounds__(160) apply_tc_kernel(const TcApplyArgs a) {
             // column g of tile q: half = g / 4 (0: Re output, 1: Im output), rhs r = 4 q + g % 4
             const int half = g >> 2, r = 4 * q + (g & 3);
             const int sp = (p == half) ? 0 : 1;  // X_re or X_im
-            const bf16* xb = xs + (size_t)sp * xplane + ((size_t)d * NRHS + r) * xrow + k0 + 2 * tq;
+            const bf16* xb = xs + (size_t)sp * xplane + (size_t)r * xrow + k0 + 2 * tq;
             unsigned b0 = lds32(xb), b1 = lds32(xb + 8);
             if (p == 1 && half == 0) {
               b0 ^= 0x80008000u;
@@ -162,7 +179,6 @@ __global__ void __launch_bounds__(160) apply_tc_kernel(const TcApplyArgs a) {
         }
       }
     }
-    consumer_sync(nct);
   }
 }
 
@@ -532,16 +548,23 @@ __global__ void bf16_to_dc_kernel(const bf16* __restrict__ in, double2* __restri
   }
 }
 
+int tc_xpitch(const Geom& g, int nrhs) { return ((2 * nrhs * (g.nc + 8) + 64) + 7) / 8 * 8; }
+
 template <int NRHS>
 amg_status launch_apply_tc(amg_coarse* h, const void* x, void* y, cudaStream_t st, const int* skip,
                            const double* xscale, void* vout) {
   const int nc = h->g.nc;
+  const int xpitch = tc_xpitch(h->g, NRHS);
+  if ((size_t)h->g.Vc * xpitch * sizeof(bf16) > h->tc_xbytes) return AMG_ERR_INVALID_ARG;  // nrhs > max_nrhs
+  xc_to_planes_kernel<NRHS><<<4 * 152, 256, 0, st>>>((const float2*)x, (bf16*)h->tc_x, nc, h->g.Vc, xpitch, xscale,
+                                                     (float2*)vout, skip);
+  AMG_LAUNCH_CHECK();
+  h->launches++;
   const int threads = 32 + 32 * (nc / 16);
-  const size_t chunk = (size_t)2 * nc * nc * sizeof(bf16);
-  int ns = (int)((48 * 1024) / chunk);
+  const size_t chunk = (size_t)2 * nc * nc * sizeof(bf16) + (size_t)xpitch * sizeof(bf16);
+  int ns = (int)((72 * 1024) / chunk);
   ns = ns < 2 ? 2 : (ns > 6 ? 6 : ns);
-  const size_t xbytes = (size_t)2 * (9 * NRHS * (nc + 8) + 32) * sizeof(bf16);
-  const size_t smem = kPipeBytes + ns * chunk + xbytes;
+  const size_t smem = kPipeBytes + ns * chunk;
   if (smem > 227 * 1024) return AMG_ERR_UNSUPPORTED;
   AMG_CUDA_TRY(cudaFuncSetAttribute(apply_tc_kernel<NRHS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
@@ -549,7 +572,7 @@ amg_status launch_apply_tc(amg_coarse* h, const void* x, void* y, cudaStream_t s
   if (per_sm < 1) return AMG_ERR_UNSUPPORTED;
   const long long gmax = (long long)per_sm * sm_count_tc();
   const int grid = (int)(h->g.Vc < gmax ? h->g.Vc : gmax);
-  TcApplyArgs a{(const bf16*)h->Dtc, h->nbr, (const float2*)x, (float2*)y, (float2*)vout, xscale, skip, h->err, h->g, ns};
+  TcApplyArgs a{(const bf16*)h->Dtc, (const bf16*)h->tc_x, h->nbr, (float2*)y, skip, h->err, h->g, ns, xpitch};
   apply_tc_kernel<NRHS><<<grid, threads, smem, st>>>(a);
   AMG_LAUNCH_CHECK();
   h->launches++;
@@ -565,6 +588,10 @@ amg_status amg_internal_tc_prepare(amg_coarse* h, cudaStream_t st) {
     AMG_CUDA_TRY(cudaMalloc(&h->Dtc, n * sizeof(bf16)));
     dc_to_bf16_kernel<<<4 * 152, 256, 0, st>>>(h->Dc64, (bf16*)h->Dtc, h->g.nc, h->g.Vc * 9);
     AMG_LAUNCH_CHECK();
+    // BF16 planes of the apply's input, sized for the largest supported column count <= max_nrhs
+    const int nmax = h->p.max_nrhs >= 16 ? 16 : (h->p.max_nrhs + 3) / 4 * 4;
+    h->tc_xbytes = (size_t)h->g.Vc * tc_xpitch(h->g, nmax) * sizeof(bf16);
+    AMG_CUDA_TRY(cudaMalloc(&h->tc_x, h->tc_xbytes));
   }
   if (h->p.r_prec == AMG_BF16) {
     const Geom& g = h->g;
@@ -581,7 +608,8 @@ amg_status amg_internal_tc_prepare(amg_coarse* h, cudaStream_t st) {
 void amg_internal_free_tc(amg_coarse* h) {
   cudaFree(h->Dtc);
   cudaFree(h->Rtc);
-  h->Dtc = h->Rtc = nullptr;
+  cudaFree(h->tc_x);
+  h->Dtc = h->Rtc = h->tc_x = nullptr;
 }
 
 amg_status amg_internal_export_stored(amg_coarse* h, double2* out) {
