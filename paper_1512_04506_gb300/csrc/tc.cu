@@ -1,17 +1,23 @@
-// Multi-right-hand-side coarse operator on the tensor cores: y_c = D_c x_c for nrhs = 4, 8, 12 or 16
-// right-hand sides with D_c stored as BF16 Re/Im planes and FP32 accumulation (the serving form of
-// Alg. 2's coarse-operator application; Sec. 3 stores D_c in half precision).
+// Multi-right-hand-side forms of Alg. 2 on the tensor cores (mma.sync m16n8k16, BF16 operands,
+// FP32 accumulation) for nrhs = 4, 8, 12 or 16 right-hand sides:
+//   coarse apply   y_c = D_c x_c   (D_c in BF16 Re/Im planes; Sec. 3 stores D_c in half precision)
+//   restriction    y_c = R y       (R in BF16 Re/Im planes, y BF16)
+//   prolongation   x   = R^dag x_c (x BF16)
 //
-// Complex products become one real product per stencil block d:
-//     [Y_re | Y_im] += [A_re | A_im] . [[X_re, X_im], [-X_im, X_re]]
-// with A = D_c[i][d] (nc x nc) and X = x_c(nbr(i, d)) (nc x nrhs), so M = nc, K = 2 nc and
-// N = 2 nrhs.  The N axis is ordered in groups of 8 columns (Re of 4 right-hand sides, then Im of
-// the same 4), so each 16x8 accumulator tile holds complete complex outputs.  A comes from the
-// D_c stream (cp.async.bulk into an mbarrier ring, as in stream.cu); X is converted to BF16 once
-// per call into padded BF16 planes (xc_to_planes_kernel), and the producer warp copies, next to
-// each stencil block D_c[i][d], the planes of the neighbour nbr(i, d) into the same stage, so the
-// consumers only issue tensor-core instructions.  Warp w of the consumers owns rows 16 w .. 16 w + 15
-// of the site's output and all N columns.
+// Complex products.  One operand is a pair of real planes (P_re, P_im); the other stays
+// complex-interleaved (rows or columns alternate Re, Im of the same right-hand side), so
+//   out = P_re . V + P_im . V'
+// where V' is V with every (Re, Im) pair replaced by (-Im, Re) (for the product with R^dag, by
+// (Im, -Re)).  The pair partner sits in the lane four places away in an mma fragment, so V' costs
+// one shuffle and a sign flip per fragment register, and the accumulator holds complete complex
+// outputs.
+//
+// Shared-memory layouts are chosen so that every ldmatrix phase (8 rows of 16 bytes) touches eight
+// different 16-byte bank groups:
+//   * BF16 rows of D_c and R (stored that way in HBM by the setup): the 16-byte pieces of row r are
+//     rotated by rot(r) (tc_rot below);
+//   * vectors: rows (apply) or sites (restriction) are placed an odd number of 16-byte units apart.
+// All operands arrive by cp.async.bulk into an mbarrier ring filled by one producer warp (pipe.cuh).
 #include "amg_internal.cuh"
 #include "pipe.cuh"
 
@@ -27,35 +33,88 @@ __device__ inline void mma_bf16(float (&c)[4], const unsigned (&a)[4], unsigned 
       : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
-__device__ inline unsigned lds32(const bf16* p) { return *reinterpret_cast<const unsigned*>(p); }
+__device__ inline void ldsm_x4(unsigned (&r)[4], const void* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(smem_addr(p)));
+}
+__device__ inline void ldsm_x2(unsigned& r0, unsigned& r1, const void* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];" : "=r"(r0), "=r"(r1) : "r"(smem_addr(p)));
+}
+__device__ inline void ldsm_x4_trans(unsigned (&r)[4], const void* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(smem_addr(p)));
+}
+__device__ inline void ldsm_x2_trans(unsigned& r0, unsigned& r1, const void* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];" : "=r"(r0), "=r"(r1) : "r"(smem_addr(p)));
+}
+
+// Rotation of the 16-byte pieces of BF16 row r in a row of P pieces (P = 2, 4, 6 or 8): piece c is
+// stored at position (c + tc_rot(r, P)) % P.  For 8 consecutive rows r0 .. r0 + 7 (r0 a multiple of
+// 8) and any fixed c, the stored units r P + position are distinct modulo 8.
+__host__ __device__ inline int tc_rot(int r, int P) {
+  return P == 8 ? (r & 7) : (P == 4 ? ((r >> 1) & 3) : ((r >> 2) & 1));
+}
+__host__ __device__ inline int tc_pos(int r, int c, int P) { return (c + tc_rot(r, P)) % P; }
+
+// (Re, Im) partner exchange: lane (g, tq) <-> lane (g ^ 1, tq)
+__device__ inline unsigned partner(unsigned v) { return __shfl_xor_sync(0xffffffffu, v, 4); }
+__device__ inline float partnerf(float v) { return __shfl_xor_sync(0xffffffffu, v, 4); }
+constexpr unsigned kNeg2 = 0x80008000u;  // sign bits of two packed BF16
+
+__device__ inline unsigned pack_bf16(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  unsigned u;
+  memcpy(&u, &v, 4);
+  return u;
+}
+
+int sm_count_tc() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 152;
+  }
+  return n;
+}
+
+// ------------------------------------------------------------------ coarse apply
+// Per coarse site i and stencil block d the stage holds D_c[i][d] (2 planes x nc rows x nc BF16,
+// rotated pieces) followed by the BF16 coarse vector of nbr(i, d): nc rows of nrhs (Re, Im) pairs,
+// row pitch tc_xunits(nrhs) 16-byte units (odd).  A = D plane (M = nc, K = nc), B = x rows (K = nc,
+// N = 2 nrhs interleaved), B' from B by the partner exchange.  Consumer warp w owns output rows
+// 16 w .. 16 w + 15 of every site and all right-hand sides.
+
+__host__ __device__ inline int tc_xunits(int nrhs) {
+  const int pieces = nrhs / 4;
+  return pieces + ((pieces & 1) ? 0 : 1);
+}
 
 struct TcApplyArgs {
-  const bf16* D;   // [Vc][9][2][nc][nc]: Re plane then Im plane, row-major (row a, column b)
-  const bf16* X;   // [Vc][xpitch]: the coarse vector in BF16 planes, see xc_to_planes_kernel
+  const bf16* D;   // [Vc][9][2][nc][nc] BF16 planes, rows with rotated pieces
+  const bf16* X;   // [Vc][nc][xunits * 8] BF16 (Re, Im) pairs, see xc_to_bf16_kernel
   const int* nbr;
   float2* y;
   const int* skip;
   unsigned* err;
   Geom g;
-  int ns, xpitch;
+  int ns;
 };
 
-// Coarse vector (FP32, [Vc][nc][nrhs], optionally times xscale[r]; the (scaled) FP32 vector is also
-// stored to vout when given) -> BF16 planes per site: plane p (0 Re, 1 Im) at offset p * (nrhs (nc + 8) + 32),
-// row r of length nc + 8 (8 pad); the paddings put the two planes and consecutive rows on
-// different shared-memory banks once a site's block is copied to shared memory.
+// Coarse vector (FP32 [Vc][nc][nrhs], optionally times xscale[r]; the (scaled) FP32 vector is also
+// stored to vout when given) -> BF16 rows [Vc][nc][xunits * 8], round to nearest even.
 template <int NRHS>
-__global__ void xc_to_planes_kernel(const float2* __restrict__ x, bf16* __restrict__ X, int nc, long long Vc,
-                                    int xpitch, const double* __restrict__ xscale, float2* __restrict__ vout,
-                                    const int* __restrict__ skip) {
+__global__ void xc_to_bf16_kernel(const float2* __restrict__ x, __nv_bfloat162* __restrict__ X, long long rows,
+                                  const double* __restrict__ xscale, float2* __restrict__ vout,
+                                  const int* __restrict__ skip) {
   if (skip && *skip) return;
-  const int prow = nc + 8, pplane = NRHS * prow + 32;
-  const long long total = Vc * nc * NRHS;
+  constexpr int pitch = 4 * (NRHS / 4 + ((NRHS / 4) & 1 ? 0 : 1));  // (Re, Im) pairs per row
+  const long long total = rows * NRHS;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
     const int r = (int)(e % NRHS);
-    const long long ib = e / NRHS;
-    const int b = (int)(ib % nc);
-    const long long i = ib / nc;
     float2 v = x[e];
     if (xscale) {
       const float f = (float)xscale[r];
@@ -63,24 +122,22 @@ __global__ void xc_to_planes_kernel(const float2* __restrict__ x, bf16* __restri
       v.y *= f;
     }
     if (vout) vout[e] = v;
-    bf16* site = X + i * xpitch;
-    site[r * prow + b] = __float2bfloat16_rn(v.x);
-    site[pplane + r * prow + b] = __float2bfloat16_rn(v.y);
+    X[(e / NRHS) * pitch + r] = __floats2bfloat162_rn(v.x, v.y);
   }
 }
 
 template <int NRHS>
-__global__ void __launch_bounds__(160) apply_tc_kernel(const TcApplyArgs a) {
-  constexpr int NT = NRHS / 4;  // n-tiles of 8 columns
+__global__ void __launch_bounds__(160, 1) apply_tc_kernel(const TcApplyArgs a) {
+  constexpr int NT = NRHS / 4;  // n-tiles: 8 columns = 4 right-hand sides x (Re, Im)
+  constexpr int XU = NRHS / 4 + ((NRHS / 4) & 1 ? 0 : 1);
   if (a.skip && *a.skip) return;
   extern __shared__ __align__(128) unsigned char sm[];
   Pipe* pp = reinterpret_cast<Pipe*>(sm);
-  const int nc = a.g.nc, ns = a.ns, mt_count = nc / 16;
+  const int nc = a.g.nc, ns = a.ns, P = nc / 8;
   const unsigned dbytes = (unsigned)(2 * nc * nc * sizeof(bf16));
-  const unsigned xbytes = (unsigned)(a.xpitch * sizeof(bf16));
-  const unsigned chunk = dbytes + xbytes;  // stencil block d of D_c and the neighbour's planes
+  const unsigned xbytes = (unsigned)(nc * XU * 16);
+  const unsigned chunk = dbytes + xbytes;
   unsigned char* stages = sm + kPipeBytes;
-  const int xrow = nc + 8, xplane = NRHS * xrow + 32;
   const int ncw = (blockDim.x - 32) >> 5;
   if (threadIdx.x == 0) {
     for (int s = 0; s < ns; ++s) {
@@ -106,22 +163,27 @@ __global__ void __launch_bounds__(160) apply_tc_kernel(const TcApplyArgs a) {
           mbar_expect_tx(&pp->full[s], chunk);
           unsigned char* st = stages + (size_t)s * chunk;
           bulk_load(st, a.D + (i * 9 + d) * 2LL * nc * nc, dbytes, &pp->full[s]);
-          bulk_load(st + dbytes, a.X + (long long)a.nbr[i * 9 + d] * a.xpitch, xbytes, &pp->full[s]);
+          bulk_load(st + dbytes, reinterpret_cast<const unsigned char*>(a.X) + (long long)a.nbr[i * 9 + d] * xbytes,
+                    xbytes, &pp->full[s]);
         }
       }
       drain(pp, c, ns);
     }
     return;
   }
-  const int t = threadIdx.x - 32, w = t >> 5, lane = t & 31;
-  const int g = lane >> 2, tq = lane & 3;
+  const int w = (threadIdx.x - 32) >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 2, tq = lane & 3, q = lane >> 3, li = lane & 7;
+  const bool even = !(g & 1);
+  // ldmatrix row of this lane: A (non-trans) matrix q = rows 8 (q & 1) .., pieces + (q >> 1);
+  // B (trans) matrix q = k rows 8 (q & 1) .., n-tile + (q >> 1)
+  const int arow = w * 16 + 8 * (q & 1) + li;
   long long c = 0;
   for (long long i = blockIdx.x; i < Vc; i += gridDim.x) {
     float acc[NT][4];
 #pragma unroll
-    for (int q = 0; q < NT; ++q)
+    for (int t = 0; t < NT; ++t)
 #pragma unroll
-      for (int u = 0; u < 4; ++u) acc[q][u] = 0.f;
+      for (int u = 0; u < 4; ++u) acc[t][u] = 0.f;
     for (int d = 0; d < 9; ++d, ++c) {
       const int s = (int)(c % ns);
       bool ok = !pp->abort;
@@ -129,82 +191,64 @@ __global__ void __launch_bounds__(160) apply_tc_kernel(const TcApplyArgs a) {
         abort_cta(pp, a.err);
         ok = false;
       }
-      if (ok && w < mt_count) {
-        const bf16* Ablk = reinterpret_cast<const bf16*>(stages + (size_t)s * chunk);
-        const bf16* xs = reinterpret_cast<const bf16*>(stages + (size_t)s * chunk + dbytes);
-        const int row0 = w * 16 + g;
-        for (int kk = 0; kk < 2 * (nc / 16); ++kk) {
-          const int p = kk / (nc / 16), k0 = (kk % (nc / 16)) * 16;  // p = 0: A_re, 1: A_im
-          const bf16* P = Ablk + (size_t)p * nc * nc;
-          unsigned af[4];
-          af[0] = lds32(P + (size_t)row0 * nc + k0 + 2 * tq);
-          af[1] = lds32(P + (size_t)(row0 + 8) * nc + k0 + 2 * tq);
-          af[2] = lds32(P + (size_t)row0 * nc + k0 + 8 + 2 * tq);
-          af[3] = lds32(P + (size_t)(row0 + 8) * nc + k0 + 8 + 2 * tq);
+      ok = __all_sync(0xffffffffu, ok);  // the fragment loads and mma below need the whole warp
+      if (ok) {
+        const unsigned char* Ds = stages + (size_t)s * chunk;
+        const unsigned char* Xs = Ds + dbytes;
+        for (int ks = 0; ks < nc / 16; ++ks) {
+          unsigned are[4], aim[4];
+          const unsigned char* ap = Ds + (size_t)arow * nc * 2 + tc_pos(arow, 2 * ks + (q >> 1), P) * 16;
+          ldsm_x4(are, ap);
+          ldsm_x4(aim, ap + (size_t)nc * nc * 2);
+          const unsigned char* bp = Xs + (size_t)(16 * ks + 8 * (q & 1) + li) * XU * 16;
 #pragma unroll
-          for (int q = 0; q < NT; ++q) {
-            // column g of tile q: half = g / 4 (0: Re output, 1: Im output), rhs r = 4 q + g % 4
-            const int half = g >> 2, r = 4 * q + (g & 3);
-            const int sp = (p == half) ? 0 : 1;  // X_re or X_im
-            const bf16* xb = xs + (size_t)sp * xplane + (size_t)r * xrow + k0 + 2 * tq;
-            unsigned b0 = lds32(xb), b1 = lds32(xb + 8);
-            if (p == 1 && half == 0) {
-              b0 ^= 0x80008000u;
-              b1 ^= 0x80008000u;
+          for (int t = 0; t < NT; t += 2) {
+            unsigned b[4];
+            if (t + 1 < NT) {
+              ldsm_x4_trans(b, bp + (t + (q >> 1)) * 16);
+            } else {
+              ldsm_x2_trans(b[0], b[1], bp + t * 16);
+              b[2] = b[3] = 0u;
             }
-            mma_bf16(acc[q], af, b0, b1);
+#pragma unroll
+            for (int v = 0; v < 2 && t + v < NT; ++v) {
+              const unsigned b0 = b[2 * v], b1 = b[2 * v + 1];
+              unsigned p0 = partner(b0), p1 = partner(b1);
+              if (even) {
+                p0 ^= kNeg2;
+                p1 ^= kNeg2;
+              }
+              mma_bf16(acc[t + v], are, b0, b1);
+              mma_bf16(acc[t + v], aim, p0, p1);
+            }
           }
         }
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&pp->empty[s]);
     }
-    // tile q, lane (g, tq): c0, c1 = rows g, cols 2 tq, 2 tq + 1; c2, c3 = row g + 8.
-    // Columns 0..3 are Re of rhs 4q..4q+3, columns 4..7 their Im: lanes tq = 0, 1 hold Re and
-    // receive the Im from lane tq + 2.
-    if (w < mt_count) {
+    // tile t, lane (g, tq): (acc0, acc1) = (Re, Im) of row 16 w + g, right-hand side 4 t + tq;
+    // (acc2, acc3) the same for row 16 w + g + 8
+    const int row = w * 16 + g;
 #pragma unroll
-      for (int q = 0; q < NT; ++q) {
-        const float i0 = __shfl_down_sync(0xffffffffu, acc[q][0], 2);
-        const float i1 = __shfl_down_sync(0xffffffffu, acc[q][1], 2);
-        const float i2 = __shfl_down_sync(0xffffffffu, acc[q][2], 2);
-        const float i3 = __shfl_down_sync(0xffffffffu, acc[q][3], 2);
-        if (tq < 2) {
-          const int r = 4 * q + 2 * tq;
-          const int row = w * 16 + g;
-          float4* y0 = reinterpret_cast<float4*>(a.y + (i * nc + row) * NRHS + r);
-          float4* y1 = reinterpret_cast<float4*>(a.y + (i * nc + row + 8) * NRHS + r);
-          *y0 = make_float4(acc[q][0], i0, acc[q][1], i1);
-          *y1 = make_float4(acc[q][2], i2, acc[q][3], i3);
-        }
-      }
+    for (int t = 0; t < NT; ++t) {
+      a.y[(i * nc + row) * NRHS + 4 * t + tq] = make_float2(acc[t][0], acc[t][1]);
+      a.y[(i * nc + row + 8) * NRHS + 4 * t + tq] = make_float2(acc[t][2], acc[t][3]);
     }
   }
 }
 
-int sm_count_tc() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 152;
-  }
-  return n;
-}
-
 // ------------------------------------------------------------------ R and P on the tensor cores
-// R in BF16 planes, tiled for the tensor cores: Rtc[blk][c][h][p][j][48], chunk c covering the
-// aggregate dofs n = 48 c .. 48 c + 47 (block-local sites 8 c .. 8 c + 7), p = 0 (Re), 1 (Im).
-// Restriction:  [Yc_re | Yc_im] = [R_re | R_im] . [[Y_re, Y_im], [-Y_im, Y_re]]  (M = ntv, K = 2 n)
-// Prolongation: [X_re | X_im] = [Q_re | Q_im] . [[c_re, c_im], [-c_im, c_re]]   (M = n, K = 2 ntv)
-// with Q = R^dagger, Q_re = R_re^T, Q_im = -R_im^T.
-
-__device__ inline void ldsm_x4_trans(unsigned (&r)[4], const bf16* p) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(smem_addr(p)));
-}
+// R in BF16 planes, tiled in chunks of 8 block-local sites: Rtc[blk][c][h][p][j][48] with
+// p = 0 (Re), 1 (Im).  Within a chunk the 48 aggregate dofs n = 6 sl + d' (site sl = 0..7 of the
+// chunk, spin-colour d' = 0..5 of chirality h) are ordered k = 8 d' + sl, so a 16-byte piece of a row
+// is one d' over the 8 sites; pieces are rotated by tc_rot(j, 6).
+//
+// Restriction, per aggregate: Yc^T = Y^T . R^T with A = Y^T (rows: right-hand side x (Re, Im),
+// k = 8 d' + sl), B = R plane (k, n = j); A' from A by the partner exchange.  The fine-vector rows
+// of the chunk's sites are copied to the stage site by site, 48 nrhs + 16 bytes apart.
+// Prolongation, per aggregate: X^T = C^T . conj(R) with A = C^T from x_c (FP32 -> BF16 in
+// registers, once per block) and B = R plane (k = j, n = 8 d' + sl).
 
 struct TcRPArgs {
   const bf16* R;       // Rtc
@@ -212,27 +256,20 @@ struct TcRPArgs {
   void* out;           // restrict: coarse FP32 y_c; prolong: fine BF16 x
   unsigned* err;
   Geom g;
-  int ns, run;         // run = consecutive sites of a chunk that are consecutive on the lattice
+  int ns;
 };
 
-// Block-local sites 8c .. 8c+7 as (8 / run) runs of `run` lattice-consecutive sites.
-__device__ inline long long chunk_site(const Geom& g, long long blk, int c, int u, int run) {
-  return block_site_fast(g, block_origin(g, blk), 8 * c + u * run);
-}
-
 template <int NRHS>
-__global__ void __launch_bounds__(160) restrict_tc_kernel(const TcRPArgs a) {
-  constexpr int NT = NRHS / 4;
+__global__ void __launch_bounds__(160, 1) restrict_tc_kernel(const TcRPArgs a) {
+  constexpr int MT = (NRHS + 7) / 8;      // m-tiles per aggregate (16 rows = 8 rhs x (Re, Im))
+  constexpr int PIECES = NRHS / 4;        // 16-byte pieces of one fine-vector row
+  constexpr int YSITE = 48 * NRHS + 16;   // stage bytes per site (odd number of 16-byte units)
   extern __shared__ __align__(128) unsigned char sm[];
   Pipe* pp = reinterpret_cast<Pipe*>(sm);
-  const int ntv = a.g.ntv, ns = a.ns, run = a.run, cpb = (int)(a.g.Vb / 8);  // chunks per block
-  const int mts = (ntv + 15) / 16;                                          // m-tiles per chirality
+  const int ntv = a.g.ntv, ns = a.ns, cpb = (int)(a.g.Vb / 8), NTL = ntv / 8;
   const unsigned rbytes = (unsigned)(2 * 2 * ntv * 48 * sizeof(bf16));
-  const unsigned ybytes = (unsigned)(8 * 12 * NRHS * 4);
-  const unsigned chunk = rbytes + ybytes + 1024;  // slack: padded A rows read past the last plane
+  const unsigned chunk = rbytes + 8 * YSITE;
   unsigned char* stages = sm + kPipeBytes;
-  const int yrow = 48 + 8, yplane = 2 * NRHS * yrow + 32;  // Ybuf[buf][plane][h][r][n]
-  bf16* ybuf = reinterpret_cast<bf16*>(stages + (size_t)ns * chunk);
   const int ncw = (blockDim.x - 32) >> 5;
   if (threadIdx.x == 0) {
     for (int s = 0; s < ns; ++s) {
@@ -244,11 +281,12 @@ __global__ void __launch_bounds__(160) restrict_tc_kernel(const TcRPArgs a) {
   }
   __syncthreads();
   const long long nblk = a.g.Vc;
-  const __nv_bfloat162* Y = reinterpret_cast<const __nv_bfloat162*>(a.in);
+  const unsigned char* Y = reinterpret_cast<const unsigned char*>(a.in);
   if (threadIdx.x < 32) {
     if (threadIdx.x == 0) {
       long long c = 0;
       for (long long blk = blockIdx.x; blk < nblk && !pp->abort; blk += gridDim.x) {
+        const long long origin = block_origin(a.g, blk);
         for (int cc = 0; cc < cpb; ++cc, ++c) {
           const int s = (int)(c % ns);
           const long long q = c / ns;
@@ -256,13 +294,12 @@ __global__ void __launch_bounds__(160) restrict_tc_kernel(const TcRPArgs a) {
             abort_cta(pp, a.err);
             break;
           }
-          mbar_expect_tx(&pp->full[s], rbytes + ybytes);
+          mbar_expect_tx(&pp->full[s], rbytes + 8 * 48 * NRHS);
           unsigned char* st = stages + (size_t)s * chunk;
           bulk_load(st, a.R + (blk * cpb + cc) * (long long)(rbytes / sizeof(bf16)), rbytes, &pp->full[s]);
-          const unsigned rb = (unsigned)(run * 12 * NRHS * 4);
-          for (int u = 0; u < 8 / run; ++u) {
-            const long long site = chunk_site(a.g, blk, cc, u, run);
-            bulk_load(st + rbytes + u * rb, Y + site * 12 * NRHS, rb, &pp->full[s]);
+          for (int sl = 0; sl < 8; ++sl) {
+            const long long site = block_site_fast(a.g, origin, 8 * cc + sl);
+            bulk_load(st + rbytes + sl * YSITE, Y + site * 48 * NRHS, 48 * NRHS, &pp->full[s]);
           }
         }
       }
@@ -270,16 +307,20 @@ __global__ void __launch_bounds__(160) restrict_tc_kernel(const TcRPArgs a) {
     }
     return;
   }
-  const int t = threadIdx.x - 32, nct = blockDim.x - 32, w = t >> 5, lane = t & 31;
-  const int g = lane >> 2, tq = lane & 3;
-  const int hw = w / mts, mt = w % mts;  // warp -> (chirality, m-tile)
+  const int w = (threadIdx.x - 32) >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 2, tq = lane & 3, q = lane >> 3, li = lane & 7;
+  const bool even = !(g & 1);
+  const int hw = w / MT, mt = w % MT;  // warp -> (chirality, m-tile)
+  const bool half = 2 * mt + 1 >= PIECES;  // m-tile with right-hand sides 8 mt .. 8 mt + 3 only
+  // A (trans) matrix q: piece 2 mt + (q & 1) (clamped), d' = 2 ks + (q >> 1), site li
+  const int apiece = (2 * mt + (q & 1)) < PIECES ? 2 * mt + (q & 1) : PIECES - 1;
   long long c = 0;
   for (long long blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
-    float acc[NT][4];
+    float acc[4][4];
 #pragma unroll
-    for (int q = 0; q < NT; ++q)
+    for (int t = 0; t < 4; ++t)
 #pragma unroll
-      for (int u = 0; u < 4; ++u) acc[q][u] = 0.f;
+      for (int u = 0; u < 4; ++u) acc[t][u] = 0.f;
     for (int cc = 0; cc < cpb; ++cc, ++c) {
       const int s = (int)(c % ns);
       bool ok = !pp->abort;
@@ -287,79 +328,75 @@ __global__ void __launch_bounds__(160) restrict_tc_kernel(const TcRPArgs a) {
         abort_cta(pp, a.err);
         ok = false;
       }
-      const unsigned char* st = stages + (size_t)s * chunk;
-      const __nv_bfloat162* Ys = reinterpret_cast<const __nv_bfloat162*>(st + rbytes);
-      bf16* yb = ybuf + (size_t)(c & 1) * 2 * yplane;
-      // Y of the chunk into planes yb[plane][h][r][n] (n = aggregate dof within the chunk)
-      for (int e = t; e < 8 * 12 * NRHS && ok; e += nct) {
-        const int r = e % NRHS, dofs = e / NRHS, sl = dofs / 12, dof = dofs % 12;
-        const int h = dof / 6, n = sl * 6 + dof % 6;
-        const __nv_bfloat162 v = Ys[e];
-        yb[((size_t)h * NRHS + r) * yrow + n] = v.x;
-        yb[yplane + ((size_t)h * NRHS + r) * yrow + n] = v.y;
-      }
-      consumer_sync(nct);
-      if (ok && hw < 2) {
-        const bf16* Rb = reinterpret_cast<const bf16*>(st);
-        const int row0 = mt * 16 + g;
-        for (int kk = 0; kk < 6; ++kk) {
-          const int p = kk / 3, k0 = (kk % 3) * 16;  // p = 0: R_re, 1: R_im; k = n within the chunk
-          const bf16* P = Rb + (size_t)((hw * 2 + p) * ntv) * 48;
-          unsigned af[4];
-          af[0] = lds32(P + (size_t)row0 * 48 + k0 + 2 * tq);
-          af[1] = lds32(P + (size_t)(row0 + 8) * 48 + k0 + 2 * tq);
-          af[2] = lds32(P + (size_t)row0 * 48 + k0 + 8 + 2 * tq);
-          af[3] = lds32(P + (size_t)(row0 + 8) * 48 + k0 + 8 + 2 * tq);
+      ok = __all_sync(0xffffffffu, ok);  // the fragment loads and mma below need the whole warp
+      if (ok) {
+        const unsigned char* st = stages + (size_t)s * chunk;
+        const unsigned char* Ys = st + rbytes;
 #pragma unroll
-          for (int q = 0; q < NT; ++q) {
-            const int half = g >> 2, r = 4 * q + (g & 3);
-            const int sp = (p == half) ? 0 : 1;
-            const bf16* xb = yb + (size_t)sp * yplane + ((size_t)hw * NRHS + r) * yrow + k0 + 2 * tq;
-            unsigned b0 = lds32(xb), b1 = lds32(xb + 8);
-            if (p == 1 && half == 0) {
-              b0 ^= 0x80008000u;
-              b1 ^= 0x80008000u;
+        for (int ks = 0; ks < 3; ++ks) {
+          unsigned af[4], ap[4];
+          ldsm_x4_trans(af, Ys + li * YSITE + (6 * hw + 2 * ks + (q >> 1)) * (NRHS * 4) + apiece * 16);
+          if (half) af[1] = af[3] = 0u;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            ap[u] = partner(af[u]);
+            if (even) ap[u] ^= kNeg2;
+          }
+#pragma unroll
+          for (int p = 0; p < 2; ++p) {
+            const unsigned char* Rp = st + (size_t)((hw * 2 + p) * ntv) * 96;
+#pragma unroll
+            for (int t = 0; t < 4; t += 2) {
+              if (t >= NTL) break;
+              unsigned b[4];
+              // B (non-trans) matrix q: rows j = 8 (t + (q >> 1)) + li, k-piece 2 ks + (q & 1)
+              if (t + 1 < NTL) {
+                const int j = 8 * (t + (q >> 1)) + li;
+                ldsm_x4(b, Rp + (size_t)j * 96 + tc_pos(j, 2 * ks + (q & 1), 6) * 16);
+              } else {
+                const int j = 8 * t + li;
+                ldsm_x2(b[0], b[1], Rp + (size_t)j * 96 + tc_pos(j, 2 * ks + (q & 1), 6) * 16);
+                b[2] = b[3] = 0u;
+              }
+#pragma unroll
+              for (int v = 0; v < 2; ++v) {
+                if (t + v >= NTL) break;
+                mma_bf16(acc[t + v], p == 0 ? af : ap, b[2 * v], b[2 * v + 1]);
+              }
             }
-            mma_bf16(acc[q], af, b0, b1);
           }
         }
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&pp->empty[s]);
     }
-    // rows j = mt*16 + g (+8) < ntv of chirality hw: y_c[blk][hw][j][r]
-    if (hw < 2) {
-      float2* yc = reinterpret_cast<float2*>(a.out);
+    // tile t, lane (g, tq): rows g (right-hand side 8 mt + g / 2, Re for even g, Im for odd g) and
+    // g + 8 (right-hand side + 4); columns j = 8 t + 2 tq, + 1.  Even lanes write column 2 tq, odd
+    // lanes column 2 tq + 1, after exchanging one value with the partner.
+    float2* yc = reinterpret_cast<float2*>(a.out);
 #pragma unroll
-      for (int q = 0; q < NT; ++q) {
-        const float i0 = __shfl_down_sync(0xffffffffu, acc[q][0], 2);
-        const float i1 = __shfl_down_sync(0xffffffffu, acc[q][1], 2);
-        const float i2 = __shfl_down_sync(0xffffffffu, acc[q][2], 2);
-        const float i3 = __shfl_down_sync(0xffffffffu, acc[q][3], 2);
-        if (tq < 2) {
-          const int r = 4 * q + 2 * tq, j0 = mt * 16 + g;
-          if (j0 < ntv)
-            *reinterpret_cast<float4*>(yc + ((blk * 2 + hw) * ntv + j0) * NRHS + r) =
-                make_float4(acc[q][0], i0, acc[q][1], i1);
-          if (j0 + 8 < ntv)
-            *reinterpret_cast<float4*>(yc + ((blk * 2 + hw) * ntv + j0 + 8) * NRHS + r) =
-                make_float4(acc[q][2], i2, acc[q][3], i3);
-        }
+    for (int t = 0; t < 4; ++t) {
+      if (t >= NTL) break;
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const float x0 = acc[t][2 * u], x1 = acc[t][2 * u + 1];
+        const float recv = partnerf(even ? x1 : x0);
+        const int r = 8 * mt + (g >> 1) + 4 * u, j = 8 * t + 2 * tq + (g & 1);
+        if (r < NRHS)
+          yc[((blk * 2 + hw) * ntv + j) * NRHS + r] = even ? make_float2(x0, recv) : make_float2(recv, x1);
       }
     }
   }
 }
 
 template <int NRHS>
-__global__ void __launch_bounds__(224) prolong_tc_kernel(const TcRPArgs a) {
-  constexpr int NT = NRHS / 4;
+__global__ void __launch_bounds__(160, 1) prolong_tc_kernel(const TcRPArgs a) {
+  constexpr int MT = (NRHS + 7) / 8;
   extern __shared__ __align__(128) unsigned char sm[];
   Pipe* pp = reinterpret_cast<Pipe*>(sm);
-  const int ntv = a.g.ntv, ns = a.ns, run = a.run, cpb = (int)(a.g.Vb / 8);
+  const int ntv = a.g.ntv, ns = a.ns, cpb = (int)(a.g.Vb / 8);
   const unsigned chunk = (unsigned)(2 * 2 * ntv * 48 * sizeof(bf16));
   unsigned char* stages = sm + kPipeBytes;
-  const int crow = ntv + 8, cplane = 2 * NRHS * crow + 32;  // cbuf[plane][h][r][j]
-  bf16* cbuf = reinterpret_cast<bf16*>(stages + (size_t)ns * chunk);
   const int ncw = (blockDim.x - 32) >> 5;
   if (threadIdx.x == 0) {
     for (int s = 0; s < ns; ++s) {
@@ -391,21 +428,36 @@ __global__ void __launch_bounds__(224) prolong_tc_kernel(const TcRPArgs a) {
     }
     return;
   }
-  const int t = threadIdx.x - 32, nct = blockDim.x - 32, w = t >> 5, lane = t & 31;
-  const int g = lane >> 2, tq = lane & 3;
-  const int hw = w / 3, mt = w % 3;  // warp -> (chirality, m-tile of 16 dofs)
+  const int w = (threadIdx.x - 32) >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 2, tq = lane & 3, q = lane >> 3, li = lane & 7;
+  const bool even = !(g & 1);
+  const int hw = w / MT, mt = w % MT;
+  const int KS = (ntv + 15) / 16;  // k-steps over j (ntv = 8, 16, 24 or 32)
   const float2* xc = reinterpret_cast<const float2*>(a.in);
   __nv_bfloat162* X = reinterpret_cast<__nv_bfloat162*>(a.out);
   long long c = 0;
   for (long long blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
-    consumer_sync(nct);
-    for (int e = t; e < 2 * ntv * NRHS; e += nct) {
-      const int r = e % NRHS, hj = e / NRHS, h = hj / ntv, j = hj % ntv;
-      const float2 v = xc[(blk * 2 * ntv + hj) * NRHS + r];
-      cbuf[((size_t)h * NRHS + r) * crow + j] = __float2bfloat16_rn(v.x);
-      cbuf[cplane + ((size_t)h * NRHS + r) * crow + j] = __float2bfloat16_rn(v.y);
-    }
-    consumer_sync(nct);
+    // A = C^T and A' (rows: right-hand side 8 mt + g / 2 (+ 4), Re / Im; k = j) from x_c
+    unsigned af[2][4], ap[2][4];
+#pragma unroll
+    for (int ks = 0; ks < 2; ++ks)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int r = 8 * mt + (g >> 1) + 4 * (u & 1), j0 = 16 * ks + 2 * tq + 8 * (u >> 1);
+        float lo = 0.f, hi = 0.f, plo = 0.f, phi = 0.f;
+        if (ks < KS && r < NRHS) {
+          const float2* src = xc + ((blk * 2 + hw) * ntv + j0) * NRHS + r;
+          const float2 v0 = j0 < ntv ? src[0] : make_float2(0.f, 0.f);
+          const float2 v1 = j0 + 1 < ntv ? src[NRHS] : make_float2(0.f, 0.f);
+          lo = even ? v0.x : v0.y;
+          hi = even ? v1.x : v1.y;
+          plo = even ? v0.y : -v0.x;  // A' rows: (Re -> Im, Im -> -Re) for the product with conj(R)
+          phi = even ? v1.y : -v1.x;
+        }
+        af[ks][u] = pack_bf16(lo, hi);
+        ap[ks][u] = pack_bf16(plo, phi);
+      }
+    const long long origin = block_origin(a.g, blk);
     for (int cc = 0; cc < cpb; ++cc, ++c) {
       const int s = (int)(c % ns);
       bool ok = !pp->abort;
@@ -413,66 +465,48 @@ __global__ void __launch_bounds__(224) prolong_tc_kernel(const TcRPArgs a) {
         abort_cta(pp, a.err);
         ok = false;
       }
-      if (ok && hw < 2) {
-        const bf16* Rb = reinterpret_cast<const bf16*>(stages + (size_t)s * chunk);
-        const long long origin = block_origin(a.g, blk);
-        float acc[NT][4];
+      ok = __all_sync(0xffffffffu, ok);  // the fragment loads and mma below need the whole warp
+      if (ok) {
+        const unsigned char* st = stages + (size_t)s * chunk;
+        float acc[6][4];
 #pragma unroll
-        for (int q = 0; q < NT; ++q)
+        for (int t = 0; t < 6; ++t)
 #pragma unroll
-          for (int u = 0; u < 4; ++u) acc[q][u] = 0.f;
-        for (int k0 = 0; k0 < 2 * ntv; k0 += 16) {
-          // A = [Q_re | Q_im] rows n = mt*16.., columns k = k0..k0+15: four transposed 8x8 tiles
-          const int tile = lane >> 3, kt = k0 + (tile >> 1) * 8 + (lane & 7), n0 = mt * 16 + (tile & 1) * 8;
-          const int pl = kt < ntv ? 0 : 1, j = kt < ntv ? kt : kt - ntv;
-          unsigned af[4];
-          ldsm_x4_trans(af, Rb + ((size_t)(hw * 2 + pl) * ntv + j) * 48 + n0);
-          // Q_im = -R_im^T: negate the registers whose 8 k-columns lie in the R_im plane
-          if (k0 >= ntv) {
-            af[0] ^= 0x80008000u;
-            af[1] ^= 0x80008000u;
-          }
-          if (k0 + 8 >= ntv) {
-            af[2] ^= 0x80008000u;
-            af[3] ^= 0x80008000u;
-          }
+          for (int u = 0; u < 4; ++u) acc[t][u] = 0.f;
 #pragma unroll
-          for (int q = 0; q < NT; ++q) {
-            const int half = g >> 2, r = 4 * q + (g & 3);
-            // B[k][col]: k < ntv (Q_re part): c_re (half 0) / c_im (half 1); k >= ntv: -c_im / c_re
-            unsigned b[2];
+        for (int ks = 0; ks < 2; ++ks) {
+          if (ks >= KS) break;
+          // B (trans) matrix q: rows j = 16 ks + 8 (q & 1) + li (clamped; zeroed past ntv), piece t + (q >> 1)
+          int j = 16 * ks + 8 * (q & 1) + li;
+          const bool jhi_ok = 16 * ks + 8 < ntv;
+          j = j < ntv ? j : ntv - 1;
 #pragma unroll
-            for (int u = 0; u < 2; ++u) {
-              const int k = k0 + 8 * u + 2 * tq, p = k < ntv ? 0 : 1, jj = k < ntv ? k : k - ntv;
-              const int sp = (p == half) ? 0 : 1;
-              b[u] = lds32(cbuf + (size_t)sp * cplane + ((size_t)hw * NRHS + r) * crow + jj);
-              if (p == 1 && half == 0) b[u] ^= 0x80008000u;
+          for (int p = 0; p < 2; ++p) {
+            const unsigned char* Rp = st + (size_t)((hw * 2 + p) * ntv + j) * 96;
+#pragma unroll
+            for (int t = 0; t < 6; t += 2) {
+              unsigned b[4];
+              ldsm_x4_trans(b, Rp + tc_pos(j, t + (q >> 1), 6) * 16);
+              if (!jhi_ok) b[1] = b[3] = 0u;
+              mma_bf16(acc[t], p == 0 ? af[ks] : ap[ks], b[0], b[1]);
+              mma_bf16(acc[t + 1], p == 0 ? af[ks] : ap[ks], b[2], b[3]);
             }
-            mma_bf16(acc[q], af, b[0], b[1]);
           }
         }
-        // rows n = mt*16 + g (+8): aggregate dof of chirality hw within the chunk
+        // tile t (= d'), lane (g, tq): rows g / g + 8 as in A, columns = sites 2 tq, 2 tq + 1
 #pragma unroll
-        for (int q = 0; q < NT; ++q) {
-          const float i0 = __shfl_down_sync(0xffffffffu, acc[q][0], 2);
-          const float i1 = __shfl_down_sync(0xffffffffu, acc[q][1], 2);
-          const float i2 = __shfl_down_sync(0xffffffffu, acc[q][2], 2);
-          const float i3 = __shfl_down_sync(0xffffffffu, acc[q][3], 2);
-          if (tq < 2) {
-            const int r = 4 * q + 2 * tq;
+        for (int t = 0; t < 6; ++t)
 #pragma unroll
-            for (int u = 0; u < 2; ++u) {
-              const int n = mt * 16 + g + 8 * u, sl = n / 6, dof = hw * 6 + n % 6;
+          for (int u = 0; u < 2; ++u) {
+            const float x0 = acc[t][2 * u], x1 = acc[t][2 * u + 1];
+            const float recv = partnerf(even ? x1 : x0);
+            const int r = 8 * mt + (g >> 1) + 4 * u, sl = 2 * tq + (g & 1);
+            if (r < NRHS) {
               const long long site = block_site_fast(a.g, origin, 8 * cc + sl);
-              __nv_bfloat162 v0 = __floats2bfloat162_rn(u ? acc[q][2] : acc[q][0], u ? i2 : i0);
-              __nv_bfloat162 v1 = __floats2bfloat162_rn(u ? acc[q][3] : acc[q][1], u ? i3 : i1);
-              uint2 pk;
-              memcpy(&pk.x, &v0, 4);
-              memcpy(&pk.y, &v1, 4);
-              *reinterpret_cast<uint2*>(X + (site * 12 + dof) * NRHS + r) = pk;
+              X[(site * 12 + 6 * hw + t) * NRHS + r] =
+                  even ? __floats2bfloat162_rn(x0, recv) : __floats2bfloat162_rn(recv, x1);
             }
           }
-        }
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&pp->empty[s]);
@@ -480,7 +514,7 @@ __global__ void __launch_bounds__(224) prolong_tc_kernel(const TcRPArgs a) {
   }
 }
 
-// R64 [blk][h][j][n] (complex double) -> Rtc [blk][c][h][p][j][48] (BF16, round to nearest even)
+// R64 [blk][h][j][n] (complex double) -> Rtc (BF16, round to nearest even)
 __global__ void r_to_tc_kernel(const double2* __restrict__ R, bf16* __restrict__ out, Geom g) {
   const int ntv = g.ntv, nagg = g.nagg, cpb = (int)(g.Vb / 8);
   const long long total = g.Vc * 2LL * ntv * nagg;
@@ -489,30 +523,24 @@ __global__ void r_to_tc_kernel(const double2* __restrict__ R, bf16* __restrict__
     const long long q = e / nagg;
     const int j = (int)(q % ntv), h = (int)((q / ntv) % 2);
     const long long blk = q / (2LL * ntv);
-    const int c = n / 48, nn = n % 48;
+    const int site = n / 6, dp = n % 6, c = site / 8, sl = site % 8;
+    const int off = tc_pos(j, dp, 6) * 8 + sl;
     const double2 v = R[e];
     const long long base = ((blk * cpb + c) * 2 + h) * 2;
-    out[((base + 0) * ntv + j) * 48 + nn] = __double2bfloat16(v.x);
-    out[((base + 1) * ntv + j) * 48 + nn] = __double2bfloat16(v.y);
+    out[((base + 0) * ntv + j) * 48 + off] = __double2bfloat16(v.x);
+    out[((base + 1) * ntv + j) * 48 + off] = __double2bfloat16(v.y);
   }
 }
 
 template <int NRHS, bool RESTRICT>
 amg_status launch_rp_tc(amg_coarse* h, const void* in, void* out, cudaStream_t st) {
   const Geom& g = h->g;
-  const int run = g.B[0] >= 8 ? 8 : g.B[0];
-  const int mts = (g.ntv + 15) / 16;
-  const int threads = RESTRICT ? 32 + 32 * 2 * mts : 32 + 32 * 6;
-  size_t chunk, extra;
-  if (RESTRICT) {
-    chunk = (size_t)2 * 2 * g.ntv * 48 * sizeof(bf16) + 8 * 12 * NRHS * 4 + 1024;
-    extra = (size_t)2 * 2 * (2 * NRHS * (48 + 8) + 32) * sizeof(bf16);
-  } else {
-    chunk = (size_t)2 * 2 * g.ntv * 48 * sizeof(bf16);
-    extra = (size_t)2 * (2 * NRHS * (g.ntv + 8) + 32) * sizeof(bf16);
-  }
-  const int ns = 4;
-  const size_t smem = kPipeBytes + ns * chunk + extra;
+  const int threads = 32 + 64 * ((NRHS + 7) / 8);
+  const size_t rbytes = (size_t)2 * 2 * g.ntv * 48 * sizeof(bf16);
+  const size_t chunk = RESTRICT ? rbytes + 8 * (48 * NRHS + 16) : rbytes;
+  int ns = (int)((60 * 1024) / chunk);
+  ns = ns < 2 ? 2 : (ns > 8 ? 8 : ns);
+  const size_t smem = kPipeBytes + ns * chunk;
   if (smem > 227 * 1024) return AMG_ERR_UNSUPPORTED;
   auto kern = RESTRICT ? restrict_tc_kernel<NRHS> : prolong_tc_kernel<NRHS>;
   AMG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -521,47 +549,54 @@ amg_status launch_rp_tc(amg_coarse* h, const void* in, void* out, cudaStream_t s
   if (per_sm < 1) return AMG_ERR_UNSUPPORTED;
   const long long gmax = (long long)per_sm * sm_count_tc();
   const int grid = (int)(g.Vc < gmax ? g.Vc : gmax);
-  TcRPArgs a{(const bf16*)h->Rtc, in, out, h->err, g, ns, run};
+  TcRPArgs a{(const bf16*)h->Rtc, in, out, h->err, g, ns};
   kern<<<grid, threads, smem, st>>>(a);
   AMG_LAUNCH_CHECK();
   h->launches++;
   return AMG_OK;
 }
 
-// D_c (canonical FP64 [Vc][9][nc][nc]) -> BF16 planes [Vc][9][2][nc][nc], round to nearest even.
+// D_c (canonical FP64 [Vc][9][nc][nc]) -> BF16 planes [Vc][9][2][nc][nc] with rotated row pieces,
+// round to nearest even; bf16_to_dc_kernel is the inverse (for export).
 __global__ void dc_to_bf16_kernel(const double2* __restrict__ Dc, bf16* __restrict__ out, int nc, long long nblk) {
   const long long n2 = (long long)nc * nc, total = nblk * n2;
+  const int P = nc / 8;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
-    const long long blk = e / n2, rem = e % n2;
+    const long long blk = e / n2;
+    const int rem = (int)(e % n2), row = rem / nc, col = rem % nc;
+    const int off = row * nc + tc_pos(row, col / 8, P) * 8 + col % 8;
     const double2 v = Dc[e];
-    out[blk * 2 * n2 + rem] = __double2bfloat16(v.x);
-    out[blk * 2 * n2 + n2 + rem] = __double2bfloat16(v.y);
+    out[blk * 2 * n2 + off] = __double2bfloat16(v.x);
+    out[blk * 2 * n2 + n2 + off] = __double2bfloat16(v.y);
   }
 }
 
 __global__ void bf16_to_dc_kernel(const bf16* __restrict__ in, double2* __restrict__ out, int nc, long long nblk) {
   const long long n2 = (long long)nc * nc, total = nblk * n2;
+  const int P = nc / 8;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
-    const long long blk = e / n2, rem = e % n2;
-    out[e] = make_double2((double)__bfloat162float(in[blk * 2 * n2 + rem]),
-                          (double)__bfloat162float(in[blk * 2 * n2 + n2 + rem]));
+    const long long blk = e / n2;
+    const int rem = (int)(e % n2), row = rem / nc, col = rem % nc;
+    const int off = row * nc + tc_pos(row, col / 8, P) * 8 + col % 8;
+    out[e] = make_double2((double)__bfloat162float(in[blk * 2 * n2 + off]),
+                          (double)__bfloat162float(in[blk * 2 * n2 + n2 + off]));
   }
 }
 
-int tc_xpitch(const Geom& g, int nrhs) { return ((2 * nrhs * (g.nc + 8) + 64) + 7) / 8 * 8; }
+size_t tc_xbytes_per_site(const Geom& g, int nrhs) { return (size_t)g.nc * tc_xunits(nrhs) * 16; }
 
 template <int NRHS>
 amg_status launch_apply_tc(amg_coarse* h, const void* x, void* y, cudaStream_t st, const int* skip,
                            const double* xscale, void* vout) {
   const int nc = h->g.nc;
-  const int xpitch = tc_xpitch(h->g, NRHS);
-  if ((size_t)h->g.Vc * xpitch * sizeof(bf16) > h->tc_xbytes) return AMG_ERR_INVALID_ARG;  // nrhs > max_nrhs
-  xc_to_planes_kernel<NRHS><<<4 * 152, 256, 0, st>>>((const float2*)x, (bf16*)h->tc_x, nc, h->g.Vc, xpitch, xscale,
-                                                     (float2*)vout, skip);
+  const size_t xsite = tc_xbytes_per_site(h->g, NRHS);
+  if ((size_t)h->g.Vc * xsite > h->tc_xbytes) return AMG_ERR_INVALID_ARG;  // nrhs > max_nrhs
+  xc_to_bf16_kernel<NRHS><<<4 * 152, 256, 0, st>>>((const float2*)x, (__nv_bfloat162*)h->tc_x, h->g.Vc * nc, xscale,
+                                                   (float2*)vout, skip);
   AMG_LAUNCH_CHECK();
   h->launches++;
   const int threads = 32 + 32 * (nc / 16);
-  const size_t chunk = (size_t)2 * nc * nc * sizeof(bf16) + (size_t)xpitch * sizeof(bf16);
+  const size_t chunk = (size_t)2 * nc * nc * sizeof(bf16) + xsite;
   int ns = (int)((72 * 1024) / chunk);
   ns = ns < 2 ? 2 : (ns > 6 ? 6 : ns);
   const size_t smem = kPipeBytes + ns * chunk;
@@ -572,7 +607,7 @@ amg_status launch_apply_tc(amg_coarse* h, const void* x, void* y, cudaStream_t s
   if (per_sm < 1) return AMG_ERR_UNSUPPORTED;
   const long long gmax = (long long)per_sm * sm_count_tc();
   const int grid = (int)(h->g.Vc < gmax ? h->g.Vc : gmax);
-  TcApplyArgs a{(const bf16*)h->Dtc, (const bf16*)h->tc_x, h->nbr, (float2*)y, skip, h->err, h->g, ns, xpitch};
+  TcApplyArgs a{(const bf16*)h->Dtc, (const bf16*)h->tc_x, h->nbr, (float2*)y, skip, h->err, h->g, ns};
   apply_tc_kernel<NRHS><<<grid, threads, smem, st>>>(a);
   AMG_LAUNCH_CHECK();
   h->launches++;
@@ -590,13 +625,12 @@ amg_status amg_internal_tc_prepare(amg_coarse* h, cudaStream_t st) {
     AMG_LAUNCH_CHECK();
     // BF16 planes of the apply's input, sized for the largest supported column count <= max_nrhs
     const int nmax = h->p.max_nrhs >= 16 ? 16 : (h->p.max_nrhs + 3) / 4 * 4;
-    h->tc_xbytes = (size_t)h->g.Vc * tc_xpitch(h->g, nmax) * sizeof(bf16);
+    h->tc_xbytes = (size_t)h->g.Vc * tc_xbytes_per_site(h->g, nmax);
     AMG_CUDA_TRY(cudaMalloc(&h->tc_x, h->tc_xbytes));
   }
   if (h->p.r_prec == AMG_BF16) {
     const Geom& g = h->g;
-    const bool run_ok = g.B[0] % 8 == 0 || 8 % g.B[0] == 0;
-    if (g.ntv % 8 || g.Vb % 8 || !run_ok) return AMG_ERR_UNSUPPORTED;
+    if (g.ntv % 8 || g.Vb % 8) return AMG_ERR_UNSUPPORTED;
     const size_t n = (size_t)g.Vc * 2 * 2 * g.ntv * g.nagg;
     AMG_CUDA_TRY(cudaMalloc(&h->Rtc, n * sizeof(bf16)));
     r_to_tc_kernel<<<4 * 152, 256, 0, st>>>(h->R64, (bf16*)h->Rtc, g);

@@ -109,7 +109,7 @@ def test_tc_coarse_apply(amg, case, nrhs):
     assert H.rel(got, ref) <= bound
 
 
-@pytest.mark.parametrize("nrhs", [4, 16])
+@pytest.mark.parametrize("nrhs", [4, 8, 12, 16])
 def test_tc_restrict_prolong(amg, case, nrhs):
     c = case
     y = bf16_round(si.fine_rhs(c.seed + 2, nrhs, si.all_sites(c.L)))        # (V, 4, 3, nrhs)
