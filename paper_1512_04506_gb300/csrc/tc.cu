@@ -152,7 +152,17 @@ __global__ void __launch_bounds__(160, 1) apply_tc_kernel(const TcApplyArgs a) {
   if (threadIdx.x < 32) {
     if (threadIdx.x == 0) {
       long long c = 0;
+      // the neighbour indices of the next site are loaded while the current site's copies are issued
+      int nb[9], nx[9];
+      if (blockIdx.x < Vc)
+        for (int d = 0; d < 9; ++d) nx[d] = __ldg(a.nbr + blockIdx.x * 9LL + d);
       for (long long i = blockIdx.x; i < Vc && !pp->abort; i += gridDim.x) {
+#pragma unroll
+        for (int d = 0; d < 9; ++d) nb[d] = nx[d];
+        if (i + gridDim.x < Vc)
+#pragma unroll
+          for (int d = 0; d < 9; ++d) nx[d] = __ldg(a.nbr + (i + gridDim.x) * 9 + d);
+#pragma unroll
         for (int d = 0; d < 9; ++d, ++c) {
           const int s = (int)(c % ns);
           const long long q = c / ns;
@@ -163,8 +173,8 @@ __global__ void __launch_bounds__(160, 1) apply_tc_kernel(const TcApplyArgs a) {
           mbar_expect_tx(&pp->full[s], chunk);
           unsigned char* st = stages + (size_t)s * chunk;
           bulk_load(st, a.D + (i * 9 + d) * 2LL * nc * nc, dbytes, &pp->full[s]);
-          bulk_load(st + dbytes, reinterpret_cast<const unsigned char*>(a.X) + (long long)a.nbr[i * 9 + d] * xbytes,
-                    xbytes, &pp->full[s]);
+          bulk_load(st + dbytes, reinterpret_cast<const unsigned char*>(a.X) + (long long)nb[d] * xbytes, xbytes,
+                    &pp->full[s]);
         }
       }
       drain(pp, c, ns);
@@ -179,11 +189,11 @@ __global__ void __launch_bounds__(160, 1) apply_tc_kernel(const TcApplyArgs a) {
   const int arow = w * 16 + 8 * (q & 1) + li;
   long long c = 0;
   for (long long i = blockIdx.x; i < Vc; i += gridDim.x) {
-    float acc[NT][4];
+    float acc[NT][4], acc2[NT][4];  // products with the Re and the Im plane (two shorter mma chains)
 #pragma unroll
     for (int t = 0; t < NT; ++t)
 #pragma unroll
-      for (int u = 0; u < 4; ++u) acc[t][u] = 0.f;
+      for (int u = 0; u < 4; ++u) acc[t][u] = acc2[t][u] = 0.f;
     for (int d = 0; d < 9; ++d, ++c) {
       const int s = (int)(c % ns);
       bool ok = !pp->abort;
@@ -219,7 +229,7 @@ __global__ void __launch_bounds__(160, 1) apply_tc_kernel(const TcApplyArgs a) {
                 p1 ^= kNeg2;
               }
               mma_bf16(acc[t + v], are, b0, b1);
-              mma_bf16(acc[t + v], aim, p0, p1);
+              mma_bf16(acc2[t + v], aim, p0, p1);
             }
           }
         }
@@ -232,8 +242,8 @@ __global__ void __launch_bounds__(160, 1) apply_tc_kernel(const TcApplyArgs a) {
     const int row = w * 16 + g;
 #pragma unroll
     for (int t = 0; t < NT; ++t) {
-      a.y[(i * nc + row) * NRHS + 4 * t + tq] = make_float2(acc[t][0], acc[t][1]);
-      a.y[(i * nc + row + 8) * NRHS + 4 * t + tq] = make_float2(acc[t][2], acc[t][3]);
+      a.y[(i * nc + row) * NRHS + 4 * t + tq] = make_float2(acc[t][0] + acc2[t][0], acc[t][1] + acc2[t][1]);
+      a.y[(i * nc + row + 8) * NRHS + 4 * t + tq] = make_float2(acc[t][2] + acc2[t][2], acc[t][3] + acc2[t][3]);
     }
   }
 }
@@ -493,20 +503,51 @@ __global__ void __launch_bounds__(160, 1) prolong_tc_kernel(const TcRPArgs a) {
             }
           }
         }
-        // tile t (= d'), lane (g, tq): rows g / g + 8 as in A, columns = sites 2 tq, 2 tq + 1
+        // tile t (= d'), lane (g, tq): rows g / g + 8 as in A, columns = sites 2 tq, 2 tq + 1.  After
+        // the partner exchange lane (g, tq) holds one BF16 pair w[c] per combination c = 2 (t - t0) + u
+        // of a tile pair t0, t0 + 1 and row half u: site 2 tq + (g & 1), right-hand side
+        // 8 mt + 4 u + k (k = g / 2).  A 4 x 4 transpose over k (lanes 8 apart) leaves lane k with the
+        // four right-hand sides 8 mt + 4 (k & 1) + 0..3 of combination c = k: one 16-byte store.
+        const int k = g >> 1, sl = 2 * tq + (g & 1);
+        const long long site = block_site_fast(a.g, origin, 8 * cc + sl);
 #pragma unroll
-        for (int t = 0; t < 6; ++t)
+        for (int t0 = 0; t0 < 6; t0 += 2) {
+          unsigned wv[4];
 #pragma unroll
-          for (int u = 0; u < 2; ++u) {
+          for (int c4 = 0; c4 < 4; ++c4) {
+            const int t = t0 + (c4 >> 1), u = c4 & 1;
             const float x0 = acc[t][2 * u], x1 = acc[t][2 * u + 1];
             const float recv = partnerf(even ? x1 : x0);
-            const int r = 8 * mt + (g >> 1) + 4 * u, sl = 2 * tq + (g & 1);
-            if (r < NRHS) {
-              const long long site = block_site_fast(a.g, origin, 8 * cc + sl);
-              X[(site * 12 + 6 * hw + t) * NRHS + r] =
-                  even ? __floats2bfloat162_rn(x0, recv) : __floats2bfloat162_rn(recv, x1);
+            wv[c4] = even ? pack_bf16(x0, recv) : pack_bf16(recv, x1);
+          }
+          {
+            const bool odd = k & 1;
+            const unsigned r0 = __shfl_xor_sync(0xffffffffu, odd ? wv[0] : wv[1], 8);
+            const unsigned r1 = __shfl_xor_sync(0xffffffffu, odd ? wv[2] : wv[3], 8);
+            if (odd) {
+              wv[0] = r0;
+              wv[2] = r1;
+            } else {
+              wv[1] = r0;
+              wv[3] = r1;
             }
           }
+          {
+            const bool hi = k & 2;
+            const unsigned r0 = __shfl_xor_sync(0xffffffffu, hi ? wv[0] : wv[2], 16);
+            const unsigned r1 = __shfl_xor_sync(0xffffffffu, hi ? wv[1] : wv[3], 16);
+            if (hi) {
+              wv[0] = r0;
+              wv[1] = r1;
+            } else {
+              wv[2] = r0;
+              wv[3] = r1;
+            }
+          }
+          const int r = 8 * mt + 4 * (k & 1), t = t0 + (k >> 1);
+          if (r < NRHS)
+            *reinterpret_cast<uint4*>(X + (site * 12 + 6 * hw + t) * NRHS + r) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+        }
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&pp->empty[s]);
