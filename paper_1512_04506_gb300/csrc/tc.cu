@@ -638,7 +638,8 @@ amg_status launch_apply_tc(amg_coarse* h, const void* x, void* y, cudaStream_t s
   h->launches++;
   const int threads = 32 + 32 * (nc / 16);
   const size_t chunk = (size_t)2 * nc * nc * sizeof(bf16) + xsite;
-  int ns = (int)((72 * 1024) / chunk);
+  // a short ring: more CTAs per SM (each works through its chunks in order) beat deeper prefetch
+  int ns = (int)((32 * 1024) / chunk);
   ns = ns < 2 ? 2 : (ns > 6 ? 6 : ns);
   const size_t smem = kPipeBytes + ns * chunk;
   if (smem > 227 * 1024) return AMG_ERR_UNSUPPORTED;
