@@ -36,7 +36,7 @@ TOL, RESTART, MAX_APPLIES = 0.05, 30, 200
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the 32^4 workload, from
 # the ncu captures of the 24^4 case summarised under profiles/ scaled by the number of blocks /
 # coarse sites (the per-unit work is the same); valid for the kernels as captured.
-TRAFFIC = {"restrict": 2125495915, "prolong": 2160730820, "apply": 483984978}
+TRAFFIC = {"restrict": 2124549284, "prolong": 2159132874, "apply": 484378194}
 METRIC = "coarse-grid correction GB/s & % HBM roofline; batched-mixed vs plain speedup"
 WORKLOAD = "fp32_32^4_b4_ntv20: 32^4 Wilson-clover, 4^4 blocks -> 8^4 coarse, Ntv=20, 1 RHS, " \
            "FP64 setup, FP32 R and D_c; step = R y, FGMRES(30) to 0.05 (<=200 applies), P x_c"
