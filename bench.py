@@ -37,6 +37,9 @@ TOL, RESTART, MAX_APPLIES = 0.05, 30, 200
 # the ncu captures of the 24^4 case summarised under profiles/ scaled by the number of blocks /
 # coarse sites (the per-unit work is the same); valid for the kernels as captured.
 TRAFFIC = {"restrict": 2124549284, "prolong": 2159132874, "apply": 484378194}
+# the same for the 48^3 x 96 tensor-core workload (captures of the 24^3 x 48 case, x16; the apply
+# figure is the tensor-core kernel alone, without the FP32 -> BF16 conversion launch)
+TRAFFIC_TC16 = {"restrict": 20641533184, "prolong": 20024094720, "apply": 3793358848}
 METRIC = "coarse-grid correction GB/s & % HBM roofline; batched-mixed vs plain speedup"
 WORKLOAD = "fp32_32^4_b4_ntv20: 32^4 Wilson-clover, 4^4 blocks -> 8^4 coarse, Ntv=20, 1 RHS, " \
            "FP64 setup, FP32 R and D_c; step = R y, FGMRES(30) to 0.05 (<=200 applies), P x_c"
@@ -539,7 +542,8 @@ def run_tc16(args):
                                if Lt == (48, 48, 48, 96) else "%dx%dx%dx%d variant of tc16" % Lt,
                    "applies_per_step": applies, "bytes_per_step": step_bytes},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["GB/s"], "peak": peaks["hbm_gbs"],
-                     "unit": "GB/s", "frac": kern[dom]["frac"], "peak_source": src, "traffic": None},
+                     "unit": "GB/s", "frac": kern[dom]["frac"], "peak_source": src,
+                     "traffic": TRAFFIC_TC16.get(dom) if Lt == (48, 48, 48, 96) else None},
         "kernels": kern, "setup_ms": [round(v, 1) for v in setup_ms], "clocks": clk,
     }
 
