@@ -600,8 +600,11 @@ def run_fp16(args):
 
 def run_batch(args):
     """The uneven batch in one persistent launch, captured in a CUDA graph: lattices 16^4 (Ntv=16,
-    1 RHS), 24^3 x 48 (Ntv=20, 4 RHS), 32^3 x 64 (Ntv=24, 12 RHS), 4^4 blocks, eps 0.2 / 0.3 / 0.4,
-    FP32 storage; step = x_k = P_k D_ck R_k y_k for all three; launch shape from the autotuner."""
+    1 RHS), 24^3 x 48 (Ntv=20, 4 RHS), 32^3 x 64 (Ntv=24, 12 RHS), 4^4 blocks, eps 0.2 / 0.3 / 0.4;
+    step = x_k = P_k D_ck R_k y_k for all three; launch shape from the autotuner.  Precision
+    (--batch-precision): "mixed" = the 1-RHS lattice in FP32, the multi-RHS lattices in BF16 on the
+    tensor cores (BF16 R, D_c and fine vectors); "fp32" = all FP32.  Algorithmic bytes in the
+    storage precision of each lattice (BF16 rows of y_c: 4 B per complex entry)."""
     import torch
     import paper_1512_04506_gb300 as amg
     from synth import device as sd
@@ -609,23 +612,30 @@ def run_batch(args):
     st = torch.cuda.current_stream()
     hs, ys, xs, nr = [], [], [], []
     step_bytes = 0
+    precs = []
     for k, (Lk, ntv, nrhs, eps) in enumerate(spec):
         seed = 20151204 + 5 + 10 * k
         U = sd.links(seed, eps, Lk)
         tv = sd.test_vectors(seed, ntv, Lk)
-        h, _ = amg.amg_setup_coarse(amg.make_params(Lk, B, ntv, nrhs, M0, CSW, amg.AMG_FP32, amg.AMG_FP32,
-                                                    amg.AMG_FP32), U, tv, st)
+        bf = args.batch_precision == "mixed" and nrhs in (4, 8, 12, 16)
+        pr = amg.AMG_BF16 if bf else amg.AMG_FP32
+        h, _ = amg.amg_setup_coarse(amg.make_params(Lk, B, ntv, nrhs, M0, CSW, pr, pr, pr), U, tv, st)
         del U, tv
         y = sd.fine_rhs(seed, nrhs, Lk, torch.complex64)
+        if bf:
+            y = torch.view_as_real(y).to(torch.bfloat16)
+            torch.cuda.empty_cache()
         hs.append(h)
         ys.append(y)
         xs.append(torch.empty_like(y))
         nr.append(nrhs)
+        precs.append("bf16" if bf else "fp32")
         V = int(np.prod(Lk))
         Vc = V // int(np.prod(B))
         nc = 2 * ntv
-        step_bytes += 2 * Vc * 2 * ntv * 6 * int(np.prod(B)) * 8 + 2 * V * 12 * nrhs * 8 \
-            + Vc * 9 * nc * nc * 8 + 4 * Vc * nc * nrhs * 8
+        e = 4 if bf else 8  # bytes per complex entry of R, D_c, fine vectors and y_c
+        step_bytes += 2 * Vc * 2 * ntv * 6 * int(np.prod(B)) * e + 2 * V * 12 * nrhs * e \
+            + Vc * 9 * nc * nc * e + 2 * Vc * nc * nrhs * e + 2 * Vc * nc * nrhs * 8
     torch.cuda.empty_cache()
     amg.amg_batch_cgc(hs, ys, xs, nr, st)
     best = amg.amg_batch_autotune(hs, ys, xs, nr, st)
@@ -647,9 +657,12 @@ def run_batch(args):
     return {
         "metric": METRIC, "value": round(gbs, 2), "unit": "GB/s", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(1000 * t / args.steps, 4), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f32" if "bf16" in precs else "f32",
+        "data": "synthetic",
         "config": {"workload": "batch: 16^4 (Ntv 16, 1 RHS) + 24^3x48 (Ntv 20, 4 RHS) + 32^3x64 (Ntv 24, "
-                               "12 RHS), 4^4 blocks, FP32; one persistent launch per step, CUDA graph",
+                               "12 RHS), 4^4 blocks; one persistent launch per step, CUDA graph; inputs "
+                               "larger than L2",
+                   "precision": dict(zip(["16^4", "24^3x48", "32^3x64"], precs)),
                    "bytes_per_step": step_bytes, "autotuned_ms": round(best, 4)},
         "roofline": {"bound": "hbm", "kernel": "fused batch (whole launch)", "achieved": round(gbs, 1),
                      "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(gbs / peaks["hbm_gbs"], 4),
@@ -670,6 +683,8 @@ def main():
     ap.add_argument("--workload", default="fp32", choices=["fp32", "tc16", "fp16", "batch"],
                     help="fp32: the default 32^4 workload; tc16: 48^3x96 with 16 RHS on the tensor cores; "
                          "fp16: 200 FP16 coarse applications at 32^3x64; batch: the uneven batch")
+    ap.add_argument("--batch-precision", default="mixed", choices=["mixed", "fp32"],
+                    help="batch workload: BF16 tensor cores for the multi-RHS lattices (mixed) or all FP32")
     ap.add_argument("--lattice", default=None,
                     help="Lx,Ly,Lz,Lt override of the 32^4 lattice (smaller cases for ncu captures)")
     args = ap.parse_args()

@@ -161,22 +161,26 @@ amg_status amg_cgc(amg_handle h, const void *d_y, void *d_x, int nrhs, double to
  * amg_batch_cgc -- x_k = P_k D_ck R_k y_k for n lattices (handles hs[k]) in one
  * persistent launch: each lattice's restriction, one D_c application and its
  * prolongation run as phases separated by per-lattice device barriers with a
- * bounded wait (AMG_ERR_TIMEOUT when a wait runs out).  All handles must use
- * FP32 coarse vectors.  The launch is capturable in a CUDA graph.
+ * bounded wait (AMG_ERR_TIMEOUT when a wait runs out).  Each lattice runs in its
+ * handle's precision: FP32 R, D_c and vectors (any nrhs), or BF16 R, D_c and fine
+ * vectors with nrhs = 4, 8, 12 or 16 (tensor cores; y_c and D_c y_c are kept in
+ * the work buffer, y_c as BF16).  Other combinations return AMG_ERR_UNSUPPORTED.
+ * The launch is capturable in a CUDA graph.
  * Scratch: the first call for a given set of handles allocates a work buffer
  * owned by hs[0]; later calls reuse it.
  */
 amg_status amg_batch_cgc(const amg_handle *hs, int n, const void *const *d_y, void *const *d_x,
-                         const int *nrhs, void *stream);   /* n <= 8; FP32 R, D_c and vectors */
+                         const int *nrhs, void *stream);   /* n <= 8 */
 
 /*
- * amg_batch_autotune -- times the fused batch launch for each candidate shape (128, 256 or 512
- * threads per CTA x 1, 2 or 4 CTAs per SM) on the given buffers (which it overwrites like
- * amg_batch_cgc) and keeps the fastest in hs[0] for later amg_batch_cgc calls.  best_ms (may be
+ * amg_batch_autotune -- times the fused batch launch for each candidate shape (1, 2, 3 or 4 CTAs
+ * per SM, capped by occupancy, x 2, 3 or 4 bulk-copy ring stages) on the caller's arguments (same
+ * as amg_batch_cgc) and keeps the fastest in hs[0] for later amg_batch_cgc calls.  best_ms (may be
  * NULL) receives its time in milliseconds.  Synchronises the stream.
  */
 amg_status amg_batch_autotune(const amg_handle *hs, int n, const void *const *d_y, void *const *d_x,
                               const int *nrhs, void *stream, double *best_ms);
+
 /*
  * amg_batch_test_hook -- test hook for the bounded waits of amg_batch_cgc: the next launches whose
  * first handle is h0 expect extra_need more phase-1 jobs for lattice 0 than exist, so its

@@ -285,7 +285,6 @@ amg_status amg_batch_cgc(const amg_handle* hs, int n, const void* const* d_y, vo
   if (!hs || n < 1 || !d_y || !d_x || !nrhs) return AMG_ERR_INVALID_ARG;
   for (int k = 0; k < n; ++k) {
     AMG_TRY(check_apply_args(hs[k], d_y[k], d_x[k], nrhs[k]));
-    if (hs[k]->p.vec_prec != AMG_FP32) return AMG_ERR_UNSUPPORTED;
   }
   for (int k = 0; k < n; ++k) hs[k]->last_stream = (cudaStream_t)stream;
   return amg_internal_batch(const_cast<amg_coarse* const*>(hs), n, d_y, d_x, nrhs, (cudaStream_t)stream);

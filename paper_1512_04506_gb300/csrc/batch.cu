@@ -3,47 +3,64 @@
 // threads with synchronisation points of Sec. 3 become persistent CTAs with per-lattice phase
 // counters).
 //
-// The host lists every job in phase order: all restriction jobs (one block of one lattice), then
-// all coarse-operator jobs (one coarse site), then all prolongation jobs (one block).  CTAs take
-// jobs from a global atomic counter.  A phase-2 job of lattice k first waits until all phase-1
-// jobs of lattice k have completed, a phase-3 job until all phase-2 jobs of k have; since every job
-// waits only on jobs that were handed out earlier, and a job that has been handed out belongs to
-// a running CTA that never waits on a later job, the schedule cannot deadlock whatever the number
-// of resident CTAs.  Waits are bounded (about one second of clock cycles): a wait that runs out
-// sets AMG_EBIT_TIMEOUT and an abort flag that makes every later wait return at once.
+// The host lists every job in phase order: all restriction jobs, then all coarse-operator jobs,
+// then all prolongation jobs; a job is a run of consecutive blocks or coarse sites of one lattice.
+// CTAs take jobs from a global atomic counter.  A phase-2 job of lattice k first waits until all
+// phase-1 jobs of lattice k have completed, a phase-3 job until all phase-2 jobs of k have; since
+// every job waits only on jobs that were handed out earlier, and a job that has been handed out
+// belongs to a running CTA that never waits on a later job, the schedule cannot deadlock whatever
+// the number of resident CTAs.  Waits are bounded (about one second of clock cycles): a wait that
+// runs out sets AMG_EBIT_TIMEOUT and an abort flag that makes every later wait return at once.
+//
+// Each lattice runs in its handle's precision.  FP32 lattices use the SIMT jobs below.  BF16
+// lattices (R and D_c stored for the tensor cores, BF16 fine vectors, 4, 8, 12 or 16 right-hand
+// sides) run the tensor-core bodies of tc_body.cuh through one bulk-copy ring per CTA that lives as
+// long as the CTA; their restriction writes y_c directly as the BF16 rows the tensor-core apply
+// reads, and the apply writes D_c y_c in FP32 for the prolongation.
 //
 // The launch issues only a memset and a kernel, so it can be captured in a CUDA graph once the
 // work buffer exists (it is allocated by the first call).  amg_batch_autotune times candidate
-// launch shapes (threads per CTA x CTAs per SM) on the caller's data and keeps the fastest.
-#include "amg_internal.cuh"
+// launch shapes (CTAs per SM x ring stages) on the caller's data and keeps the fastest.
+#include "tc_body.cuh"
 
 #include <vector>
 
 namespace {
+using namespace amgtc;
 
 constexpr int kMaxLat = 8;
 constexpr long long kBatchWaitCycles = 2000000000LL;
+constexpr int kBatchThreads = 160;  // one producer warp + four consumer warps
 
 struct LatDesc {
   Geom g;
-  const float2* R;   // [Vc][2][ntv][6Vb] FP32
-  const float2* D;   // apply layout [Vc][9][nc col][nc row] FP32
-  const int* nbr;    // [Vc][9]
-  const float2* y;   // fine input  [V][12][nrhs]
-  float2* x;         // fine output [V][12][nrhs]
-  float2* yc;        // coarse scratch R y
-  float2* zc;        // coarse scratch D_c R y
+  int tc;            // 1: BF16 tensor-core jobs, 0: FP32 SIMT jobs
   int nrhs;
+  int ipj[3];        // blocks / sites per job of each phase
+  const float2* R;   // FP32: [Vc][2][ntv][6Vb]
+  const float2* D;   // FP32: apply layout [Vc][9][nc col][nc row]
+  const int* nbr;    // [Vc][9]
+  const float2* y;   // FP32 fine input  [V][12][nrhs]
+  float2* x;         // FP32 fine output [V][12][nrhs]
+  float2* yc;        // coarse scratch R y (FP32 lattices)
+  float2* zc;        // coarse scratch D_c R y (FP32, both kinds)
+  const bf16* Rtc;   // BF16: tensor-core R
+  const bf16* Dtc;   // BF16: tensor-core D_c
+  const void* ybf;   // BF16 fine input
+  void* xbf;         // BF16 fine output
+  __nv_bfloat162* rows;  // BF16: R y as the apply's BF16 rows
 };
 
 struct BatchArgs {
   LatDesc lat[kMaxLat];
   int nlat;
-  const unsigned* jobs;  // (phase << 28) | (lattice << 24) | item
+  const unsigned* jobs;  // (phase << 28) | (lattice << 24) | first item
   int njobs;
   unsigned* counters;    // [0] job counter, [1] abort, [2 + 3 k + p] completed jobs of phase p of k
   const int* need;       // [3 k + p] jobs of phase p of lattice k
   unsigned* err;
+  int ns;                // ring stages
+  unsigned stride;       // bytes per ring stage
 };
 
 __device__ inline unsigned ld_acquire(const unsigned* p) {
@@ -51,6 +68,7 @@ __device__ inline unsigned ld_acquire(const unsigned* p) {
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
+__device__ inline void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
 
 template <int NR>
 __device__ void restrict_job(const LatDesc& L, long long blk, int r0, float2* sm) {
@@ -188,17 +206,38 @@ __device__ void prolong_job(const LatDesc& L, long long blk, int r0, float2* sm)
 }
 
 template <int NR>
-__device__ void run_job(const LatDesc& L, int phase, long long item, int r0, float2* sm) {
+__device__ __noinline__ void run_job(const LatDesc& L, int phase, long long item, int r0, float2* sm) {
   if (phase == 0) restrict_job<NR>(L, item, r0, sm);
   else if (phase == 1) apply_job<NR>(L, item, r0, sm);
   else prolong_job<NR>(L, item, r0, sm);
 }
 
-__global__ void __launch_bounds__(512) batch_kernel(const BatchArgs a) {
-  extern __shared__ __align__(16) float2 sm[];
+template <int NRHS>
+__device__ __noinline__ void tc_job(const LatDesc& L, int phase, long long i0, long long i1, const Ring& rg, long long& c,
+                       unsigned* err) {
+  if (phase == 0) {
+    const TcRPArgs a{L.Rtc, L.ybf, nullptr, L.rows, false, err, L.g};
+    restrict_tc_items<NRHS>(a, rg, i0, i1, 1, c);
+  } else if (phase == 1) {
+    const TcApplyArgs a{L.Dtc, reinterpret_cast<const bf16*>(L.rows), L.nbr, L.zc, err, L.g};
+    apply_tc_items<NRHS>(a, rg, i0, i1, 1, c);
+  } else {
+    const TcRPArgs a{L.Rtc, L.zc, L.xbf, nullptr, false, err, L.g};
+    prolong_tc_items<NRHS>(a, rg, i0, i1, 1, c);
+  }
+}
+
+__global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchArgs a) {
+  extern __shared__ __align__(128) unsigned char sm[];
   __shared__ unsigned job_s;
   __shared__ int ok_s;
+  Pipe* pp = reinterpret_cast<Pipe*>(sm);
+  ring_init(pp, a.ns, (int)(blockDim.x >> 5) - 1);
+  __syncthreads();
+  const Ring rg{pp, sm + kPipeBytes, a.ns, a.stride};
+  float2* scratch = reinterpret_cast<float2*>(sm + kPipeBytes);  // SIMT jobs (the ring is idle then)
   volatile unsigned* abort_flag = a.counters + 1;
+  long long c = 0;  // chunks through the ring (tensor-core jobs)
   for (;;) {
     if (threadIdx.x == 0) job_s = atomicAdd(a.counters, 1u);
     __syncthreads();
@@ -206,11 +245,12 @@ __global__ void __launch_bounds__(512) batch_kernel(const BatchArgs a) {
     if (jid >= (unsigned)a.njobs) break;
     const unsigned code = a.jobs[jid];
     const int phase = (int)(code >> 28), k = (int)((code >> 24) & 15);
-    const long long item = code & 0xFFFFFF;
+    const long long first = code & 0xFFFFFF;
     const LatDesc& L = a.lat[k];
+    const long long last = first + L.ipj[phase] < L.g.Vc ? first + L.ipj[phase] : L.g.Vc;
     if (threadIdx.x == 0) {
-      int ok = 1;
-      if (phase > 0) {
+      int ok = !pp->abort;
+      if (ok && phase > 0) {
         const unsigned* done = a.counters + 2 + 3 * k + (phase - 1);
         const unsigned need = (unsigned)a.need[3 * k + phase - 1];
         const long long t0 = clock64();
@@ -226,32 +266,49 @@ __global__ void __launch_bounds__(512) batch_kernel(const BatchArgs a) {
             break;
           }
         }
+        // the earlier phase's results (written by other CTAs) are read next, partly by bulk copies
+        __threadfence();
+        fence_proxy_async_global();
       }
       ok_s = ok;
     }
     __syncthreads();
     if (ok_s) {
-      int r0 = 0;
-      while (r0 < L.nrhs) {
-        if (L.nrhs - r0 >= 4) {
-          run_job<4>(L, phase, item, r0, sm);
-          r0 += 4;
-        } else {
-          run_job<1>(L, phase, item, r0, sm);
-          r0 += 1;
+      if (L.tc) {
+        switch (L.nrhs) {
+          case 4: tc_job<4>(L, phase, first, last, rg, c, a.err); break;
+          case 8: tc_job<8>(L, phase, first, last, rg, c, a.err); break;
+          case 12: tc_job<12>(L, phase, first, last, rg, c, a.err); break;
+          default: tc_job<16>(L, phase, first, last, rg, c, a.err); break;
+        }
+      } else {
+        for (long long item = first; item < last; ++item) {
+          int r0 = 0;
+          while (r0 < L.nrhs) {
+            if (L.nrhs - r0 >= 4) {
+              run_job<4>(L, phase, item, r0, scratch);
+              r0 += 4;
+            } else {
+              run_job<1>(L, phase, item, r0, scratch);
+              r0 += 1;
+            }
+          }
         }
       }
     }
+    fence_proxy_async_global();  // this job's stores may be read by bulk copies of a later job
     __syncthreads();
     if (threadIdx.x == 0) {
       __threadfence();
       atomicAdd(a.counters + 2 + 3 * k + phase, 1u);
+      if (pp->abort) *abort_flag = 1;
     }
   }
+  if (threadIdx.x == 0) drain(pp, c, a.ns);
 }
 
-size_t batch_smem(const Geom& g, int threads) {
-  const int NR = 4;
+size_t simt_smem(const Geom& g, int nrhs, int threads) {
+  const int NR = nrhs >= 4 ? 4 : 1;
   const size_t r = (size_t)2 * g.nagg * NR * sizeof(float2);
   const int G = threads / (g.nc / 2) < g.nc ? threads / (g.nc / 2) : g.nc;
   const size_t ap = ((size_t)9 * g.nc * NR + (size_t)G * g.nc * NR) * sizeof(float2);
@@ -260,23 +317,37 @@ size_t batch_smem(const Geom& g, int threads) {
   return m > p ? m : p;
 }
 
+bool tc_lattice(const amg_coarse* h, int nrhs) {
+  return h->p.r_prec == AMG_BF16 && h->p.link_prec == AMG_BF16 && h->p.vec_prec == AMG_BF16;
+}
+
 struct Prepared {
   BatchArgs a;
   size_t smem;
 };
 
 amg_status prepare(amg_coarse* const* hs, int n, const void* const* y, void* const* x, const int* nrhs,
-                   cudaStream_t st, int threads, Prepared* out) {
+                   cudaStream_t st, int ns, Prepared* out) {
   if (n > kMaxLat) return AMG_ERR_UNSUPPORTED;
   BatchWork& bw = hs[0]->bw;
-  // layout of the work buffer: counters | need | jobs | per lattice yc, zc
+  // items per job: tensor-core restriction / prolongation 2 blocks, apply 8 sites; SIMT 1
+  auto ipj = [&](int k, int p) { return tc_lattice(hs[k], nrhs[k]) ? (p == 1 ? 8 : 2) : 1; };
+  // layout of the work buffer: counters | need | jobs | per lattice coarse scratch
   size_t njobs = 0, coarse_bytes = 0;
   for (int k = 0; k < n; ++k) {
     const amg_coarse* h = hs[k];
-    if (h->p.r_prec != AMG_FP32 || h->p.link_prec != AMG_FP32) return AMG_ERR_UNSUPPORTED;
+    const bool tc = tc_lattice(h, nrhs[k]);
+    if (tc) {
+      if (!h->Rtc || !h->Dtc) return AMG_ERR_UNSUPPORTED;
+      if (nrhs[k] != 4 && nrhs[k] != 8 && nrhs[k] != 12 && nrhs[k] != 16) return AMG_ERR_UNSUPPORTED;
+    } else if (h->p.r_prec != AMG_FP32 || h->p.link_prec != AMG_FP32 || h->p.vec_prec != AMG_FP32) {
+      return AMG_ERR_UNSUPPORTED;
+    }
     if (h->g.Vc >= (1 << 24) || h->g.nc % 2) return AMG_ERR_UNSUPPORTED;
-    njobs += 3 * (size_t)h->g.Vc;
-    coarse_bytes += 2 * (((size_t)h->g.Vc * h->g.nc * nrhs[k] * sizeof(float2) + 255) / 256 * 256);
+    for (int p = 0; p < 3; ++p) njobs += (size_t)((h->g.Vc + ipj(k, p) - 1) / ipj(k, p));
+    const size_t vc = ((size_t)h->g.Vc * h->g.nc * nrhs[k] * sizeof(float2) + 255) / 256 * 256;
+    const size_t rows = ((size_t)h->g.Vc * h->g.nc * tc_xunits(nrhs[k]) * 16 + 255) / 256 * 256;
+    coarse_bytes += tc ? vc + rows : 2 * vc;
   }
   const size_t head = 256 + 256 + (njobs * sizeof(unsigned) + 255) / 256 * 256;
   const size_t need_bytes = head + coarse_bytes;
@@ -298,36 +369,56 @@ amg_status prepare(amg_coarse* const* hs, int n, const void* const* y, void* con
   a.jobs = (const unsigned*)(base + 512);
   a.njobs = (int)njobs;
   a.err = hs[0]->err;
+  a.ns = ns;
   size_t off = head;
   std::vector<int> need(3 * kMaxLat, 0);
   std::vector<unsigned> jobs;
   jobs.reserve(njobs);
   for (int phase = 0; phase < 3; ++phase)
     for (int k = 0; k < n; ++k)
-      for (long long it = 0; it < hs[k]->g.Vc; ++it) jobs.push_back(((unsigned)phase << 28) | ((unsigned)k << 24) | (unsigned)it);
-  size_t smem = 0;
+      for (long long it = 0; it < hs[k]->g.Vc; it += ipj(k, phase)) {
+        jobs.push_back(((unsigned)phase << 28) | ((unsigned)k << 24) | (unsigned)it);
+        need[3 * k + phase]++;
+      }
+  size_t simt = 0;
+  unsigned stride = 0;
   unsigned long long sig = 1469598103934665603ull;  // FNV-1a over the batch description
   for (int k = 0; k < n; ++k) {
     const amg_coarse* h = hs[k];
     LatDesc& L = a.lat[k];
     L.g = h->g;
-    L.R = (const float2*)h->Rq;
-    L.D = (const float2*)h->Dq;
-    L.nbr = h->nbr;
-    L.y = (const float2*)y[k];
-    L.x = (float2*)x[k];
+    L.tc = tc_lattice(h, nrhs[k]) ? 1 : 0;
     L.nrhs = nrhs[k];
-    const size_t cb = ((size_t)h->g.Vc * h->g.nc * nrhs[k] * sizeof(float2) + 255) / 256 * 256;
-    L.yc = (float2*)(base + off);
-    L.zc = (float2*)(base + off + cb);
-    off += 2 * cb;
-    for (int p = 0; p < 3; ++p) need[3 * k + p] = (int)h->g.Vc;
+    for (int p = 0; p < 3; ++p) L.ipj[p] = ipj(k, p);
+    L.nbr = h->nbr;
+    const size_t vc = ((size_t)h->g.Vc * h->g.nc * nrhs[k] * sizeof(float2) + 255) / 256 * 256;
+    if (L.tc) {
+      L.Rtc = (const bf16*)h->Rtc;
+      L.Dtc = (const bf16*)h->Dtc;
+      L.ybf = y[k];
+      L.xbf = x[k];
+      L.zc = (float2*)(base + off);
+      L.rows = (__nv_bfloat162*)(base + off + vc);
+      off += vc + ((size_t)h->g.Vc * h->g.nc * tc_xunits(nrhs[k]) * 16 + 255) / 256 * 256;
+      const unsigned ch[3] = {tc_restrict_chunk(h->g.ntv, nrhs[k]), tc_apply_chunk(h->g.nc, nrhs[k]),
+                              tc_prolong_chunk(h->g.ntv)};
+      for (int p = 0; p < 3; ++p) stride = ch[p] > stride ? ch[p] : stride;
+    } else {
+      L.R = (const float2*)h->Rq;
+      L.D = (const float2*)h->Dq;
+      L.y = (const float2*)y[k];
+      L.x = (float2*)x[k];
+      L.yc = (float2*)(base + off);
+      L.zc = (float2*)(base + off + vc);
+      off += 2 * vc;
+      const size_t sm = simt_smem(h->g, nrhs[k], kBatchThreads);
+      simt = sm > simt ? sm : simt;
+    }
     if (k == 0) need[0] += bw.test_extra_need;
-    const size_t s = batch_smem(h->g, threads);
-    smem = s > smem ? s : smem;
     sig = (sig ^ (unsigned long long)(uintptr_t)h) * 1099511628211ull;
     sig = (sig ^ (unsigned long long)nrhs[k]) * 1099511628211ull;
   }
+  a.stride = stride;
   sig = (sig ^ (unsigned long long)bw.test_extra_need) * 1099511628211ull;
   if (bw.sig != sig) {  // job list and phase counts only change with the batch description
     AMG_CUDA_TRY(cudaMemcpyAsync((void*)a.need, need.data(), need.size() * sizeof(int), cudaMemcpyHostToDevice, st));
@@ -335,23 +426,25 @@ amg_status prepare(amg_coarse* const* hs, int n, const void* const* y, void* con
     AMG_CUDA_TRY(cudaStreamSynchronize(st));
     bw.sig = sig;
   }
+  const size_t ring = (size_t)ns * stride;
+  const size_t smem = kPipeBytes + (ring > simt ? ring : simt);
   if (smem > 227 * 1024) return AMG_ERR_UNSUPPORTED;
   out->a = a;
   out->smem = smem;
   return AMG_OK;
 }
 
-amg_status launch(const Prepared& pr, int threads, int per_sm, cudaStream_t st, amg_coarse* h0) {
+amg_status launch(const Prepared& pr, int per_sm, cudaStream_t st, amg_coarse* h0) {
   AMG_CUDA_TRY(cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pr.smem));
   int occ = 0;
-  AMG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel, threads, pr.smem));
+  AMG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel, kBatchThreads, pr.smem));
   if (occ < 1) return AMG_ERR_UNSUPPORTED;
   if (per_sm > occ) per_sm = occ;
   int dev = 0, sms = 0;
   AMG_CUDA_TRY(cudaGetDevice(&dev));
   AMG_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   AMG_CUDA_TRY(cudaMemsetAsync(pr.a.counters, 0, 256, st));
-  batch_kernel<<<per_sm * sms, threads, pr.smem, st>>>(pr.a);
+  batch_kernel<<<per_sm * sms, kBatchThreads, pr.smem, st>>>(pr.a);
   AMG_LAUNCH_CHECK();
   h0->launches++;
   return AMG_OK;
@@ -362,40 +455,38 @@ amg_status launch(const Prepared& pr, int threads, int per_sm, cudaStream_t st, 
 amg_status amg_internal_batch(amg_coarse* const* hs, int n, const void* const* y, void* const* x, const int* nrhs,
                               cudaStream_t s) {
   BatchWork& bw = hs[0]->bw;
-  const int threads = bw.threads ? bw.threads : 256;
-  const int per_sm = bw.per_sm ? bw.per_sm : 2;
+  const int ns = bw.ns ? bw.ns : 3;
+  const int per_sm = bw.per_sm ? bw.per_sm : 3;
   Prepared pr;
-  amg_status st = prepare(hs, n, y, x, nrhs, s, threads, &pr);
+  amg_status st = prepare(hs, n, y, x, nrhs, s, ns, &pr);
   if (st != AMG_OK) return st;
-  return launch(pr, threads, per_sm, s, hs[0]);
+  return launch(pr, per_sm, s, hs[0]);
 }
 
 extern "C" amg_status amg_batch_autotune(const amg_handle* hs, int n, const void* const* d_y, void* const* d_x,
                                          const int* nrhs, void* stream, double* best_ms) {
   if (!hs || n < 1 || !d_y || !d_x || !nrhs) return AMG_ERR_INVALID_ARG;
-  for (int k = 0; k < n; ++k) {
+  for (int k = 0; k < n; ++k)
     if (!hs[k] || !d_y[k] || !d_x[k] || nrhs[k] < 1 || nrhs[k] > hs[k]->p.max_nrhs) return AMG_ERR_INVALID_ARG;
-    if (hs[k]->p.vec_prec != AMG_FP32) return AMG_ERR_UNSUPPORTED;
-  }
   cudaStream_t st = (cudaStream_t)stream;
   amg_coarse* const* H = const_cast<amg_coarse* const*>(hs);
-  const int cand_threads[3] = {128, 256, 512};
-  const int cand_per_sm[3] = {1, 2, 4};
+  const int cand_ns[3] = {2, 3, 4};
+  const int cand_per_sm[4] = {1, 2, 3, 4};
   float best = 1e30f;
-  int bt = 256, bp = 2;
+  int bn = 3, bp = 3;
   cudaEvent_t e0, e1;
   AMG_CUDA_TRY(cudaEventCreate(&e0));
   AMG_CUDA_TRY(cudaEventCreate(&e1));
-  for (int ti = 0; ti < 3; ++ti)
-    for (int pi = 0; pi < 3; ++pi) {
+  for (int ni = 0; ni < 3; ++ni)
+    for (int pi = 0; pi < 4; ++pi) {
       Prepared pr;
-      if (prepare(H, n, d_y, d_x, nrhs, st, cand_threads[ti], &pr) != AMG_OK) continue;
-      if (launch(pr, cand_threads[ti], cand_per_sm[pi], st, H[0]) != AMG_OK) continue;  // warm-up
+      if (prepare(H, n, d_y, d_x, nrhs, st, cand_ns[ni], &pr) != AMG_OK) continue;
+      if (launch(pr, cand_per_sm[pi], st, H[0]) != AMG_OK) continue;  // warm-up
       float ms = 0, tot = 0;
       bool good = true;
       for (int rep = 0; rep < 3 && good; ++rep) {
         cudaEventRecord(e0, st);
-        good = launch(pr, cand_threads[ti], cand_per_sm[pi], st, H[0]) == AMG_OK;
+        good = launch(pr, cand_per_sm[pi], st, H[0]) == AMG_OK;
         cudaEventRecord(e1, st);
         cudaEventSynchronize(e1);
         cudaEventElapsedTime(&ms, e0, e1);
@@ -403,13 +494,13 @@ extern "C" amg_status amg_batch_autotune(const amg_handle* hs, int n, const void
       }
       if (good && tot / 3 < best) {
         best = tot / 3;
-        bt = cand_threads[ti];
+        bn = cand_ns[ni];
         bp = cand_per_sm[pi];
       }
     }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  H[0]->bw.threads = bt;
+  H[0]->bw.ns = bn;
   H[0]->bw.per_sm = bp;
   if (best_ms) *best_ms = best;
   for (int k = 0; k < n; ++k) H[k]->last_stream = st;
