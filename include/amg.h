@@ -75,6 +75,9 @@ typedef struct {
     amg_prec r_prec;     /* storage of R for restrict/prolong: FP64, FP32, BF16         */
     amg_prec vec_prec;   /* element type of fine vectors: FP64, FP32 or BF16            */
 } amg_params;
+/* BF16 storage runs on the tensor cores and needs ntv a multiple of 4 and V_block a
+ * multiple of 8 (else amg_setup_coarse returns AMG_ERR_UNSUPPORTED); its applies take
+ * nrhs = 4, 8, 12 or 16 with FP32 coarse vectors. */
 
 typedef struct amg_coarse *amg_handle;
 

@@ -113,7 +113,7 @@ struct BatchWork {
   void* buf = nullptr;
   size_t bytes = 0;
   unsigned long long sig = 0;  // description of the batch whose job list is in buf
-  int ns = 0, per_sm = 0;      // ring stages and CTAs per SM chosen by amg_batch_autotune (0: defaults)
+  int ns = 0, threads = 0, per_sm = 0;  // launch shape chosen by amg_batch_autotune (0: defaults)
   int test_extra_need = 0;     // test hook: jobs of phase 1 of lattice 0 that never arrive
 };
 

@@ -20,7 +20,8 @@
 //
 // The launch issues only a memset and a kernel, so it can be captured in a CUDA graph once the
 // work buffer exists (it is allocated by the first call).  amg_batch_autotune times candidate
-// launch shapes (CTAs per SM x ring stages) on the caller's data and keeps the fastest.
+// launch shapes (CTAs per SM x ring stages, or x threads per CTA when no lattice uses the tensor
+// cores) on the caller's data and keeps the fastest.
 #include "tc_body.cuh"
 
 #include <vector>
@@ -206,38 +207,51 @@ __device__ void prolong_job(const LatDesc& L, long long blk, int r0, float2* sm)
 }
 
 template <int NR>
-__device__ __noinline__ void run_job(const LatDesc& L, int phase, long long item, int r0, float2* sm) {
+__device__ void run_job(const LatDesc& L, int phase, long long item, int r0, float2* sm) {
   if (phase == 0) restrict_job<NR>(L, item, r0, sm);
   else if (phase == 1) apply_job<NR>(L, item, r0, sm);
   else prolong_job<NR>(L, item, r0, sm);
 }
 
-template <int NRHS>
-__device__ __noinline__ void tc_job(const LatDesc& L, int phase, long long i0, long long i1, const Ring& rg, long long& c,
-                       unsigned* err) {
-  if (phase == 0) {
-    const TcRPArgs a{L.Rtc, L.ybf, nullptr, L.rows, false, err, L.g};
-    restrict_tc_items<NRHS>(a, rg, i0, i1, 1, c);
-  } else if (phase == 1) {
-    const TcApplyArgs a{L.Dtc, reinterpret_cast<const bf16*>(L.rows), L.nbr, L.zc, err, L.g};
-    apply_tc_items<NRHS>(a, rg, i0, i1, 1, c);
-  } else {
-    const TcRPArgs a{L.Rtc, L.zc, L.xbf, nullptr, false, err, L.g};
-    prolong_tc_items<NRHS>(a, rg, i0, i1, 1, c);
-  }
+// out of line in the tensor-core kernel, where inlining it would raise the register count of
+// the whole kernel
+template <int NR>
+__device__ __noinline__ void run_job_outlined(const LatDesc& L, int phase, long long item, int r0, float2* sm) {
+  run_job<NR>(L, phase, item, r0, sm);
 }
 
-__global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchArgs a) {
+// The ring position goes in and out by value so that it stays in registers inside the call.
+template <int NRHS>
+__device__ __noinline__ RingPos tc_job(const LatDesc& L, int phase, long long i0, long long i1, const Ring rg,
+                                       RingPos rp, unsigned* err) {
+  if (phase == 0) {
+    const TcRPArgs a{L.Rtc, L.ybf, nullptr, L.rows, false, err, L.g};
+    restrict_tc_items<NRHS>(a, rg, i0, i1, 1, rp);
+  } else if (phase == 1) {
+    const TcApplyArgs a{L.Dtc, reinterpret_cast<const bf16*>(L.rows), L.nbr, L.zc, err, L.g};
+    apply_tc_items<NRHS>(a, rg, i0, i1, 1, rp);
+  } else {
+    const TcRPArgs a{L.Rtc, L.zc, L.xbf, nullptr, false, err, L.g};
+    prolong_tc_items<NRHS>(a, rg, i0, i1, 1, rp);
+  }
+  return rp;
+}
+
+// TC: the batch holds tensor-core lattices (160 threads: one producer warp, four consumer warps);
+// otherwise only SIMT jobs run and the thread count is free (autotuned).
+template <bool TC>
+__global__ void __launch_bounds__(TC ? kBatchThreads : 512, TC ? 3 : 1) batch_kernel(const BatchArgs a) {
   extern __shared__ __align__(128) unsigned char sm[];
   __shared__ unsigned job_s;
   __shared__ int ok_s;
   Pipe* pp = reinterpret_cast<Pipe*>(sm);
-  ring_init(pp, a.ns, (int)(blockDim.x >> 5) - 1);
+  if (TC) ring_init(pp, a.ns, (int)(blockDim.x >> 5) - 1);
+  else if (threadIdx.x == 0) pp->abort = 0;
   __syncthreads();
   const Ring rg{pp, sm + kPipeBytes, a.ns, a.stride};
   float2* scratch = reinterpret_cast<float2*>(sm + kPipeBytes);  // SIMT jobs (the ring is idle then)
   volatile unsigned* abort_flag = a.counters + 1;
-  long long c = 0;  // chunks through the ring (tensor-core jobs)
+  RingPos rp;  // chunks through the ring (tensor-core jobs)
   for (;;) {
     if (threadIdx.x == 0) job_s = atomicAdd(a.counters, 1u);
     __syncthreads();
@@ -268,35 +282,37 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchArgs
         }
         // the earlier phase's results (written by other CTAs) are read next, partly by bulk copies
         __threadfence();
-        fence_proxy_async_global();
+        if (TC) fence_proxy_async_global();
       }
       ok_s = ok;
     }
     __syncthreads();
     if (ok_s) {
-      if (L.tc) {
+      if (TC && L.tc) {
         switch (L.nrhs) {
-          case 4: tc_job<4>(L, phase, first, last, rg, c, a.err); break;
-          case 8: tc_job<8>(L, phase, first, last, rg, c, a.err); break;
-          case 12: tc_job<12>(L, phase, first, last, rg, c, a.err); break;
-          default: tc_job<16>(L, phase, first, last, rg, c, a.err); break;
+          case 4: rp = tc_job<4>(L, phase, first, last, rg, rp, a.err); break;
+          case 8: rp = tc_job<8>(L, phase, first, last, rg, rp, a.err); break;
+          case 12: rp = tc_job<12>(L, phase, first, last, rg, rp, a.err); break;
+          default: rp = tc_job<16>(L, phase, first, last, rg, rp, a.err); break;
         }
       } else {
         for (long long item = first; item < last; ++item) {
           int r0 = 0;
           while (r0 < L.nrhs) {
-            if (L.nrhs - r0 >= 4) {
-              run_job<4>(L, phase, item, r0, scratch);
-              r0 += 4;
+            const int nr = L.nrhs - r0 >= 4 ? 4 : 1;
+            if (TC) {
+              if (nr == 4) run_job_outlined<4>(L, phase, item, r0, scratch);
+              else run_job_outlined<1>(L, phase, item, r0, scratch);
             } else {
-              run_job<1>(L, phase, item, r0, scratch);
-              r0 += 1;
+              if (nr == 4) run_job<4>(L, phase, item, r0, scratch);
+              else run_job<1>(L, phase, item, r0, scratch);
             }
+            r0 += nr;
           }
         }
       }
     }
-    fence_proxy_async_global();  // this job's stores may be read by bulk copies of a later job
+    if (TC) fence_proxy_async_global();  // this job's stores may be read by bulk copies of a later job
     __syncthreads();
     if (threadIdx.x == 0) {
       __threadfence();
@@ -304,7 +320,7 @@ __global__ void __launch_bounds__(kBatchThreads, 3) batch_kernel(const BatchArgs
       if (pp->abort) *abort_flag = 1;
     }
   }
-  if (threadIdx.x == 0) drain(pp, c, a.ns);
+  if (TC && threadIdx.x == 0) drain(pp, rp.c, a.ns);
 }
 
 size_t simt_smem(const Geom& g, int nrhs, int threads) {
@@ -324,10 +340,11 @@ bool tc_lattice(const amg_coarse* h, int nrhs) {
 struct Prepared {
   BatchArgs a;
   size_t smem;
+  bool tc;  // some lattice runs on the tensor cores
 };
 
 amg_status prepare(amg_coarse* const* hs, int n, const void* const* y, void* const* x, const int* nrhs,
-                   cudaStream_t st, int ns, Prepared* out) {
+                   cudaStream_t st, int ns, int threads, Prepared* out) {
   if (n > kMaxLat) return AMG_ERR_UNSUPPORTED;
   BatchWork& bw = hs[0]->bw;
   // items per job: tensor-core restriction / prolongation 2 blocks, apply 8 sites; SIMT 1
@@ -411,7 +428,7 @@ amg_status prepare(amg_coarse* const* hs, int n, const void* const* y, void* con
       L.yc = (float2*)(base + off);
       L.zc = (float2*)(base + off + vc);
       off += 2 * vc;
-      const size_t sm = simt_smem(h->g, nrhs[k], kBatchThreads);
+      const size_t sm = simt_smem(h->g, nrhs[k], threads);
       simt = sm > simt ? sm : simt;
     }
     if (k == 0) need[0] += bw.test_extra_need;
@@ -431,20 +448,29 @@ amg_status prepare(amg_coarse* const* hs, int n, const void* const* y, void* con
   if (smem > 227 * 1024) return AMG_ERR_UNSUPPORTED;
   out->a = a;
   out->smem = smem;
+  out->tc = stride > 0;
   return AMG_OK;
 }
 
-amg_status launch(const Prepared& pr, int per_sm, cudaStream_t st, amg_coarse* h0) {
-  AMG_CUDA_TRY(cudaFuncSetAttribute(batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pr.smem));
+bool batch_has_tc(amg_coarse* const* hs, int n, const int* nrhs) {
+  for (int k = 0; k < n; ++k)
+    if (tc_lattice(hs[k], nrhs[k])) return true;
+  return false;
+}
+
+amg_status launch(const Prepared& pr, int threads, int per_sm, cudaStream_t st, amg_coarse* h0) {
+  auto kern = pr.tc ? batch_kernel<true> : batch_kernel<false>;
+  if (pr.tc) threads = kBatchThreads;
+  AMG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pr.smem));
   int occ = 0;
-  AMG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel, kBatchThreads, pr.smem));
+  AMG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, pr.smem));
   if (occ < 1) return AMG_ERR_UNSUPPORTED;
   if (per_sm > occ) per_sm = occ;
   int dev = 0, sms = 0;
   AMG_CUDA_TRY(cudaGetDevice(&dev));
   AMG_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   AMG_CUDA_TRY(cudaMemsetAsync(pr.a.counters, 0, 256, st));
-  batch_kernel<<<per_sm * sms, kBatchThreads, pr.smem, st>>>(pr.a);
+  kern<<<per_sm * sms, threads, pr.smem, st>>>(pr.a);
   AMG_LAUNCH_CHECK();
   h0->launches++;
   return AMG_OK;
@@ -455,12 +481,14 @@ amg_status launch(const Prepared& pr, int per_sm, cudaStream_t st, amg_coarse* h
 amg_status amg_internal_batch(amg_coarse* const* hs, int n, const void* const* y, void* const* x, const int* nrhs,
                               cudaStream_t s) {
   BatchWork& bw = hs[0]->bw;
+  const bool tc = batch_has_tc(hs, n, nrhs);
+  const int threads = tc ? kBatchThreads : (bw.threads ? bw.threads : 256);
   const int ns = bw.ns ? bw.ns : 3;
-  const int per_sm = bw.per_sm ? bw.per_sm : 3;
+  const int per_sm = bw.per_sm ? bw.per_sm : (tc ? 3 : 2);
   Prepared pr;
-  amg_status st = prepare(hs, n, y, x, nrhs, s, ns, &pr);
+  amg_status st = prepare(hs, n, y, x, nrhs, s, tc ? ns : 0, threads, &pr);
   if (st != AMG_OK) return st;
-  return launch(pr, per_sm, s, hs[0]);
+  return launch(pr, threads, per_sm, s, hs[0]);
 }
 
 extern "C" amg_status amg_batch_autotune(const amg_handle* hs, int n, const void* const* d_y, void* const* d_x,
@@ -470,23 +498,26 @@ extern "C" amg_status amg_batch_autotune(const amg_handle* hs, int n, const void
     if (!hs[k] || !d_y[k] || !d_x[k] || nrhs[k] < 1 || nrhs[k] > hs[k]->p.max_nrhs) return AMG_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   amg_coarse* const* H = const_cast<amg_coarse* const*>(hs);
-  const int cand_ns[3] = {2, 3, 4};
+  // tensor-core batches: ring stages x CTAs per SM; SIMT-only batches: threads per CTA x CTAs per SM
+  const bool tc = batch_has_tc(H, n, nrhs);
+  const int cand_a[3] = {2, 3, 4}, cand_threads[3] = {128, 256, 512};
   const int cand_per_sm[4] = {1, 2, 3, 4};
   float best = 1e30f;
-  int bn = 3, bp = 3;
+  int ba = tc ? 3 : 256, bp = tc ? 3 : 2;
   cudaEvent_t e0, e1;
   AMG_CUDA_TRY(cudaEventCreate(&e0));
   AMG_CUDA_TRY(cudaEventCreate(&e1));
-  for (int ni = 0; ni < 3; ++ni)
+  for (int ai = 0; ai < 3; ++ai)
     for (int pi = 0; pi < 4; ++pi) {
+      const int ns = tc ? cand_a[ai] : 0, threads = tc ? kBatchThreads : cand_threads[ai];
       Prepared pr;
-      if (prepare(H, n, d_y, d_x, nrhs, st, cand_ns[ni], &pr) != AMG_OK) continue;
-      if (launch(pr, cand_per_sm[pi], st, H[0]) != AMG_OK) continue;  // warm-up
+      if (prepare(H, n, d_y, d_x, nrhs, st, ns, threads, &pr) != AMG_OK) continue;
+      if (launch(pr, threads, cand_per_sm[pi], st, H[0]) != AMG_OK) continue;  // warm-up
       float ms = 0, tot = 0;
       bool good = true;
       for (int rep = 0; rep < 3 && good; ++rep) {
         cudaEventRecord(e0, st);
-        good = launch(pr, cand_per_sm[pi], st, H[0]) == AMG_OK;
+        good = launch(pr, threads, cand_per_sm[pi], st, H[0]) == AMG_OK;
         cudaEventRecord(e1, st);
         cudaEventSynchronize(e1);
         cudaEventElapsedTime(&ms, e0, e1);
@@ -494,13 +525,14 @@ extern "C" amg_status amg_batch_autotune(const amg_handle* hs, int n, const void
       }
       if (good && tot / 3 < best) {
         best = tot / 3;
-        bn = cand_ns[ni];
+        ba = tc ? cand_a[ai] : cand_threads[ai];
         bp = cand_per_sm[pi];
       }
     }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  H[0]->bw.ns = bn;
+  if (tc) H[0]->bw.ns = ba;
+  else H[0]->bw.threads = ba;
   H[0]->bw.per_sm = bp;
   if (best_ms) *best_ms = best;
   for (int k = 0; k < n; ++k) H[k]->last_stream = st;

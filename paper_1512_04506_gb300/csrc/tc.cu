@@ -51,9 +51,9 @@ __global__ void __launch_bounds__(160, 1) apply_tc_kernel(const TcApplyArgs a, c
   ring_init(pp, ns, (int)(blockDim.x >> 5) - 1);
   __syncthreads();
   const Ring rg{pp, sm + kPipeBytes, ns, tc_apply_chunk(a.g.nc, NRHS)};
-  long long c = 0;
-  apply_tc_items<NRHS>(a, rg, blockIdx.x, a.g.Vc, gridDim.x, c);
-  if (threadIdx.x == 0) drain(pp, c, ns);
+  RingPos rp;
+  apply_tc_items<NRHS>(a, rg, blockIdx.x, a.g.Vc, gridDim.x, rp);
+  if (threadIdx.x == 0) drain(pp, rp.c, ns);
 }
 
 template <int NRHS>
@@ -63,9 +63,9 @@ __global__ void __launch_bounds__(160, 1) restrict_tc_kernel(const TcRPArgs a, i
   ring_init(pp, ns, (int)(blockDim.x >> 5) - 1);
   __syncthreads();
   const Ring rg{pp, sm + kPipeBytes, ns, tc_restrict_chunk(a.g.ntv, NRHS)};
-  long long c = 0;
-  restrict_tc_items<NRHS>(a, rg, blockIdx.x, a.g.Vc, gridDim.x, c);
-  if (threadIdx.x == 0) drain(pp, c, ns);
+  RingPos rp;
+  restrict_tc_items<NRHS>(a, rg, blockIdx.x, a.g.Vc, gridDim.x, rp);
+  if (threadIdx.x == 0) drain(pp, rp.c, ns);
 }
 
 template <int NRHS>
@@ -75,9 +75,9 @@ __global__ void __launch_bounds__(160, 1) prolong_tc_kernel(const TcRPArgs a, in
   ring_init(pp, ns, (int)(blockDim.x >> 5) - 1);
   __syncthreads();
   const Ring rg{pp, sm + kPipeBytes, ns, tc_prolong_chunk(a.g.ntv)};
-  long long c = 0;
-  prolong_tc_items<NRHS>(a, rg, blockIdx.x, a.g.Vc, gridDim.x, c);
-  if (threadIdx.x == 0) drain(pp, c, ns);
+  RingPos rp;
+  prolong_tc_items<NRHS>(a, rg, blockIdx.x, a.g.Vc, gridDim.x, rp);
+  if (threadIdx.x == 0) drain(pp, rp.c, ns);
 }
 
 template <int NRHS, bool RESTRICT>
@@ -160,7 +160,7 @@ amg_status launch_apply_tc(amg_coarse* h, const void* x, void* y, cudaStream_t s
                                                    (float2*)vout, skip);
   AMG_LAUNCH_CHECK();
   h->launches++;
-  const int threads = 32 + 32 * (nc / 16);
+  const int threads = 32 + 32 * ((nc + 15) / 16);
   const size_t chunk = tc_apply_chunk(nc, NRHS);
   // a short ring: more CTAs per SM (each works through its chunks in order) beat deeper prefetch
   int ns = (int)((32 * 1024) / chunk);
@@ -184,7 +184,7 @@ amg_status launch_apply_tc(amg_coarse* h, const void* x, void* y, cudaStream_t s
 
 amg_status amg_internal_tc_prepare(amg_coarse* h, cudaStream_t st) {
   if (h->p.link_prec == AMG_BF16) {
-    if (h->g.nc % 16 || h->g.nc > 64) return AMG_ERR_UNSUPPORTED;
+    if (h->g.nc % 8 || h->g.nc > 64) return AMG_ERR_UNSUPPORTED;
     const size_t n = (size_t)h->g.Vc * 9 * 2 * h->g.nc * h->g.nc;
     AMG_CUDA_TRY(cudaMalloc(&h->Dtc, n * sizeof(bf16)));
     dc_to_bf16_kernel<<<4 * 152, 256, 0, st>>>(h->Dc64, (bf16*)h->Dtc, h->g.nc, h->g.Vc * 9);
@@ -196,7 +196,7 @@ amg_status amg_internal_tc_prepare(amg_coarse* h, cudaStream_t st) {
   }
   if (h->p.r_prec == AMG_BF16) {
     const Geom& g = h->g;
-    if (g.ntv % 8 || g.Vb % 8) return AMG_ERR_UNSUPPORTED;
+    if (g.ntv % 4 || g.Vb % 8) return AMG_ERR_UNSUPPORTED;
     const size_t n = (size_t)g.Vc * 2 * 2 * g.ntv * g.nagg;
     AMG_CUDA_TRY(cudaMalloc(&h->Rtc, n * sizeof(bf16)));
     r_to_tc_kernel<<<4 * 152, 256, 0, st>>>(h->R64, (bf16*)h->Rtc, g);

@@ -18,8 +18,8 @@
 //   * vectors: rows (apply) or sites (restriction) are placed an odd number of 16-byte units apart.
 //
 // Thread roles: a CTA has 32 + 32 ncw threads; lane 0 of warp 0 issues the bulk copies of every
-// chunk, warps 1 .. ncw consume (warps a job does not need only wait and release).  The chunk
-// counter c runs on across calls, identically in the producer lane and in the consumers.
+// chunk, warps 1 .. ncw consume (warps a job does not need only wait and release).  The ring
+// position runs on across calls, identically in the producer lane and in the consumers.
 #pragma once
 
 #include "amg_internal.cuh"
@@ -54,11 +54,11 @@ __device__ inline void ldsm_x2_trans(unsigned& r0, unsigned& r1, const void* p) 
   asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];" : "=r"(r0), "=r"(r1) : "r"(smem_addr(p)));
 }
 
-// Rotation of the 16-byte pieces of BF16 row r in a row of P pieces (P = 2, 4, 6 or 8): piece c is
+// Rotation of the 16-byte pieces of BF16 row r in a row of P pieces (P = 1 .. 8): piece c is
 // stored at position (c + tc_rot(r, P)) % P.  For 8 consecutive rows r0 .. r0 + 7 (r0 a multiple of
-// 8) and any fixed c, the stored units r P + position are distinct modulo 8.
+// 8) and any fixed c, the stored units r P + position are distinct modulo 8 (odd P needs no rotation).
 __host__ __device__ inline int tc_rot(int r, int P) {
-  return P == 8 ? (r & 7) : (P == 4 ? ((r >> 1) & 3) : ((r >> 2) & 1));
+  return P == 8 ? (r & 7) : P == 4 ? ((r >> 1) & 3) : (P == 2 || P == 6) ? ((r >> 2) & 1) : 0;
 }
 __host__ __device__ inline int tc_pos(int r, int c, int P) { return (c + tc_rot(r, P)) % P; }
 
@@ -106,34 +106,50 @@ __device__ inline void ring_init(Pipe* pp, int ns, int consumers) {
   }
 }
 
+// Position in the ring: chunk count c, its stage s = c % ns and phase parity ph = (c / ns) & 1,
+// advanced without divisions.
+struct RingPos {
+  long long c = 0;
+  int s = 0;
+  unsigned ph = 0;
+  __device__ void advance(int ns) {
+    ++c;
+    if (++s == ns) {
+      s = 0;
+      ph ^= 1u;
+    }
+  }
+};
+
 // Producer side of one chunk: wait until stage s is free, announce the bytes.
-__device__ inline unsigned char* ring_acquire(const Ring& rg, long long c, unsigned bytes, unsigned* err, bool& ok) {
+__device__ inline unsigned char* ring_acquire(const Ring& rg, const RingPos& rp, unsigned bytes, unsigned* err,
+                                              bool& ok) {
   Pipe* pp = rg.pp;
-  const int s = (int)(c % rg.ns);
-  const long long q = c / rg.ns;
-  if (c >= rg.ns && !wait_phase(&pp->empty[s], (unsigned)((q - 1) & 1), pp)) {
+  if (rp.c >= rg.ns && !wait_phase(&pp->empty[rp.s], rp.ph ^ 1u, pp)) {
     abort_cta(pp, err);
     ok = false;
     return nullptr;
   }
-  mbar_expect_tx(&pp->full[s], bytes);
+  mbar_expect_tx(&pp->full[rp.s], bytes);
   ok = true;
-  return rg.stages + (size_t)s * rg.stride;
+  return rg.stages + (size_t)rp.s * rg.stride;
 }
-// Consumer side: wait for chunk c (warp-uniform result).
-__device__ inline bool ring_wait(const Ring& rg, long long c, unsigned* err) {
+// Consumer side: wait for the chunk at rp (warp-uniform result).
+__device__ inline bool ring_wait(const Ring& rg, const RingPos& rp, unsigned* err) {
   Pipe* pp = rg.pp;
-  const int s = (int)(c % rg.ns);
   bool ok = !pp->abort;
-  if (ok && !wait_phase(&pp->full[s], (unsigned)((c / rg.ns) & 1), pp)) {
+  if (ok && !wait_phase(&pp->full[rp.s], rp.ph, pp)) {
     abort_cta(pp, err);
     ok = false;
   }
   return __all_sync(0xffffffffu, ok);  // the fragment loads and mma need the whole warp
 }
-__device__ inline void ring_release(const Ring& rg, long long c) {
+__device__ inline void ring_release(const Ring& rg, const RingPos& rp) {
   __syncwarp();
-  if ((threadIdx.x & 31) == 0) mbar_arrive(&rg.pp->empty[(int)(c % rg.ns)]);
+  if ((threadIdx.x & 31) == 0) mbar_arrive(&rg.pp->empty[rp.s]);
+}
+__device__ inline const unsigned char* ring_stage(const Ring& rg, const RingPos& rp) {
+  return rg.stages + (size_t)rp.s * rg.stride;
 }
 
 // ------------------------------------------------------------------ coarse apply
@@ -154,7 +170,7 @@ struct TcApplyArgs {
 
 template <int NRHS>
 __device__ void apply_tc_items(const TcApplyArgs& a, const Ring& rg, long long i0, long long i1, long long step,
-                               long long& c) {
+                               RingPos& rp) {
   constexpr int NT = NRHS / 4;  // n-tiles: 8 columns = 4 right-hand sides x (Re, Im)
   constexpr int XU = NRHS / 4 + ((NRHS / 4) & 1 ? 0 : 1);
   Pipe* pp = rg.pp;
@@ -177,13 +193,12 @@ __device__ void apply_tc_items(const TcApplyArgs& a, const Ring& rg, long long i
         bool ok = true;
 #pragma unroll
         for (int d = 0; d < 9; ++d) {
-          unsigned char* st = ring_acquire(rg, c, dbytes + xbytes, a.err, ok);
+          unsigned char* st = ring_acquire(rg, rp, dbytes + xbytes, a.err, ok);
           if (!ok) break;
-          const int s = (int)(c % rg.ns);
-          bulk_load(st, a.D + (i * 9 + d) * 2LL * nc * nc, dbytes, &pp->full[s]);
+          bulk_load(st, a.D + (i * 9 + d) * 2LL * nc * nc, dbytes, &pp->full[rp.s]);
           bulk_load(st + dbytes, reinterpret_cast<const unsigned char*>(a.X) + (long long)nb[d] * xbytes, xbytes,
-                    &pp->full[s]);
-          ++c;
+                    &pp->full[rp.s]);
+          rp.advance(rg.ns);
         }
         if (!ok) break;
       }
@@ -191,29 +206,33 @@ __device__ void apply_tc_items(const TcApplyArgs& a, const Ring& rg, long long i
     return;
   }
   const int w = warp - 1;
-  const bool active = w < nc / 16;
+  const int KS = (nc + 15) / 16;  // m-tiles and k-steps (nc a multiple of 8: the last may be half)
+  const bool active = w < KS;
   const int g = lane >> 2, tq = lane & 3, q = lane >> 3, li = lane & 7;
   const bool even = !(g & 1);
   // ldmatrix row of this lane: A (non-trans) matrix q = rows 8 (q & 1) .., pieces + (q >> 1);
-  // B (trans) matrix q = k rows 8 (q & 1) .., n-tile + (q >> 1)
-  const int arow = w * 16 + 8 * (q & 1) + li;
+  // B (trans) matrix q = k rows 8 (q & 1) .., n-tile + (q >> 1).  Rows past nc are clamped (their
+  // results are not stored); k columns past nc are zeroed in A.
+  const int arow = min(w * 16 + 8 * (q & 1) + li, nc - 1);
   for (long long i = i0; i < i1; i += step) {
     float acc[NT][4], acc2[NT][4];  // products with the Re and the Im plane (two shorter mma chains)
 #pragma unroll
     for (int t = 0; t < NT; ++t)
 #pragma unroll
       for (int u = 0; u < 4; ++u) acc[t][u] = acc2[t][u] = 0.f;
-    for (int d = 0; d < 9; ++d, ++c) {
-      const bool ok = ring_wait(rg, c, a.err);
+    for (int d = 0; d < 9; ++d) {
+      const bool ok = ring_wait(rg, rp, a.err);
       if (ok && active) {
-        const unsigned char* Ds = rg.stages + (size_t)(c % rg.ns) * rg.stride;
+        const unsigned char* Ds = ring_stage(rg, rp);
         const unsigned char* Xs = Ds + dbytes;
-        for (int ks = 0; ks < nc / 16; ++ks) {
+        for (int ks = 0; ks < KS; ++ks) {
           unsigned are[4], aim[4];
-          const unsigned char* ap = Ds + (size_t)arow * nc * 2 + tc_pos(arow, 2 * ks + (q >> 1), P) * 16;
+          const int apc = min(2 * ks + (q >> 1), P - 1);
+          const unsigned char* ap = Ds + (size_t)arow * nc * 2 + tc_pos(arow, apc, P) * 16;
           ldsm_x4(are, ap);
           ldsm_x4(aim, ap + (size_t)nc * nc * 2);
-          const unsigned char* bp = Xs + (size_t)(16 * ks + 8 * (q & 1) + li) * XU * 16;
+          if (16 * ks + 8 >= nc) are[2] = are[3] = aim[2] = aim[3] = 0u;
+          const unsigned char* bp = Xs + (size_t)min(16 * ks + 8 * (q & 1) + li, nc - 1) * XU * 16;
 #pragma unroll
           for (int t = 0; t < NT; t += 2) {
             unsigned b[4];
@@ -237,7 +256,8 @@ __device__ void apply_tc_items(const TcApplyArgs& a, const Ring& rg, long long i
           }
         }
       }
-      ring_release(rg, c);
+      ring_release(rg, rp);
+      rp.advance(rg.ns);
     }
     // tile t, lane (g, tq): (acc0, acc1) = (Re, Im) of row 16 w + g, right-hand side 4 t + tq;
     // (acc2, acc3) the same for row 16 w + g + 8
@@ -246,7 +266,9 @@ __device__ void apply_tc_items(const TcApplyArgs& a, const Ring& rg, long long i
 #pragma unroll
       for (int t = 0; t < NT; ++t) {
         a.y[(i * nc + row) * NRHS + 4 * t + tq] = make_float2(acc[t][0] + acc2[t][0], acc[t][1] + acc2[t][1]);
-        a.y[(i * nc + row + 8) * NRHS + 4 * t + tq] = make_float2(acc[t][2] + acc2[t][2], acc[t][3] + acc2[t][3]);
+        if (row + 8 < nc)
+          a.y[(i * nc + row + 8) * NRHS + 4 * t + tq] =
+              make_float2(acc[t][2] + acc2[t][2], acc[t][3] + acc2[t][3]);
       }
     }
   }
@@ -276,13 +298,13 @@ struct TcRPArgs {
 
 template <int NRHS>
 __device__ void restrict_tc_items(const TcRPArgs& a, const Ring& rg, long long i0, long long i1, long long step,
-                                  long long& c) {
+                                  RingPos& rp) {
   constexpr int MT = (NRHS + 7) / 8;      // m-tiles per aggregate (16 rows = 8 rhs x (Re, Im))
   constexpr int PIECES = NRHS / 4;        // 16-byte pieces of one fine-vector row
   constexpr int YSITE = 48 * NRHS + 16;   // stage bytes per site (odd number of 16-byte units)
   constexpr int XPITCH = 4 * (NRHS / 4 + ((NRHS / 4) & 1 ? 0 : 1));  // pairs per BF16 coarse row
   Pipe* pp = rg.pp;
-  const int ntv = a.g.ntv, cpb = (int)(a.g.Vb / 8), NTL = ntv / 8;
+  const int ntv = a.g.ntv, cpb = (int)(a.g.Vb / 8), NTL = (ntv + 7) / 8;  // ntv a multiple of 4
   const unsigned rbytes = (unsigned)(2 * 2 * ntv * 48 * sizeof(bf16));
   const unsigned char* Y = reinterpret_cast<const unsigned char*>(a.in);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -292,15 +314,14 @@ __device__ void restrict_tc_items(const TcRPArgs& a, const Ring& rg, long long i
         const long long origin = block_origin(a.g, blk);
         bool ok = true;
         for (int cc = 0; cc < cpb; ++cc) {
-          unsigned char* st = ring_acquire(rg, c, rbytes + 8 * 48 * NRHS, a.err, ok);
+          unsigned char* st = ring_acquire(rg, rp, rbytes + 8 * 48 * NRHS, a.err, ok);
           if (!ok) break;
-          const int s = (int)(c % rg.ns);
-          bulk_load(st, a.R + (blk * cpb + cc) * (long long)(rbytes / sizeof(bf16)), rbytes, &pp->full[s]);
+          bulk_load(st, a.R + (blk * cpb + cc) * (long long)(rbytes / sizeof(bf16)), rbytes, &pp->full[rp.s]);
           for (int sl = 0; sl < 8; ++sl) {
             const long long site = block_site_fast(a.g, origin, 8 * cc + sl);
-            bulk_load(st + rbytes + sl * YSITE, Y + site * 48 * NRHS, 48 * NRHS, &pp->full[s]);
+            bulk_load(st + rbytes + sl * YSITE, Y + site * 48 * NRHS, 48 * NRHS, &pp->full[rp.s]);
           }
-          ++c;
+          rp.advance(rg.ns);
         }
         if (!ok) break;
       }
@@ -321,10 +342,10 @@ __device__ void restrict_tc_items(const TcRPArgs& a, const Ring& rg, long long i
     for (int t = 0; t < 4; ++t)
 #pragma unroll
       for (int u = 0; u < 4; ++u) acc[t][u] = 0.f;
-    for (int cc = 0; cc < cpb; ++cc, ++c) {
-      const bool ok = ring_wait(rg, c, a.err);
+    for (int cc = 0; cc < cpb; ++cc) {
+      const bool ok = ring_wait(rg, rp, a.err);
       if (ok && active) {
-        const unsigned char* st = rg.stages + (size_t)(c % rg.ns) * rg.stride;
+        const unsigned char* st = ring_stage(rg, rp);
         const unsigned char* Ys = st + rbytes;
 #pragma unroll
         for (int ks = 0; ks < 3; ++ks) {
@@ -343,7 +364,8 @@ __device__ void restrict_tc_items(const TcRPArgs& a, const Ring& rg, long long i
             for (int t = 0; t < 4; t += 2) {
               if (t >= NTL) break;
               unsigned b[4];
-              // B (non-trans) matrix q: rows j = 8 (t + (q >> 1)) + li, k-piece 2 ks + (q & 1)
+              // B (non-trans) matrix q: rows j = 8 (t + (q >> 1)) + li, k-piece 2 ks + (q & 1); rows past
+              // ntv (last tile when ntv % 8 = 4) read finite data of the stage and are not stored
               if (t + 1 < NTL) {
                 const int j = 8 * (t + (q >> 1)) + li;
                 ldsm_x4(b, Rp + (size_t)j * 96 + tc_pos(j, 2 * ks + (q & 1), 6) * 16);
@@ -361,7 +383,8 @@ __device__ void restrict_tc_items(const TcRPArgs& a, const Ring& rg, long long i
           }
         }
       }
-      ring_release(rg, c);
+      ring_release(rg, rp);
+      rp.advance(rg.ns);
     }
     // tile t, lane (g, tq): rows g (right-hand side 8 mt + g / 2, Re for even g, Im for odd g) and
     // g + 8 (right-hand side + 4); columns j = 8 t + 2 tq, + 1.  Even lanes write column 2 tq, odd
@@ -376,7 +399,7 @@ __device__ void restrict_tc_items(const TcRPArgs& a, const Ring& rg, long long i
           const float x0 = acc[t][2 * u], x1 = acc[t][2 * u + 1];
           const float recv = partnerf(even ? x1 : x0);
           const int r = 8 * mt + (g >> 1) + 4 * u, j = 8 * t + 2 * tq + (g & 1);
-          if (r < NRHS) {
+          if (r < NRHS && j < ntv) {
             const float2 v = even ? make_float2(x0, recv) : make_float2(recv, x1);
             if (a.fp32_out) yc[((blk * 2 + hw) * ntv + j) * NRHS + r] = v;
             if (a.rows) a.rows[((blk * 2 + hw) * ntv + j) * XPITCH + r] = __floats2bfloat162_rn(v.x, v.y);
@@ -389,7 +412,7 @@ __device__ void restrict_tc_items(const TcRPArgs& a, const Ring& rg, long long i
 
 template <int NRHS>
 __device__ void prolong_tc_items(const TcRPArgs& a, const Ring& rg, long long i0, long long i1, long long step,
-                                 long long& c) {
+                                 RingPos& rp) {
   constexpr int MT = (NRHS + 7) / 8;
   Pipe* pp = rg.pp;
   const int ntv = a.g.ntv, cpb = (int)(a.g.Vb / 8);
@@ -400,11 +423,10 @@ __device__ void prolong_tc_items(const TcRPArgs& a, const Ring& rg, long long i0
       for (long long blk = i0; blk < i1 && !pp->abort; blk += step) {
         bool ok = true;
         for (int cc = 0; cc < cpb; ++cc) {
-          unsigned char* st = ring_acquire(rg, c, chunk, a.err, ok);
+          unsigned char* st = ring_acquire(rg, rp, chunk, a.err, ok);
           if (!ok) break;
-          bulk_load(st, a.R + (blk * cpb + cc) * (long long)(chunk / sizeof(bf16)), chunk,
-                    &pp->full[(int)(c % rg.ns)]);
-          ++c;
+          bulk_load(st, a.R + (blk * cpb + cc) * (long long)(chunk / sizeof(bf16)), chunk, &pp->full[rp.s]);
+          rp.advance(rg.ns);
         }
         if (!ok) break;
       }
@@ -416,7 +438,7 @@ __device__ void prolong_tc_items(const TcRPArgs& a, const Ring& rg, long long i0
   const int g = lane >> 2, tq = lane & 3, q = lane >> 3, li = lane & 7;
   const bool even = !(g & 1);
   const int hw = w / MT, mt = w % MT;
-  const int KS = (ntv + 15) / 16;  // k-steps over j (ntv = 8, 16, 24 or 32)
+  const int KS = (ntv + 15) / 16;  // k-steps over j (ntv a multiple of 4, at most 32); A is zero past ntv
   const float2* xc = reinterpret_cast<const float2*>(a.in);
   __nv_bfloat162* X = reinterpret_cast<__nv_bfloat162*>(a.out);
   for (long long blk = i0; blk < i1; blk += step) {
@@ -441,10 +463,10 @@ __device__ void prolong_tc_items(const TcRPArgs& a, const Ring& rg, long long i0
         ap[ks][u] = pack_bf16(plo, phi);
       }
     const long long origin = block_origin(a.g, blk);
-    for (int cc = 0; cc < cpb; ++cc, ++c) {
-      const bool ok = ring_wait(rg, c, a.err);
+    for (int cc = 0; cc < cpb; ++cc) {
+      const bool ok = ring_wait(rg, rp, a.err);
       if (ok && active) {
-        const unsigned char* st = rg.stages + (size_t)(c % rg.ns) * rg.stride;
+        const unsigned char* st = ring_stage(rg, rp);
         float acc[6][4];
 #pragma unroll
         for (int t = 0; t < 6; ++t)
@@ -516,7 +538,8 @@ __device__ void prolong_tc_items(const TcRPArgs& a, const Ring& rg, long long i0
             *reinterpret_cast<uint4*>(X + (site * 12 + 6 * hw + t) * NRHS + r) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
         }
       }
-      ring_release(rg, c);
+      ring_release(rg, rp);
+      rp.advance(rg.ns);
     }
   }
 }

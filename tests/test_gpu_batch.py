@@ -142,7 +142,7 @@ def test_batch_bounded_wait_reports_timeout(amg, batch):
 # A batch mixing precisions: an FP32 lattice with one right-hand side and two BF16 lattices that
 # run on the tensor cores (R, D_c and fine vectors BF16; 4 and 12 right-hand sides).
 MIXED = [((8, 8, 8, 8), (4, 4, 4, 4), 8, 0.2, 1, "fp32"),
-         ((8, 8, 8, 8), (4, 4, 4, 4), 16, 0.3, 4, "bf16"),
+         ((8, 8, 8, 8), (4, 4, 4, 4), 20, 0.3, 4, "bf16"),
          ((8, 8, 8, 12), (4, 4, 4, 4), 24, 0.4, 12, "bf16")]
 U_BF16 = 2.0 ** -8
 

@@ -68,8 +68,9 @@ class TcCase:
         self.amg.amg_destroy(self.h)
 
 
-@pytest.fixture(scope="module", params=[((8, 8, 8, 8), (4, 4, 4, 4), 24), ((8, 4, 8, 12), (4, 2, 4, 4), 16)],
-                ids=["8^4_b4_ntv24", "8x4x8x12_b4x2x4x4_ntv16"])
+@pytest.fixture(scope="module", params=[((8, 8, 8, 8), (4, 4, 4, 4), 24), ((8, 4, 8, 12), (4, 2, 4, 4), 16),
+                                        ((8, 8, 8, 8), (4, 4, 4, 4), 20)],
+                ids=["8^4_b4_ntv24", "8x4x8x12_b4x2x4x4_ntv16", "8^4_b4_ntv20_half_tiles"])
 def case(amg, request):
     L, B, ntv = request.param
     c = TcCase(amg, L, B, ntv, 404)
