@@ -444,8 +444,8 @@ amg_status launch_apply_tma(amg_coarse* h, const LT* D, const float* dscale, con
   if (G < 1) return AMG_ERR_UNSUPPORTED;
   if (G > nc) G = nc;
   const size_t chunk = (size_t)nc * nc * sizeof(LT);
-  int ns = (int)((64 * 1024) / chunk);
-  ns = ns < 2 ? 2 : (ns > 6 ? 6 : ns);
+  // three stages: a short ring lets more CTAs share an SM, which beats deeper prefetch here
+  const int ns = 3;
   const size_t smem = kPipeBytes + ns * chunk + (size_t)2 * 9 * nc * NR * sizeof(AT) + (size_t)G * nc * NR * sizeof(AT);
   if (smem > 227 * 1024) return AMG_ERR_UNSUPPORTED;
   int grid = 0;
