@@ -13,6 +13,8 @@ Modules (each function cites the passage of arXiv:1512.04506 it follows):
                  restriction, coarse-operator application, prolongation
                  (Alg. 2, Alg. 5, Eq. R, Eq. cgo, Eq. dagger).
 * ``krylov``  -- the restarted FGMRES coarse solve of Alg. 2.
+* ``evenodd`` -- the even/odd (Schur complement) reduction of the coarse system
+                 that Alg. 2's coarse solve is preconditioned with.
 
 All arithmetic is complex128.  Where the paper is silent (gamma basis, sign
 and normalisation of D, the clover term, boundary conditions) the readings
