@@ -10,6 +10,8 @@
  *                                                                  coarse-grid operator"]
  *   prolong    x = P x_c, P = R^dagger                            [Alg. 2]
  *   solve      x_c ~ D_c^{-1} y_c by restarted FGMRES              [Alg. 2, coarse-grid solve]
+ *   solve_eo   the same with the even/odd (Schur complement) reduction [Alg. 2, "even/odd
+ *              preconditioning" of the coarse solve]
  *   batch_cgc  x = P D_c R y for several lattices in one launch    [Alg. 2; persistent threads of Sec. 3]
  *
  * Conventions (all device buffers are owned by the caller unless stated):
@@ -152,6 +154,37 @@ size_t amg_noalloc_scratch_bytes(void);
 amg_status amg_coarse_solve_mixed(amg_handle h_outer, amg_handle h_inner, const void *d_b, void *d_x,
                                   int nrhs, double tol, double inner_tol, int restart,
                                   int max_inner_applies, int max_outer, void *stream, double *info);
+
+/*
+ * Even/odd-reduced coarse solve [Alg. 2: the coarse system is solved by FGMRES with even/odd
+ * preconditioning].  Coarse sites split by parity (x + y + z + t) mod 2; D_c couples only
+ * opposite parities off the diagonal, so with the odd half eliminated the coarse system becomes
+ *   S x_e = b_e - D_eo D_oo^-1 b_o,   S = D_ee - D_eo D_oo^-1 D_oe,   x_o = D_oo^-1 (b_o - D_oe x_e).
+ * Half vectors [Vc/2][2 ntv][nrhs] list the sites of one parity in lexicographic order (site i is
+ * entry i / 2 of its half).  Needs every coarse extent L[mu]/B[mu] even, FP64 or FP32 storage of
+ * D_c with coarse vectors of the same precision, and nrhs <= min(16, max_nrhs).
+ *
+ * amg_setup_evenodd -- inverts the self block D_c[i][0] of every odd site (Gauss-Jordan with
+ * partial pivoting, FP64) and allocates the half-vector workspace (owned by the handle).
+ * Synchronises the stream.  AMG_ERR_UNSUPPORTED for an odd coarse extent or another precision,
+ * AMG_ERR_NONFINITE when a self block is singular.  A second call does nothing.
+ */
+amg_status amg_setup_evenodd(amg_handle h, void *stream);
+/* y_e = S x_e on half vectors (d_xe, d_ye: [Vc/2][2 ntv][nrhs], must not overlap). */
+amg_status amg_schur_apply(amg_handle h, const void *d_xe, void *d_ye, int nrhs, void *stream);
+/*
+ * amg_coarse_solve_eo -- D_c x = b for full coarse vectors through the reduction: FGMRES(restart)
+ * on S (arguments and info as for amg_coarse_solve; the counts and residuals are those of the
+ * reduced system, whose relative residual equals |b - D_c x| / |b_e - D_eo D_oo^-1 b_o|; each
+ * application of S streams about the bytes of one application of D_c).
+ */
+amg_status amg_coarse_solve_eo(amg_handle h, const void *d_b, void *d_x, int nrhs, double tol,
+                               int restart, int max_applies, void *stream, double *info);
+/* amg_cgc_eo -- x = P x_c with x_c from amg_coarse_solve_eo(R y); arguments as amg_cgc. */
+amg_status amg_cgc_eo(amg_handle h, const void *d_y, void *d_x, int nrhs, double tol, int restart,
+                      int max_applies, void *stream, double *info);
+/* D_oo^-1 in FP64, [Vc/2][2 ntv][2 ntv] row-major by odd half index (synchronises). */
+amg_status amg_export_Dinv(amg_handle h, void *out);
 
 /*
  * amg_cgc -- one coarse-grid correction, Alg. 2: x = P FGMRES(D_c, R y).

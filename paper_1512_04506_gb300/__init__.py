@@ -65,6 +65,11 @@ _proto = {
     "amg_coarse_solve_noalloc": [_vp, _vp, _vp, _i, _d, _i, _i, _vp, ctypes.POINTER(_d)],
     "amg_coarse_solve_mixed": [_vp, _vp, _vp, _vp, _i, _d, _d, _i, _i, _i, _vp, ctypes.POINTER(_d)],
     "amg_cgc": [_vp, _vp, _vp, _i, _d, _i, _i, _vp, ctypes.POINTER(_d)],
+    "amg_setup_evenodd": [_vp, _vp],
+    "amg_schur_apply": [_vp, _vp, _vp, _i, _vp],
+    "amg_coarse_solve_eo": [_vp, _vp, _vp, _i, _d, _i, _i, _vp, ctypes.POINTER(_d)],
+    "amg_cgc_eo": [_vp, _vp, _vp, _i, _d, _i, _i, _vp, ctypes.POINTER(_d)],
+    "amg_export_Dinv": [_vp, _vp],
     "amg_batch_cgc": [ctypes.POINTER(_vp), _i, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                       ctypes.POINTER(_i), _vp],
     "amg_batch_autotune": [ctypes.POINTER(_vp), _i, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
@@ -210,6 +215,33 @@ def amg_cgc(h, y, x, nrhs=1, tol=0.05, restart=30, max_applies=200, stream=None,
     buf = _info(nrhs, info)
     _check(lib.amg_cgc(h, ptr(y), ptr(x), nrhs, tol, restart, max_applies, stream_ptr(stream), buf), "amg_cgc")
     return _info_out(buf, nrhs)
+
+
+def amg_setup_evenodd(h, stream=None):
+    return _check(lib.amg_setup_evenodd(h, stream_ptr(stream)), "amg_setup_evenodd")
+
+
+def amg_schur_apply(h, xe, ye, nrhs=1, stream=None):
+    return _check(lib.amg_schur_apply(h, ptr(xe), ptr(ye), nrhs, stream_ptr(stream)), "amg_schur_apply")
+
+
+def amg_coarse_solve_eo(h, b, x, nrhs=1, tol=0.05, restart=30, max_applies=200, stream=None, info=True):
+    """Even/odd-reduced coarse solve; returns [(applications of S, reduced relative residual)]."""
+    buf = _info(nrhs, info)
+    _check(lib.amg_coarse_solve_eo(h, ptr(b), ptr(x), nrhs, tol, restart, max_applies, stream_ptr(stream), buf),
+           "amg_coarse_solve_eo")
+    return _info_out(buf, nrhs)
+
+
+def amg_cgc_eo(h, y, x, nrhs=1, tol=0.05, restart=30, max_applies=200, stream=None, info=True):
+    buf = _info(nrhs, info)
+    _check(lib.amg_cgc_eo(h, ptr(y), ptr(x), nrhs, tol, restart, max_applies, stream_ptr(stream), buf),
+           "amg_cgc_eo")
+    return _info_out(buf, nrhs)
+
+
+def amg_export_Dinv(h, out):
+    return _check(lib.amg_export_Dinv(h, ptr(out)), "amg_export_Dinv")
 
 
 def amg_batch_cgc(hs, ys, xs, nrhs, stream=None):

@@ -131,6 +131,11 @@ struct amg_coarse {
   void* tc_x = nullptr;       // BF16 planes of the coarse input of the tensor-core apply
   size_t tc_xbytes = 0;
   int* nbr = nullptr;         // [Vc][9]
+  double2* Dinv64 = nullptr;  // even/odd: inverses of the odd sites' self blocks [Vc/2][nc][nc] (row-major)
+  void* Dinvq = nullptr;      // the same in link_prec, apply layout [Vc/2][nc col][nc row]
+  int* eo_site = nullptr;     // [2][Vc/2]: site of half index h of parity p
+  void* eo_tmp = nullptr;     // even/odd half vectors (solve workspace)
+  size_t eo_tmp_bytes = 0;
   int* soff = nullptr;        // [Vb] site offsets inside a block (g.soff points here)
   unsigned int* err = nullptr;  // device error word
   float setup_ms[4] = {0, 0, 0, 0};
@@ -167,6 +172,12 @@ void amg_note_error(const char* fmt, ...);
     }                                                     \
   } while (0)
 
+#define AMG_TRY_INTERNAL(call)          \
+  do {                                  \
+    amg_status s_ = (call);             \
+    if (s_ != AMG_OK) return s_;        \
+  } while (0)
+
 inline bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
 inline size_t vec_elem_bytes(amg_prec p) {
@@ -193,6 +204,19 @@ amg_status amg_internal_tc_prepare(amg_coarse* h, cudaStream_t s);
 void amg_internal_free_tc(amg_coarse* h);
 // Coarse application for the solver: CTAs return at once while *skip != 0; with xscale the input
 // is xc * xscale[r] and that scaled input is also stored to vout (both may be null).
+// Even/odd stencil piece (see eo_apply_kernel in stream.cu); parity of the output half.
+amg_status amg_internal_eo_apply(amg_coarse* h, int parity, int d0, int d1, bool inv0, const void* s0, bool sc0,
+                                 const void* s1, double c1, bool sc1, const void* vadd, double delta, void* y,
+                                 void* vout, const double* xscale, const int* skip, int nrhs, cudaStream_t st);
+// y_e = S x_e with the Schur complement S = D_ee - D_eo D_oo^-1 D_oe (evenodd.cu); same extras as
+// amg_internal_apply_ex, for the FGMRES driver.
+amg_status amg_internal_schur_apply(amg_coarse* h, const void* xe, void* ye, int nrhs, cudaStream_t s,
+                                    const int* skip, const double* xscale, void* vout);
+typedef amg_status (*amg_apply_fn)(amg_coarse*, const void*, void*, int, cudaStream_t, const int*, const double*,
+                                   void*);
+// FGMRES on an operator over `rows` coarse rows (Vc nc for D_c, Vc nc / 2 for the Schur complement).
+amg_status amg_internal_solve_op(amg_coarse* h, long long rows, amg_apply_fn op, const void* b, void* x, int nrhs,
+                                 double tol, int restart, int max_applies, cudaStream_t s, double* info);
 amg_status amg_internal_apply_ex(amg_coarse* h, const void* xc, void* yc, int nrhs, cudaStream_t s,
                                  const int* skip, const double* xscale, void* vout);
 // Tensor-core (BF16) forms for nrhs = 4, 8, 12, 16.

@@ -77,6 +77,10 @@ void free_handle(amg_coarse* h) {
   cudaFree(h->Dscale);
   cudaFree(h->nbr);
   cudaFree(h->soff);
+  cudaFree(h->Dinv64);
+  cudaFree(h->Dinvq);
+  cudaFree(h->eo_site);
+  cudaFree(h->eo_tmp);
   cudaFree(h->err);
   cudaFree(h->sw.buf);
   if (h->sw.hflag) {

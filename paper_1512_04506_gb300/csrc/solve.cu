@@ -339,10 +339,8 @@ size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 size_t scal_doubles(int nrhs, int m) { return (size_t)nrhs * ((m + 1) * m + 3 * m + 1) * 2 + 3 * (size_t)nrhs; }
 
 template <typename CT>
-amg_status solve_impl(amg_coarse* h, const CT* b, CT* x, int nrhs, double tol, int m, int max_applies,
-                      cudaStream_t st, double* info, unsigned char* ws, bool poll) {
-  const Geom& g = h->g;
-  const long long rows = g.Vc * g.nc;
+amg_status solve_impl(amg_coarse* h, long long rows, amg_apply_fn op, const CT* b, CT* x, int nrhs, double tol, int m,
+                      int max_applies, cudaStream_t st, double* info, unsigned char* ws, bool poll) {
   const long long vstride = rows * nrhs;
   FState s;
   s.m = m;
@@ -404,7 +402,7 @@ amg_status solve_impl(amg_coarse* h, const CT* b, CT* x, int nrhs, double tol, i
     const int mc = std::min(m, max_applies - launched);
     for (int j = 0; j < mc && !stop; ++j) {
       // V_j = cur / h_{j,j-1} is written by the application itself, which reads cur scaled
-      amg_status status = amg_internal_apply_ex(h, cur, nxt, nrhs, st, s.done, s.invh, V + j * vstride);
+      amg_status status = op(h, cur, nxt, nrhs, st, s.done, s.invh, V + j * vstride);
       if (status != AMG_OK) return status;
       k_dots<CT><<<dim3(NBLK, j + 1), ST_T, 0, st>>>(s, nxt, V, vstride, j);
       k_update<CT><<<NBLK, ST_T, 0, st>>>(s, nxt, V, vstride, j);
@@ -418,7 +416,7 @@ amg_status solve_impl(amg_coarse* h, const CT* b, CT* x, int nrhs, double tol, i
     AMG_LAUNCH_CHECK();
     h->launches += 1;
     if (launched >= max_applies || stop) break;
-    amg_status status = amg_internal_apply_ex(h, x, cur, nrhs, st, s.done, nullptr, nullptr);
+    amg_status status = op(h, x, cur, nrhs, st, s.done, nullptr, nullptr);
     if (status != AMG_OK) return status;
     ++launched;
     k_residual<CT><<<NBLK, ST_T, 0, st>>>(s, cur, b, 0);
@@ -451,11 +449,47 @@ size_t amg_internal_solve_bytes(const amg_coarse* h, int nrhs, int m) {
 amg_status amg_internal_solve_ws(amg_coarse* h, const void* b, void* x, int nrhs, double tol, int restart,
                                  int max_applies, cudaStream_t s, double* info, void* ws, bool poll) {
   if (nrhs > MAXR || restart < 1 || restart > AMG_MAX_NTV || max_applies < 1) return AMG_ERR_INVALID_ARG;
+  const long long rows = h->g.Vc * h->g.nc;
   if (h->p.vec_prec == AMG_FP64)
-    return solve_impl<double2>(h, (const double2*)b, (double2*)x, nrhs, tol, restart, max_applies, s, info,
-                               (unsigned char*)ws, poll);
-  return solve_impl<float2>(h, (const float2*)b, (float2*)x, nrhs, tol, restart, max_applies, s, info,
-                            (unsigned char*)ws, poll);
+    return solve_impl<double2>(h, rows, amg_internal_apply_ex, (const double2*)b, (double2*)x, nrhs, tol, restart,
+                               max_applies, s, info, (unsigned char*)ws, poll);
+  return solve_impl<float2>(h, rows, amg_internal_apply_ex, (const float2*)b, (float2*)x, nrhs, tol, restart,
+                            max_applies, s, info, (unsigned char*)ws, poll);
+}
+
+namespace {
+amg_status ensure_solve_work(amg_coarse* h, int nrhs, int restart, cudaStream_t s) {
+  SolveWork& sw = h->sw;
+  const size_t need = amg_internal_solve_bytes(h, nrhs, restart);
+  if (need > sw.bytes) {
+    AMG_CUDA_TRY(cudaStreamSynchronize(s));
+    cudaFree(sw.buf);
+    sw.buf = nullptr;
+    sw.bytes = 0;
+    AMG_CUDA_TRY(cudaMalloc(&sw.buf, need));
+    sw.bytes = need;
+  }
+  if (!sw.hflag) {
+    AMG_CUDA_TRY(cudaHostAlloc((void**)&sw.hflag, SolveWork::kRing * sizeof(int), cudaHostAllocDefault));
+    for (int k = 0; k < SolveWork::kRing; ++k)
+      AMG_CUDA_TRY(cudaEventCreateWithFlags(&sw.ev[k], cudaEventDisableTiming));
+  }
+  return AMG_OK;
+}
+}  // namespace
+
+amg_status amg_internal_solve_op(amg_coarse* h, long long rows, amg_apply_fn op, const void* b, void* x, int nrhs,
+                                 double tol, int restart, int max_applies, cudaStream_t s, double* info) {
+  if (nrhs > MAXR || restart < 1 || restart > AMG_MAX_NTV || max_applies < 1) return AMG_ERR_INVALID_ARG;
+  if (rows > h->g.Vc * h->g.nc) return AMG_ERR_INVALID_ARG;  // the workspace is sized for D_c's rows
+  amg_status st = ensure_solve_work(h, nrhs, restart, s);
+  if (st != AMG_OK) return st;
+  unsigned char* ws = (unsigned char*)h->sw.buf;
+  if (h->p.vec_prec == AMG_FP64)
+    return solve_impl<double2>(h, rows, op, (const double2*)b, (double2*)x, nrhs, tol, restart, max_applies, s,
+                               info, ws, true);
+  return solve_impl<float2>(h, rows, op, (const float2*)b, (float2*)x, nrhs, tol, restart, max_applies, s, info,
+                            ws, true);
 }
 
 amg_status amg_internal_solve(amg_coarse* h, const void* b, void* x, int nrhs, double tol, int restart,

@@ -256,6 +256,176 @@ __global__ void __launch_bounds__(288) apply_tma_kernel(const ApplyArgs<LT, NR> 
   }
 }
 
+// ------------------------------------------------------------------ even/odd coarse operator
+// The pieces of the even/odd-reduced coarse system (Schur complement on the even sites).  Items
+// are the Vc/2 sites of one checkerboard parity in half-index order (site = site_of[h]; a
+// neighbour j of the other parity is entry j / 2 of its half vector).  Item h streams chunks
+// d = d0 .. d1 - 1: d = 0 the site's self block, or with inv0 its inverse (stored
+// [Vc/2][nc col][nc row] by half index); d >= 1 the hop block D_c[site][d].  Chunk d multiplies
+//   d = 0:  s0[h]                    (times xscale[r] when sc0; the scaled s0[h] goes to vout)
+//   d >= 1: c1 * s1[nbr(site, d) / 2] (times xscale[r] when sc1)
+// and y[h] = sum + delta vadd[h] (vadd optional).  Same pipeline as apply_tma_kernel.
+template <typename LT, int NR>
+struct EoArgs {
+  using AT = typename Acc<LT>::type;
+  const LT* D;
+  const LT* Dinv;
+  const int* nbr;
+  const int* site_of;
+  const AT* s0;
+  const AT* s1;
+  const AT* vadd;
+  AT* y;
+  AT* vout;
+  const double* xscale;
+  const int* skip;
+  unsigned* err;
+  Geom g;
+  int ld, r0, ns, G, d0, d1, inv0, sc0, sc1;
+  double c1, delta;
+};
+
+template <typename LT, int NR>
+__global__ void __launch_bounds__(288) eo_apply_kernel(const EoArgs<LT, NR> a) {
+  using AT = typename Acc<LT>::type;
+  constexpr int CPL = Vec16<LT>::CPL;
+  if (a.skip && *a.skip) return;
+  extern __shared__ __align__(128) unsigned char sm[];
+  Pipe* pp = reinterpret_cast<Pipe*>(sm);
+  const int nc = a.g.nc, K = 9 * nc, ns = a.ns;
+  const long long nc2 = (long long)nc * nc;
+  const unsigned chunk = (unsigned)(nc2 * sizeof(LT));
+  unsigned char* stages = sm + kPipeBytes;
+  AT* xs = reinterpret_cast<AT*>(stages + (size_t)ns * chunk);  // [2][K][NR]
+  AT* red = xs + (size_t)2 * K * NR;
+  const int ncw = (blockDim.x - 32) >> 5;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < ns; ++s) {
+      mbar_init(&pp->full[s], 1);
+      mbar_init(&pp->empty[s], ncw);
+    }
+    pp->abort = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const long long Vh = a.g.Vc / 2;
+  if (threadIdx.x < 32) {
+    if (threadIdx.x == 0) {
+      long long c = 0;
+      for (long long h = blockIdx.x; h < Vh && !pp->abort; h += gridDim.x) {
+        const long long site = __ldg(a.site_of + h);
+        for (int d = a.d0; d < a.d1; ++d, ++c) {
+          const int s = (int)(c % ns);
+          const long long q = c / ns;
+          if (c >= ns && !wait_phase(&pp->empty[s], (unsigned)((q - 1) & 1), pp)) {
+            abort_cta(pp, a.err);
+            break;
+          }
+          mbar_expect_tx(&pp->full[s], chunk);
+          const LT* src = d == 0 ? (a.inv0 ? a.Dinv + h * nc2 : a.D + site * 9 * nc2) : a.D + (site * 9 + d) * nc2;
+          bulk_load(stages + (size_t)s * chunk, src, chunk, &pp->full[s]);
+        }
+      }
+      drain(pp, c, ns);
+    }
+    return;
+  }
+  const int t = threadIdx.x - 32, nct = blockDim.x - 32;
+  const int Gc = nc / CPL, rc = t % Gc, grp = t / Gc;
+  const AT c1 = AT{(decltype(AT{}.x))a.c1, 0};
+  auto gather = [&](long long h, AT* buf) {
+    const long long site = __ldg(a.site_of + h);
+    for (int e = t; e < K * NR; e += nct) {
+      const int k = e / NR, r = e % NR, d = k / nc, b = k % nc;
+      if (d < a.d0 || d >= a.d1) continue;
+      const AT* src = d == 0 ? a.s0 + (h * nc + b) * a.ld + a.r0 + r
+                             : a.s1 + ((long long)(__ldg(a.nbr + site * 9 + d) >> 1) * nc + b) * a.ld + a.r0 + r;
+      cp_async_elem(buf + e, src);
+    }
+    cp_async_commit();
+  };
+  auto finish = [&](long long h, AT* buf) {
+    cp_async_wait_all();
+    for (int e = t; e < K * NR; e += nct) {
+      const int k = e / NR, r = e % NR, d = k / nc, b = k % nc;
+      if (d < a.d0 || d >= a.d1) continue;
+      AT v = buf[e];
+      if (d == 0) {
+        if (a.sc0) v = scaled(v, a.xscale[a.r0 + r]);
+        if (a.vout) a.vout[(h * nc + b) * a.ld + a.r0 + r] = v;
+      } else {
+        if (a.sc1) v = scaled(v, a.xscale[a.r0 + r]);
+        v = AT{v.x * c1.x, v.y * c1.x};
+      }
+      buf[e] = v;
+    }
+  };
+  long long c = 0;
+  int it = 0;
+  if (blockIdx.x < Vh) {
+    gather(blockIdx.x, xs);
+    finish(blockIdx.x, xs);
+  }
+  consumer_sync(nct);
+  for (long long h = blockIdx.x; h < Vh; h += gridDim.x, ++it) {
+    AT* xcur = xs + (size_t)(it & 1) * K * NR;
+    AT* xnext = xs + (size_t)((it + 1) & 1) * K * NR;
+    const long long hnext = h + gridDim.x;
+    if (hnext < Vh) gather(hnext, xnext);
+    AT acc[CPL][NR];
+#pragma unroll
+    for (int q = 0; q < CPL; ++q)
+#pragma unroll
+      for (int r = 0; r < NR; ++r) acc[q][r] = AT{0, 0};
+    for (int d = a.d0; d < a.d1; ++d, ++c) {
+      const int s = (int)(c % ns);
+      bool ok = !pp->abort;
+      if (ok && !wait_phase(&pp->full[s], (unsigned)((c / ns) & 1), pp)) {
+        abort_cta(pp, a.err);
+        ok = false;
+      }
+      if (ok && grp < a.G) {
+        const LT* blk = reinterpret_cast<const LT*>(stages + (size_t)s * chunk) + rc * CPL;
+        const AT* xd = xcur + (size_t)d * nc * NR;
+#pragma unroll 4
+        for (int b = grp; b < nc; b += a.G) {
+          AT v[CPL];
+          Vec16<LT>::ld(blk + (size_t)b * nc, v);
+#pragma unroll
+          for (int q = 0; q < CPL; ++q)
+#pragma unroll
+            for (int r = 0; r < NR; ++r) cfma(acc[q][r], v[q], xd[b * NR + r]);
+        }
+      }
+      __syncwarp();
+      if ((t & 31) == 0) mbar_arrive(&pp->empty[s]);
+    }
+    if (grp < a.G)
+#pragma unroll
+      for (int q = 0; q < CPL; ++q)
+#pragma unroll
+        for (int r = 0; r < NR; ++r) red[((size_t)grp * nc + rc * CPL + q) * NR + r] = acc[q][r];
+    consumer_sync(nct);
+    for (int e = t; e < nc * NR; e += nct) {
+      AT sum = AT{0, 0};
+      for (int gg = 0; gg < a.G; ++gg) {
+        const AT v = red[(size_t)gg * nc * NR + e];
+        sum.x += v.x;
+        sum.y += v.y;
+      }
+      const long long o = (h * nc + e / NR) * a.ld + a.r0 + e % NR;
+      if (a.vadd) {
+        const AT w = a.vadd[o];
+        sum.x += (decltype(sum.x))a.delta * w.x;
+        sum.y += (decltype(sum.x))a.delta * w.y;
+      }
+      a.y[o] = sum;
+    }
+    if (hnext < Vh) finish(hnext, xnext);
+    consumer_sync(nct);
+  }
+}
+
 // ------------------------------------------------------------------ restriction
 // One CTA per block, launched in block order, so the CTAs resident at any time read neighbouring
 // blocks.  y on the block is staged as ys[h][n][r]; warp w computes rows (h, j) of R_i^h y_i^h,
@@ -458,6 +628,42 @@ amg_status launch_apply_tma(amg_coarse* h, const LT* D, const float* dscale, con
   return AMG_OK;
 }
 
+struct EoCall {
+  int parity, d0, d1, inv0, sc0, sc1;
+  const void *s0, *s1, *vadd;
+  void *y, *vout;
+  double c1, delta;
+  const double* xscale;
+  const int* skip;
+};
+
+template <typename LT, int NR>
+amg_status launch_eo(amg_coarse* h, const EoCall& e, int ld, int r0, cudaStream_t st) {
+  using AT = typename Acc<LT>::type;
+  constexpr int CPL = Vec16<LT>::CPL;
+  const int nc = h->g.nc;
+  if (nc % CPL) return AMG_ERR_UNSUPPORTED;
+  const int threads = 288;
+  const int Gc = nc / CPL;
+  int G = (threads - 32) / Gc;
+  if (G < 1) return AMG_ERR_UNSUPPORTED;
+  if (G > nc) G = nc;
+  const size_t chunk = (size_t)nc * nc * sizeof(LT);
+  const int ns = 3;
+  const size_t smem = kPipeBytes + ns * chunk + (size_t)2 * 9 * nc * NR * sizeof(AT) + (size_t)G * nc * NR * sizeof(AT);
+  if (smem > 227 * 1024) return AMG_ERR_UNSUPPORTED;
+  int grid = 0;
+  amg_status s = grid_for(eo_apply_kernel<LT, NR>, threads, smem, h->g.Vc / 2, &grid);
+  if (s != AMG_OK) return s;
+  EoArgs<LT, NR> a{(const LT*)h->Dq, (const LT*)h->Dinvq, h->nbr, h->eo_site + (size_t)e.parity * (h->g.Vc / 2),
+                   (const AT*)e.s0, (const AT*)e.s1, (const AT*)e.vadd, (AT*)e.y, (AT*)e.vout, e.xscale, e.skip,
+                   h->err, h->g, ld, r0, ns, G, e.d0, e.d1, e.inv0, e.sc0, e.sc1, e.c1, e.delta};
+  eo_apply_kernel<LT, NR><<<grid, threads, smem, st>>>(a);
+  AMG_LAUNCH_CHECK();
+  h->launches++;
+  return AMG_OK;
+}
+
 template <typename ST, int NR>
 amg_status launch_restrict(amg_coarse* h, const ST* R, const ST* y, ST* yc, int ld, int r0, cudaStream_t st) {
   using AT = typename Acc<ST>::type;
@@ -588,4 +794,24 @@ amg_status amg_internal_apply_ex(amg_coarse* h, const void* xc, void* yc, int nr
     default:
       return AMG_ERR_UNSUPPORTED;
   }
+}
+
+amg_status amg_internal_eo_apply(amg_coarse* h, int parity, int d0, int d1, bool inv0, const void* s0, bool sc0,
+                                 const void* s1, double c1, bool sc1, const void* vadd, double delta, void* y,
+                                 void* vout, const double* xscale, const int* skip, int nrhs, cudaStream_t st) {
+  if (!h->Dinvq || !h->eo_site) return AMG_ERR_UNSUPPORTED;
+  const EoCall e{parity, d0, d1, inv0 ? 1 : 0, sc0 ? 1 : 0, sc1 ? 1 : 0, s0, s1, vadd, y, vout, c1, delta, xscale, skip};
+  if (h->p.link_prec == AMG_FP64 && h->p.vec_prec == AMG_FP64)
+    return for_rhs_chunks(nrhs, [&](int r0, int nr) {
+      if (nr == 4) return launch_eo<double2, 4>(h, e, nrhs, r0, st);
+      if (nr == 2) return launch_eo<double2, 2>(h, e, nrhs, r0, st);
+      return launch_eo<double2, 1>(h, e, nrhs, r0, st);
+    });
+  if (h->p.link_prec == AMG_FP32 && h->p.vec_prec != AMG_FP64)
+    return for_rhs_chunks(nrhs, [&](int r0, int nr) {
+      if (nr == 4) return launch_eo<float2, 4>(h, e, nrhs, r0, st);
+      if (nr == 2) return launch_eo<float2, 2>(h, e, nrhs, r0, st);
+      return launch_eo<float2, 1>(h, e, nrhs, r0, st);
+    });
+  return AMG_ERR_UNSUPPORTED;
 }
