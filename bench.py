@@ -219,6 +219,9 @@ def run_gpu(args):
         xh.copy_(x, non_blocking=True)
     torch.cuda.synchronize()
     t_e2e = time.perf_counter() - t0
+    evenodd = None
+    if world == 1 and not args.no_evenodd:
+        evenodd = evenodd_comparison(amg, h, y, x, yc, flush, stream, applies, t_total / args.steps, timed)
     status = amg.amg_sync_status(h)
     amg.amg_destroy(h)
     if status != amg.AMG_OK:
@@ -276,6 +279,8 @@ def run_gpu(args):
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
     }
+    if evenodd is not None:
+        result["evenodd"] = evenodd
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(applies)
     if not args.no_speedup:
@@ -283,6 +288,48 @@ def run_gpu(args):
     if dist:
         dist.destroy_process_group()
     return result, rank
+
+
+def evenodd_comparison(amg, h, y, x, yc, flush, stream, applies, ms_plain, timed):
+    """The even/odd-reduced coarse solve on the same handle: bandwidth of one Schur-complement
+    application (three half-lattice passes; algorithmic bytes = D_c with the odd self blocks
+    replaced by their inverses, plus x_e and y_e), and the coarse-grid correction with the reduced
+    solve against the plain one at the workload's tolerance 0.05 and at 1e-6."""
+    import torch
+    V, Vb, Vc, nc = geometry()
+    t0 = time.perf_counter()
+    amg.amg_setup_evenodd(h, stream)
+    setup_ms = (time.perf_counter() - t0) * 1e3
+    xe = torch.randn((Vc // 2, nc, 1), dtype=torch.complex64, device="cuda")
+    ye = torch.empty_like(xe)
+    t_schur = timed(lambda: amg.amg_schur_apply(h, xe, ye, 1, stream), 50)
+    schur_bytes = Vc * 9 * nc * nc * 8 + Vc * nc * 8
+    peaks, _ = measured_peaks()
+
+    def cgc_ms(fn, n=5):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+        for a, b in evs:
+            flush.zero_()
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in evs) / n
+
+    out = {"setup_ms": round(setup_ms, 2), "schur_apply_us": round(t_schur * 1e6, 1),
+           "schur_GB/s": round(schur_bytes / t_schur / 1e9, 1),
+           "schur_frac": round(schur_bytes / t_schur / 1e9 / peaks["hbm_gbs"], 4)}
+    for tol, key in ((TOL, "tol_0.05"), (1e-6, "tol_1e-6")):
+        ip = amg.amg_cgc(h, y, x, 1, tol, RESTART, 2000, stream, info=True)
+        ie = amg.amg_cgc_eo(h, y, x, 1, tol, RESTART, 2000, stream, info=True)
+        mp = cgc_ms(lambda: amg.amg_cgc(h, y, x, 1, tol, RESTART, 2000, stream, info=False))
+        me = cgc_ms(lambda: amg.amg_cgc_eo(h, y, x, 1, tol, RESTART, 2000, stream, info=False))
+        out[key] = {"plain_applies": ip[0][0], "plain_ms": round(mp, 3), "eo_schur_applies": ie[0][0],
+                    "eo_ms": round(me, 3), "speedup": round(mp / me, 2)}
+    return out
 
 
 def speedup_mixed(seed=20151204 + 3):
@@ -683,6 +730,8 @@ def main():
     ap.add_argument("--workload", default="fp32", choices=["fp32", "tc16", "fp16", "batch"],
                     help="fp32: the default 32^4 workload; tc16: 48^3x96 with 16 RHS on the tensor cores; "
                          "fp16: 200 FP16 coarse applications at 32^3x64; batch: the uneven batch")
+    ap.add_argument("--no-evenodd", action="store_true",
+                    help="skip the even/odd-reduced coarse solve comparison of the default workload")
     ap.add_argument("--batch-precision", default="mixed", choices=["mixed", "fp32"],
                     help="batch workload: BF16 tensor cores for the multi-RHS lattices (mixed) or all FP32")
     ap.add_argument("--lattice", default=None,

@@ -207,7 +207,8 @@ void amg_internal_free_tc(amg_coarse* h);
 // Even/odd stencil piece (see eo_apply_kernel in stream.cu); parity of the output half.
 amg_status amg_internal_eo_apply(amg_coarse* h, int parity, int d0, int d1, bool inv0, const void* s0, bool sc0,
                                  const void* s1, double c1, bool sc1, const void* vadd, double delta, void* y,
-                                 void* vout, const double* xscale, const int* skip, int nrhs, cudaStream_t st);
+                                 void* vout, const double* xscale, const int* skip, int nrhs, cudaStream_t st,
+                                 bool post_inv = false);
 // y_e = S x_e with the Schur complement S = D_ee - D_eo D_oo^-1 D_oe (evenodd.cu); same extras as
 // amg_internal_apply_ex, for the FGMRES driver.
 amg_status amg_internal_schur_apply(amg_coarse* h, const void* xe, void* ye, int nrhs, cudaStream_t s,

@@ -5,10 +5,10 @@
 // all extents even the checkerboard halves (parity (x + y + z + t) mod 2) are not coupled inside a
 // half.  Eliminating the odd half leaves the Schur complement S = D_ee - D_eo D_oo^-1 D_oe on the
 // even sites; FGMRES solves S x_e = b_e - D_eo D_oo^-1 b_o and x_o = D_oo^-1 (b_o - D_oe x_e)
-// follows.  One application of S is three streaming passes over half the sites each
-// (eo_apply_kernel in stream.cu): z_o = D_oe x_e (8 hop blocks per odd site), w_o = D_oo^-1 z_o
-// (the stored inverse), y_e = D_ee x_e - D_eo w_o (self block + 8 hop blocks per even site), i.e.
-// about the bytes of one application of D_c.
+// follows.  One application of S is two streaming passes over half the sites each
+// (eo_apply_kernel in stream.cu): w_o = D_oo^-1 D_oe x_e (8 hop blocks and the stored inverse per
+// odd site), y_e = D_ee x_e - D_eo w_o (self block + 8 hop blocks per even site), i.e. about the
+// bytes of one application of D_c.
 //
 // Half vectors [Vc/2][2 ntv][nrhs] list the sites of one parity in lexicographic order: with an
 // even x extent the site i of either parity is entry i / 2 of its half.
@@ -187,11 +187,9 @@ amg_status eo_solve(amg_coarse* h, const void* b, void* x, int nrhs, double tol,
                                          nullptr, nullptr, nrhs, st));
   AMG_TRY_INTERNAL(amg_internal_solve_op(h, (h->g.Vc / 2) * h->g.nc, amg_internal_schur_apply, rhs, xe, nrhs, tol,
                                          restart, max_applies, st, info));
-  // x_o = D_oo^-1 (b_o - D_oe x_e)
-  AMG_TRY_INTERNAL(amg_internal_eo_apply(h, 1, 1, 9, false, nullptr, false, xe, -1.0, false, bo, 1.0, zo, nullptr,
-                                         nullptr, nullptr, nrhs, st));
-  AMG_TRY_INTERNAL(amg_internal_eo_apply(h, 1, 0, 1, true, zo, false, nullptr, 0.0, false, nullptr, 0.0, wo, nullptr,
-                                         nullptr, nullptr, nrhs, st));
+  // x_o = D_oo^-1 (b_o - D_oe x_e), one pass
+  AMG_TRY_INTERNAL(amg_internal_eo_apply(h, 1, 1, 9, false, nullptr, false, xe, -1.0, false, bo, 1.0, wo, nullptr,
+                                         nullptr, nullptr, nrhs, st, true));
   return split_merge(h, false, xe, wo, x, nrhs, st);
 }
 
@@ -199,13 +197,11 @@ amg_status eo_solve(amg_coarse* h, const void* b, void* x, int nrhs, double tol,
 
 amg_status amg_internal_schur_apply(amg_coarse* h, const void* xe, void* ye, int nrhs, cudaStream_t st,
                                     const int* skip, const double* xscale, void* vout) {
-  void *zo = slot(h, 0, nrhs), *wo = slot(h, 1, nrhs);
+  void* wo = slot(h, 1, nrhs);
   const bool sc = xscale != nullptr;
-  // z_o = D_oe x_e, w_o = D_oo^-1 z_o, y_e = D_ee x_e - D_eo w_o
-  AMG_TRY_INTERNAL(amg_internal_eo_apply(h, 1, 1, 9, false, nullptr, false, xe, 1.0, sc, nullptr, 0.0, zo, nullptr,
-                                         xscale, skip, nrhs, st));
-  AMG_TRY_INTERNAL(amg_internal_eo_apply(h, 1, 0, 1, true, zo, false, nullptr, 0.0, false, nullptr, 0.0, wo, nullptr,
-                                         nullptr, skip, nrhs, st));
+  // w_o = D_oo^-1 D_oe x_e (hops and inverse in one pass), then y_e = D_ee x_e - D_eo w_o
+  AMG_TRY_INTERNAL(amg_internal_eo_apply(h, 1, 1, 9, false, nullptr, false, xe, 1.0, sc, nullptr, 0.0, wo, nullptr,
+                                         xscale, skip, nrhs, st, true));
   return amg_internal_eo_apply(h, 0, 0, 9, false, xe, sc, wo, -1.0, false, nullptr, 0.0, ye, vout, xscale, skip, nrhs,
                                st);
 }

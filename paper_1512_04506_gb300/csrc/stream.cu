@@ -264,7 +264,9 @@ __global__ void __launch_bounds__(288) apply_tma_kernel(const ApplyArgs<LT, NR> 
 // [Vc/2][nc col][nc row] by half index); d >= 1 the hop block D_c[site][d].  Chunk d multiplies
 //   d = 0:  s0[h]                    (times xscale[r] when sc0; the scaled s0[h] goes to vout)
 //   d >= 1: c1 * s1[nbr(site, d) / 2] (times xscale[r] when sc1)
-// and y[h] = sum + delta vadd[h] (vadd optional).  Same pipeline as apply_tma_kernel.
+// and y[h] = sum + delta vadd[h] (vadd optional).  With post_inv (and d0 = 1) one more chunk
+// follows the hops: the inverse self block, applied to that sum (reduced in shared memory), so
+// y[h] = D_ii^-1 (sum + delta vadd[h]).  Same pipeline as apply_tma_kernel.
 template <typename LT, int NR>
 struct EoArgs {
   using AT = typename Acc<LT>::type;
@@ -281,7 +283,7 @@ struct EoArgs {
   const int* skip;
   unsigned* err;
   Geom g;
-  int ld, r0, ns, G, d0, d1, inv0, sc0, sc1;
+  int ld, r0, ns, G, d0, d1, inv0, sc0, sc1, post_inv;
   double c1, delta;
 };
 
@@ -312,9 +314,10 @@ __global__ void __launch_bounds__(288) eo_apply_kernel(const EoArgs<LT, NR> a) {
   if (threadIdx.x < 32) {
     if (threadIdx.x == 0) {
       long long c = 0;
+      const int dend = a.d1 + (a.post_inv ? 1 : 0);  // chunk d1: the inverse self block
       for (long long h = blockIdx.x; h < Vh && !pp->abort; h += gridDim.x) {
         const long long site = __ldg(a.site_of + h);
-        for (int d = a.d0; d < a.d1; ++d, ++c) {
+        for (int d = a.d0; d < dend; ++d, ++c) {
           const int s = (int)(c % ns);
           const long long q = c / ns;
           if (c >= ns && !wait_phase(&pp->empty[s], (unsigned)((q - 1) & 1), pp)) {
@@ -322,7 +325,9 @@ __global__ void __launch_bounds__(288) eo_apply_kernel(const EoArgs<LT, NR> a) {
             break;
           }
           mbar_expect_tx(&pp->full[s], chunk);
-          const LT* src = d == 0 ? (a.inv0 ? a.Dinv + h * nc2 : a.D + site * 9 * nc2) : a.D + (site * 9 + d) * nc2;
+          const LT* src = d == a.d1 ? a.Dinv + h * nc2
+                                    : (d == 0 ? (a.inv0 ? a.Dinv + h * nc2 : a.D + site * 9 * nc2)
+                                              : a.D + (site * 9 + d) * nc2);
           bulk_load(stages + (size_t)s * chunk, src, chunk, &pp->full[s]);
         }
       }
@@ -373,11 +378,8 @@ __global__ void __launch_bounds__(288) eo_apply_kernel(const EoArgs<LT, NR> a) {
     const long long hnext = h + gridDim.x;
     if (hnext < Vh) gather(hnext, xnext);
     AT acc[CPL][NR];
-#pragma unroll
-    for (int q = 0; q < CPL; ++q)
-#pragma unroll
-      for (int r = 0; r < NR; ++r) acc[q][r] = AT{0, 0};
-    for (int d = a.d0; d < a.d1; ++d, ++c) {
+    // one chunk: acc += block(chunk c) * X[xd]
+    auto consume = [&](const AT* xd) {
       const int s = (int)(c % ns);
       bool ok = !pp->abort;
       if (ok && !wait_phase(&pp->full[s], (unsigned)((c / ns) & 1), pp)) {
@@ -386,7 +388,6 @@ __global__ void __launch_bounds__(288) eo_apply_kernel(const EoArgs<LT, NR> a) {
       }
       if (ok && grp < a.G) {
         const LT* blk = reinterpret_cast<const LT*>(stages + (size_t)s * chunk) + rc * CPL;
-        const AT* xd = xcur + (size_t)d * nc * NR;
 #pragma unroll 4
         for (int b = grp; b < nc; b += a.G) {
           AT v[CPL];
@@ -399,27 +400,50 @@ __global__ void __launch_bounds__(288) eo_apply_kernel(const EoArgs<LT, NR> a) {
       }
       __syncwarp();
       if ((t & 31) == 0) mbar_arrive(&pp->empty[s]);
-    }
-    if (grp < a.G)
+      ++c;
+    };
+    // sum over the column groups into out[nc][NR] (+ delta vadd[h])
+    auto reduce_to = [&](AT* out, long long h, bool add) {
+      if (grp < a.G)
+#pragma unroll
+        for (int q = 0; q < CPL; ++q)
+#pragma unroll
+          for (int r = 0; r < NR; ++r) red[((size_t)grp * nc + rc * CPL + q) * NR + r] = acc[q][r];
+      consumer_sync(nct);
+      for (int e = t; e < nc * NR; e += nct) {
+        AT sum = AT{0, 0};
+        for (int gg = 0; gg < a.G; ++gg) {
+          const AT v = red[(size_t)gg * nc * NR + e];
+          sum.x += v.x;
+          sum.y += v.y;
+        }
+        const long long o = (h * nc + e / NR) * a.ld + a.r0 + e % NR;
+        if (add && a.vadd) {
+          const AT w = a.vadd[o];
+          sum.x += (decltype(sum.x))a.delta * w.x;
+          sum.y += (decltype(sum.x))a.delta * w.y;
+        }
+        if (out) out[e] = sum;
+        else a.y[o] = sum;
+      }
+    };
+    auto zero_acc = [&]() {
 #pragma unroll
       for (int q = 0; q < CPL; ++q)
 #pragma unroll
-        for (int r = 0; r < NR; ++r) red[((size_t)grp * nc + rc * CPL + q) * NR + r] = acc[q][r];
-    consumer_sync(nct);
-    for (int e = t; e < nc * NR; e += nct) {
-      AT sum = AT{0, 0};
-      for (int gg = 0; gg < a.G; ++gg) {
-        const AT v = red[(size_t)gg * nc * NR + e];
-        sum.x += v.x;
-        sum.y += v.y;
-      }
-      const long long o = (h * nc + e / NR) * a.ld + a.r0 + e % NR;
-      if (a.vadd) {
-        const AT w = a.vadd[o];
-        sum.x += (decltype(sum.x))a.delta * w.x;
-        sum.y += (decltype(sum.x))a.delta * w.y;
-      }
-      a.y[o] = sum;
+        for (int r = 0; r < NR; ++r) acc[q][r] = AT{0, 0};
+    };
+    zero_acc();
+    for (int d = a.d0; d < a.d1; ++d) consume(xcur + (size_t)d * nc * NR);
+    if (a.post_inv) {
+      // z = sum (+ delta vadd) into the (unused) direction-0 slot, then y = D_ii^-1 z
+      reduce_to(xcur, h, true);
+      consumer_sync(nct);
+      zero_acc();
+      consume(xcur);
+      reduce_to(nullptr, h, false);
+    } else {
+      reduce_to(nullptr, h, true);
     }
     if (hnext < Vh) finish(hnext, xnext);
     consumer_sync(nct);
@@ -629,7 +653,7 @@ amg_status launch_apply_tma(amg_coarse* h, const LT* D, const float* dscale, con
 }
 
 struct EoCall {
-  int parity, d0, d1, inv0, sc0, sc1;
+  int parity, d0, d1, inv0, sc0, sc1, post_inv;
   const void *s0, *s1, *vadd;
   void *y, *vout;
   double c1, delta;
@@ -657,7 +681,7 @@ amg_status launch_eo(amg_coarse* h, const EoCall& e, int ld, int r0, cudaStream_
   if (s != AMG_OK) return s;
   EoArgs<LT, NR> a{(const LT*)h->Dq, (const LT*)h->Dinvq, h->nbr, h->eo_site + (size_t)e.parity * (h->g.Vc / 2),
                    (const AT*)e.s0, (const AT*)e.s1, (const AT*)e.vadd, (AT*)e.y, (AT*)e.vout, e.xscale, e.skip,
-                   h->err, h->g, ld, r0, ns, G, e.d0, e.d1, e.inv0, e.sc0, e.sc1, e.c1, e.delta};
+                   h->err, h->g, ld, r0, ns, G, e.d0, e.d1, e.inv0, e.sc0, e.sc1, e.post_inv, e.c1, e.delta};
   eo_apply_kernel<LT, NR><<<grid, threads, smem, st>>>(a);
   AMG_LAUNCH_CHECK();
   h->launches++;
@@ -798,9 +822,12 @@ amg_status amg_internal_apply_ex(amg_coarse* h, const void* xc, void* yc, int nr
 
 amg_status amg_internal_eo_apply(amg_coarse* h, int parity, int d0, int d1, bool inv0, const void* s0, bool sc0,
                                  const void* s1, double c1, bool sc1, const void* vadd, double delta, void* y,
-                                 void* vout, const double* xscale, const int* skip, int nrhs, cudaStream_t st) {
+                                 void* vout, const double* xscale, const int* skip, int nrhs, cudaStream_t st,
+                                 bool post_inv) {
   if (!h->Dinvq || !h->eo_site) return AMG_ERR_UNSUPPORTED;
-  const EoCall e{parity, d0, d1, inv0 ? 1 : 0, sc0 ? 1 : 0, sc1 ? 1 : 0, s0, s1, vadd, y, vout, c1, delta, xscale, skip};
+  if (post_inv && d0 == 0) return AMG_ERR_INVALID_ARG;  // the inverse takes the place of direction 0
+  const EoCall e{parity, d0, d1, inv0 ? 1 : 0, sc0 ? 1 : 0, sc1 ? 1 : 0, post_inv ? 1 : 0,
+                 s0, s1, vadd, y, vout, c1, delta, xscale, skip};
   if (h->p.link_prec == AMG_FP64 && h->p.vec_prec == AMG_FP64)
     return for_rhs_chunks(nrhs, [&](int r0, int nr) {
       if (nr == 4) return launch_eo<double2, 4>(h, e, nrhs, r0, st);
