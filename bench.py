@@ -136,6 +136,20 @@ def dist_setup():
     return world, rank, local
 
 
+def max_over_ranks(vals, dist, device):
+    """Elementwise maximum of per-rank timings over all ranks (replicas: the job ends with the
+    slowest rank)."""
+    import torch
+    t = torch.tensor(vals, dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def whole_job_gbs(world, step_bytes, steps, seconds):
+    """Whole-job throughput: every rank moved step_bytes per step (weak scaling)."""
+    return world * step_bytes * steps / seconds / 1e9
+
+
 def run_gpu(args):
     import torch
     import paper_1512_04506_gb300 as amg
@@ -227,11 +241,9 @@ def run_gpu(args):
     if status != amg.AMG_OK:
         raise RuntimeError("device error: %s" % amg.amg_status_string(status))
     if dist:
-        t = torch.tensor([t_total, t_e2e], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_total, t_e2e = t.tolist()
-    value = world * step_bytes * args.steps / t_total / 1e9
-    e2e_value = world * step_bytes * args.steps / t_e2e / 1e9
+        t_total, t_e2e = max_over_ranks([t_total, t_e2e], dist, "cuda")
+    value = whole_job_gbs(world, step_bytes, args.steps, t_total)
+    e2e_value = whole_job_gbs(world, step_bytes, args.steps, t_e2e)
     peaks, src = measured_peaks()
     # dominant kernel of the step: largest (launches per step x live launch time)
     live = {"restrict": (t_restrict, 1, parts["restrict"], "restrict y_c = R y (FP32 R)"),
