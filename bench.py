@@ -668,6 +668,8 @@ def run_batch(args):
     import paper_1512_04506_gb300 as amg
     from synth import device as sd
     spec = [((16, 16, 16, 16), 16, 1, 0.2), ((24, 24, 24, 48), 20, 4, 0.3), ((32, 32, 32, 64), 24, 12, 0.4)]
+    if args.lattice == "small":  # the three lattices at 1/2, 1/4 and 1/4 of the volume, for ncu captures
+        spec = [((8, 16, 16, 16), 16, 1, 0.2), ((24, 24, 12, 24), 20, 4, 0.3), ((16, 32, 32, 32), 24, 12, 0.4)]
     st = torch.cuda.current_stream()
     hs, ys, xs, nr = [], [], [], []
     step_bytes = 0
@@ -718,9 +720,9 @@ def run_batch(args):
         "warmup": args.warmup, "ms_per_step": round(1000 * t / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f32" if "bf16" in precs else "f32",
         "data": "synthetic",
-        "config": {"workload": "batch: 16^4 (Ntv 16, 1 RHS) + 24^3x48 (Ntv 20, 4 RHS) + 32^3x64 (Ntv 24, "
-                               "12 RHS), 4^4 blocks; one persistent launch per step, CUDA graph; inputs "
-                               "larger than L2",
+        "config": {"workload": ("batch: 16^4 (Ntv 16, 1 RHS) + 24^3x48 (Ntv 20, 4 RHS) + 32^3x64 (Ntv 24, "
+                                "12 RHS), 4^4 blocks; one persistent launch per step, CUDA graph; inputs "
+                                "larger than L2") if args.lattice != "small" else "reduced-volume variant of batch",
                    "precision": dict(zip(["16^4", "24^3x48", "32^3x64"], precs)),
                    "bytes_per_step": step_bytes, "autotuned_ms": round(best, 4)},
         "roofline": {"bound": "hbm", "kernel": "fused batch (whole launch)", "achieved": round(gbs, 1),
@@ -747,9 +749,10 @@ def main():
     ap.add_argument("--batch-precision", default="mixed", choices=["mixed", "fp32"],
                     help="batch workload: BF16 tensor cores for the multi-RHS lattices (mixed) or all FP32")
     ap.add_argument("--lattice", default=None,
-                    help="Lx,Ly,Lz,Lt override of the 32^4 lattice (smaller cases for ncu captures)")
+                    help="Lx,Ly,Lz,Lt override of the 32^4 lattice (smaller cases for ncu captures); "
+                         "'small' for the batch workload")
     args = ap.parse_args()
-    if args.lattice:
+    if args.lattice and args.workload != "batch":
         global L, WORKLOAD
         L = tuple(int(v) for v in args.lattice.split(","))
         WORKLOAD = "%dx%dx%dx%d variant of %s" % (L + (WORKLOAD,))
