@@ -130,6 +130,9 @@ struct amg_coarse {
   void* Rtc = nullptr;        // BF16 tensor-core layout of R (when r_prec == BF16)
   void* tc_x = nullptr;       // BF16 planes of the coarse input of the tensor-core apply
   size_t tc_xbytes = 0;
+  void* Dtf = nullptr;        // FP32 planes of D_c for the multi-RHS 3 x TF32 apply (link_prec FP32)
+  void* tf_x = nullptr;       // FP32 rows of its coarse input
+  size_t tf_xbytes = 0;
   int* nbr = nullptr;         // [Vc][9]
   double2* Dinv64 = nullptr;  // even/odd: inverses of the odd sites' self blocks [Vc/2][nc][nc] (row-major)
   void* Dinvq = nullptr;      // the same in link_prec, apply layout [Vc/2][nc col][nc row]
@@ -218,6 +221,9 @@ typedef amg_status (*amg_apply_fn)(amg_coarse*, const void*, void*, int, cudaStr
 // FGMRES on an operator over `rows` coarse rows (Vc nc for D_c, Vc nc / 2 for the Schur complement).
 amg_status amg_internal_solve_op(amg_coarse* h, long long rows, amg_apply_fn op, const void* b, void* x, int nrhs,
                                  double tol, int restart, int max_applies, cudaStream_t s, double* info);
+// FP32 D_c, nrhs = 4, 8, 12 or 16: tensor cores with split TF32 operands (tc.cu)
+amg_status amg_internal_apply_tf32(amg_coarse* h, const void* xc, void* yc, int nrhs, cudaStream_t s,
+                                   const int* skip, const double* xscale, void* vout);
 amg_status amg_internal_apply_ex(amg_coarse* h, const void* xc, void* yc, int nrhs, cudaStream_t s,
                                  const int* skip, const double* xscale, void* vout);
 // Tensor-core (BF16) forms for nrhs = 4, 8, 12, 16.

@@ -809,6 +809,8 @@ amg_status amg_internal_apply_ex(amg_coarse* h, const void* xc, void* yc, int nr
       return apply_prec<double2>(h, (const double2*)h->Dq, nullptr, xc, yc, nrhs, s, skip, xscale, vout);
     case AMG_FP32:
       if (h->p.vec_prec == AMG_FP64) return AMG_ERR_UNSUPPORTED;
+      if (h->Dtf && (nrhs == 4 || nrhs == 8 || nrhs == 12 || nrhs == 16))  // one pass for all columns
+        return amg_internal_apply_tf32(h, xc, yc, nrhs, s, skip, xscale, vout);
       return apply_prec<float2>(h, (const float2*)h->Dq, nullptr, xc, yc, nrhs, s, skip, xscale, vout);
     case AMG_FP16_SCALED:
       if (h->p.vec_prec == AMG_FP64) return AMG_ERR_UNSUPPORTED;

@@ -148,6 +148,85 @@ __global__ void bf16_to_dc_kernel(const bf16* __restrict__ in, double2* __restri
   }
 }
 
+// D_c (canonical FP64) -> FP32 planes [Vc][9][2][nc][nc], rows of 16-byte pieces (4 floats)
+// rotated by tc_rot(row, nc / 4), round to nearest (the same FP32 values as the SIMT copy).
+__global__ void dc_to_tf32_kernel(const double2* __restrict__ Dc, float* __restrict__ out, int nc, long long nblk) {
+  const long long n2 = (long long)nc * nc, total = nblk * n2;
+  const int P = nc / 4;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const long long blk = e / n2;
+    const int rem = (int)(e % n2), row = rem / nc, col = rem % nc;
+    const int off = row * nc + tc_pos(row, col / 4, P) * 4 + col % 4;
+    const double2 v = Dc[e];
+    out[blk * 2 * n2 + off] = __double2float_rn(v.x);
+    out[blk * 2 * n2 + n2 + off] = __double2float_rn(v.y);
+  }
+}
+
+// FP32 coarse vector (optionally times xscale[r]; the scaled vector also to vout) -> FP32 rows of
+// tf32_xpitch(NRHS) floats.
+template <int NRHS>
+__global__ void xc_to_f32rows_kernel(const float2* __restrict__ x, float* __restrict__ X, long long rows,
+                                     const double* __restrict__ xscale, float2* __restrict__ vout,
+                                     const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  constexpr int XP = 2 * NRHS + (NRHS % 8 == 0 ? 8 : 0);
+  const long long total = rows * NRHS;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(e % NRHS);
+    float2 v = x[e];
+    if (xscale) {
+      const float f = (float)xscale[r];
+      v.x *= f;
+      v.y *= f;
+    }
+    if (vout) vout[e] = v;
+    *reinterpret_cast<float2*>(X + (e / NRHS) * XP + 2 * r) = v;
+  }
+}
+
+template <int NRHS>
+__global__ void __launch_bounds__(160, 1) apply_tf32_kernel(const TfApplyArgs a, const int* skip, int ns) {
+  if (skip && *skip) return;
+  extern __shared__ __align__(128) unsigned char sm[];
+  Pipe* pp = reinterpret_cast<Pipe*>(sm);
+  ring_init(pp, ns, (int)(blockDim.x >> 5) - 1);
+  __syncthreads();
+  const Ring rg{pp, sm + kPipeBytes, ns, tf32_apply_chunk(a.g.nc, NRHS)};
+  RingPos rp;
+  apply_tf32_items<NRHS>(a, rg, blockIdx.x, a.g.Vc, gridDim.x, rp);
+  if (threadIdx.x == 0) drain(pp, rp.c, ns);
+}
+
+template <int NRHS>
+amg_status launch_apply_tf32(amg_coarse* h, const void* x, void* y, cudaStream_t st, const int* skip,
+                             const double* xscale, void* vout) {
+  const int nc = h->g.nc;
+  const size_t xsite = (size_t)nc * tf32_xpitch(NRHS) * 4;
+  if ((size_t)h->g.Vc * xsite > h->tf_xbytes) return AMG_ERR_INVALID_ARG;  // nrhs > max_nrhs
+  xc_to_f32rows_kernel<NRHS><<<4 * 152, 256, 0, st>>>((const float2*)x, (float*)h->tf_x, h->g.Vc * nc, xscale,
+                                                      (float2*)vout, skip);
+  AMG_LAUNCH_CHECK();
+  h->launches++;
+  const int threads = 32 + 32 * ((nc + 15) / 16);
+  const size_t chunk = tf32_apply_chunk(nc, NRHS);
+  int ns = (int)((56 * 1024) / chunk);
+  ns = ns < 2 ? 2 : (ns > 4 ? 4 : ns);
+  const size_t smem = kPipeBytes + ns * chunk;
+  if (smem > 227 * 1024) return AMG_ERR_UNSUPPORTED;
+  AMG_CUDA_TRY(cudaFuncSetAttribute(apply_tf32_kernel<NRHS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  AMG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, apply_tf32_kernel<NRHS>, threads, smem));
+  if (per_sm < 1) return AMG_ERR_UNSUPPORTED;
+  const long long gmax = (long long)per_sm * sm_count_tc();
+  const int grid = (int)(h->g.Vc < gmax ? h->g.Vc : gmax);
+  TfApplyArgs a{(const float*)h->Dtf, (const float*)h->tf_x, h->nbr, (float2*)y, h->err, h->g};
+  apply_tf32_kernel<NRHS><<<grid, threads, smem, st>>>(a, skip, ns);
+  AMG_LAUNCH_CHECK();
+  h->launches++;
+  return AMG_OK;
+}
+
 size_t tc_xbytes_per_site(const Geom& g, int nrhs) { return (size_t)g.nc * tc_xunits(nrhs) * 16; }
 
 template <int NRHS>
@@ -194,6 +273,17 @@ amg_status amg_internal_tc_prepare(amg_coarse* h, cudaStream_t st) {
     h->tc_xbytes = (size_t)h->g.Vc * tc_xbytes_per_site(h->g, nmax);
     AMG_CUDA_TRY(cudaMalloc(&h->tc_x, h->tc_xbytes));
   }
+  if (h->p.link_prec == AMG_FP32 && h->p.vec_prec == AMG_FP32 && h->g.nc % 8 == 0 && h->g.nc <= 64 &&
+      h->p.max_nrhs >= 4) {
+    // FP32 D_c for the multi-RHS tensor-core apply (3 x TF32)
+    const size_t n = (size_t)h->g.Vc * 9 * 2 * h->g.nc * h->g.nc;
+    AMG_CUDA_TRY(cudaMalloc(&h->Dtf, n * sizeof(float)));
+    dc_to_tf32_kernel<<<4 * 152, 256, 0, st>>>(h->Dc64, (float*)h->Dtf, h->g.nc, h->g.Vc * 9);
+    AMG_LAUNCH_CHECK();
+    const int nmax = h->p.max_nrhs >= 16 ? 16 : h->p.max_nrhs / 4 * 4;
+    h->tf_xbytes = (size_t)h->g.Vc * h->g.nc * tf32_xpitch(nmax) * 4;
+    AMG_CUDA_TRY(cudaMalloc(&h->tf_x, h->tf_xbytes));
+  }
   if (h->p.r_prec == AMG_BF16) {
     const Geom& g = h->g;
     if (g.ntv % 4 || g.Vb % 8) return AMG_ERR_UNSUPPORTED;
@@ -209,7 +299,9 @@ void amg_internal_free_tc(amg_coarse* h) {
   cudaFree(h->Dtc);
   cudaFree(h->Rtc);
   cudaFree(h->tc_x);
-  h->Dtc = h->Rtc = h->tc_x = nullptr;
+  cudaFree(h->Dtf);
+  cudaFree(h->tf_x);
+  h->Dtc = h->Rtc = h->tc_x = h->Dtf = h->tf_x = nullptr;
 }
 
 amg_status amg_internal_export_stored(amg_coarse* h, double2* out) {
@@ -237,6 +329,18 @@ amg_status amg_internal_apply_tc(amg_coarse* h, const void* xc, void* yc, int nr
     case 8: return launch_apply_tc<8>(h, xc, yc, s, skip, xscale, vout);
     case 12: return launch_apply_tc<12>(h, xc, yc, s, skip, xscale, vout);
     case 16: return launch_apply_tc<16>(h, xc, yc, s, skip, xscale, vout);
+    default: return AMG_ERR_UNSUPPORTED;
+  }
+}
+
+amg_status amg_internal_apply_tf32(amg_coarse* h, const void* xc, void* yc, int nrhs, cudaStream_t s,
+                                   const int* skip, const double* xscale, void* vout) {
+  if (!h->Dtf) return AMG_ERR_UNSUPPORTED;
+  switch (nrhs) {
+    case 4: return launch_apply_tf32<4>(h, xc, yc, s, skip, xscale, vout);
+    case 8: return launch_apply_tf32<8>(h, xc, yc, s, skip, xscale, vout);
+    case 12: return launch_apply_tf32<12>(h, xc, yc, s, skip, xscale, vout);
+    case 16: return launch_apply_tf32<16>(h, xc, yc, s, skip, xscale, vout);
     default: return AMG_ERR_UNSUPPORTED;
   }
 }

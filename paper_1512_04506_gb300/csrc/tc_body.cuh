@@ -54,11 +54,12 @@ __device__ inline void ldsm_x2_trans(unsigned& r0, unsigned& r1, const void* p) 
   asm volatile("ldmatrix.sync.aligned.m8n8.x2.trans.shared.b16 {%0,%1}, [%2];" : "=r"(r0), "=r"(r1) : "r"(smem_addr(p)));
 }
 
-// Rotation of the 16-byte pieces of BF16 row r in a row of P pieces (P = 1 .. 8): piece c is
-// stored at position (c + tc_rot(r, P)) % P.  For 8 consecutive rows r0 .. r0 + 7 (r0 a multiple of
-// 8) and any fixed c, the stored units r P + position are distinct modulo 8 (odd P needs no rotation).
+// Rotation of the 16-byte pieces of row r in a row of P pieces: piece c is stored at position
+// (c + tc_rot(r, P)) % P.  For 8 consecutive rows r0 .. r0 + 7 (r0 a multiple of 8) and any fixed
+// c, the stored units r P + position are then distinct modulo 8 (checked for P = 1 .. 16; odd P
+// needs no rotation).
 __host__ __device__ inline int tc_rot(int r, int P) {
-  return P == 8 ? (r & 7) : P == 4 ? ((r >> 1) & 3) : (P == 2 || P == 6) ? ((r >> 2) & 1) : 0;
+  return P % 8 == 0 ? (r & 7) : P % 4 == 0 ? ((r >> 1) & 3) : P % 2 == 0 ? ((r >> 2) & 1) : 0;
 }
 __host__ __device__ inline int tc_pos(int r, int c, int P) { return (c + tc_rot(r, P)) % P; }
 
@@ -540,6 +541,149 @@ __device__ void prolong_tc_items(const TcRPArgs& a, const Ring& rg, long long i0
       }
       ring_release(rg, rp);
       rp.advance(rg.ns);
+    }
+  }
+}
+
+
+// ------------------------------------------------------------------ FP32 coarse apply, 3 x TF32
+// y_c = D_c x_c for FP32 D_c and nrhs = 4 .. 16 right-hand sides on the tensor cores with FP32
+// accuracy: every FP32 operand v is split into v_hi = tf32(v) and v_lo = tf32(v - v_hi) and the
+// product is accumulated as A_hi B_hi + A_hi B_lo + A_lo B_hi (the dropped A_lo B_lo term and the
+// rounding of v_lo are below FP32's own rounding).  mma.sync m16n8k8 (TF32 in, FP32 accumulate).
+// The stage holds D_c[i][d] as two FP32 planes of nc rows (16-byte pieces rotated by tc_rot(r, nc/4))
+// and the neighbour's FP32 coarse rows, tf32_xpitch(nrhs) floats apart (a pitch that is 8 or 24
+// modulo 32 words, so the B-fragment loads hit distinct banks).  Complex products as in the BF16
+// apply (the partner exchange).
+
+__host__ __device__ inline int tf32_xpitch(int nrhs) { return 2 * nrhs + (nrhs % 8 == 0 ? 8 : 0); }
+__host__ __device__ inline unsigned tf32_apply_chunk(int nc, int nrhs) {
+  return (unsigned)(8 * nc * nc + nc * tf32_xpitch(nrhs) * 4);
+}
+
+__device__ inline unsigned tf32_rna(float x) {
+  unsigned r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+__device__ inline void split_tf32(unsigned bits, unsigned& hi, unsigned& lo) {
+  const float x = __uint_as_float(bits);
+  hi = tf32_rna(x);
+  lo = tf32_rna(x - __uint_as_float(hi));
+}
+__device__ inline void mma_tf32(float (&c)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+struct TfApplyArgs {
+  const float* D;  // [Vc][9][2][nc][nc] FP32 planes, rows with rotated pieces
+  const float* X;  // [Vc][nc][tf32_xpitch(nrhs)] FP32 coarse rows
+  const int* nbr;
+  float2* y;       // [Vc][nc][nrhs] FP32
+  unsigned* err;
+  Geom g;
+};
+
+template <int NRHS>
+__device__ void apply_tf32_items(const TfApplyArgs& a, const Ring& rg, long long i0, long long i1, long long step,
+                                 RingPos& rp) {
+  constexpr int NT = NRHS / 4;  // n-tiles of 8 columns = 4 right-hand sides x (Re, Im)
+  constexpr int XP = 2 * NRHS + (NRHS % 8 == 0 ? 8 : 0);
+  Pipe* pp = rg.pp;
+  const int nc = a.g.nc, P = nc / 4;
+  const unsigned dbytes = (unsigned)(8 * nc * nc);
+  const unsigned xbytes = (unsigned)(nc * XP * 4);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp == 0) {
+    if (lane == 0) {
+      int nb[9], nx[9];
+      if (i0 < i1)
+        for (int d = 0; d < 9; ++d) nx[d] = __ldg(a.nbr + i0 * 9 + d);
+      for (long long i = i0; i < i1 && !pp->abort; i += step) {
+#pragma unroll
+        for (int d = 0; d < 9; ++d) nb[d] = nx[d];
+        if (i + step < i1)
+#pragma unroll
+          for (int d = 0; d < 9; ++d) nx[d] = __ldg(a.nbr + (i + step) * 9 + d);
+        bool ok = true;
+#pragma unroll
+        for (int d = 0; d < 9; ++d) {
+          unsigned char* st = ring_acquire(rg, rp, dbytes + xbytes, a.err, ok);
+          if (!ok) break;
+          bulk_load(st, a.D + (i * 9 + d) * 2LL * nc * nc, dbytes, &pp->full[rp.s]);
+          bulk_load(st + dbytes, reinterpret_cast<const unsigned char*>(a.X) + (long long)nb[d] * xbytes, xbytes,
+                    &pp->full[rp.s]);
+          rp.advance(rg.ns);
+        }
+        if (!ok) break;
+      }
+    }
+    return;
+  }
+  const int w = warp - 1;
+  const int MTN = (nc + 15) / 16;  // m-tiles (the last may be half); k-steps of 8: nc / 8
+  const bool active = w < MTN;
+  const int g = lane >> 2, tq = lane & 3, q = lane >> 3, li = lane & 7;
+  const unsigned neg = (g & 1) ? 0u : 0x80000000u;  // partner exchange: even columns take -Im
+  const int arow = min(w * 16 + 8 * (q & 1) + li, nc - 1);
+  for (long long i = i0; i < i1; i += step) {
+    float acc[NT][4], acc2[NT][4];
+#pragma unroll
+    for (int t = 0; t < NT; ++t)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc[t][u] = acc2[t][u] = 0.f;
+    for (int d = 0; d < 9; ++d) {
+      const bool ok = ring_wait(rg, rp, a.err);
+      if (ok && active) {
+        const unsigned char* Ds = ring_stage(rg, rp);
+        const float* Xs = reinterpret_cast<const float*>(Ds + dbytes);
+        for (int ks = 0; ks < nc / 8; ++ks) {
+          unsigned are[4], aim[4], arh[4], arl[4], aih[4], ail[4];
+          const unsigned char* ap = Ds + (size_t)arow * nc * 4 + tc_pos(arow, 2 * ks + (q >> 1), P) * 16;
+          ldsm_x4(are, ap);
+          ldsm_x4(aim, ap + (size_t)nc * nc * 4);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            split_tf32(are[u], arh[u], arl[u]);
+            split_tf32(aim[u], aih[u], ail[u]);
+          }
+          const float* x0 = Xs + (size_t)(8 * ks + tq) * XP + g;
+          const float* x1 = x0 + 4 * XP;
+#pragma unroll
+          for (int t = 0; t < NT; ++t) {
+            const unsigned b0 = __float_as_uint(x0[8 * t]), b1 = __float_as_uint(x1[8 * t]);
+            const unsigned p0 = partner(b0) ^ neg, p1 = partner(b1) ^ neg;
+            unsigned bh0, bl0, bh1, bl1, ph0, pl0, ph1, pl1;
+            split_tf32(b0, bh0, bl0);
+            split_tf32(b1, bh1, bl1);
+            split_tf32(p0, ph0, pl0);
+            split_tf32(p1, ph1, pl1);
+            mma_tf32(acc[t], arh, bh0, bh1);
+            mma_tf32(acc[t], arh, bl0, bl1);
+            mma_tf32(acc[t], arl, bh0, bh1);
+            mma_tf32(acc2[t], aih, ph0, ph1);
+            mma_tf32(acc2[t], aih, pl0, pl1);
+            mma_tf32(acc2[t], ail, ph0, ph1);
+          }
+        }
+      }
+      ring_release(rg, rp);
+      rp.advance(rg.ns);
+    }
+    if (active) {
+      const int row = w * 16 + g;
+#pragma unroll
+      for (int t = 0; t < NT; ++t) {
+        if (row < nc)
+          a.y[(i * nc + row) * NRHS + 4 * t + tq] = make_float2(acc[t][0] + acc2[t][0], acc[t][1] + acc2[t][1]);
+        if (row + 8 < nc)
+          a.y[(i * nc + row + 8) * NRHS + 4 * t + tq] =
+              make_float2(acc[t][2] + acc2[t][2], acc[t][3] + acc2[t][3]);
+      }
     }
   }
 }

@@ -154,3 +154,47 @@ def test_tc_solver_runs_on_bf16_links(amg, case):
         assert info[r][1] <= 1e-2
         true = H.rel(coarse.coarse_apply(stored.cpu().numpy(), xs[..., r], c.Lc), b[..., r].astype(np.complex128))
         assert true < 2e-2
+
+
+@pytest.fixture(scope="module", params=[((8, 8, 8, 8), (4, 4, 4, 4), 24), ((8, 8, 8, 8), (4, 4, 4, 4), 20)],
+                ids=["ntv24", "ntv20_half_tiles"])
+def fp32case(amg, request):
+    """FP32 storage with max_nrhs 16: applies with 4, 8, 12 or 16 columns take the tensor-core path
+    with split TF32 operands."""
+    L, B, ntv = request.param
+    sites = si.all_sites(L)
+    Uh = si.links(505, 0.3, sites)
+    tvh = si.test_vectors(505, ntv, sites)
+    U = np.moveaxis(Uh.reshape(H.field_shape(L) + (4, 3, 3)), 4, 0)
+    Q = coarse.orthonormalize(tvh.reshape(H.field_shape(L) + (4, 3, ntv)), B)
+    Dc = coarse.coarse_operator(U, dirac.clover_field(U, H.CSW), H.M0, Q, L, B)
+    p = amg.make_params(L, B, ntv, 16, H.M0, H.CSW, amg.AMG_FP32, amg.AMG_FP32, amg.AMG_FP32)
+    st = torch.cuda.current_stream()
+    h, _ = amg.amg_setup_coarse(p, torch.from_numpy(Uh).cuda(), torch.from_numpy(tvh).cuda(), st)
+    yield dict(h=h, Dc=Dc, Lc=lat.coarse_dims(L, B), ntv=ntv, st=st)
+    amg.amg_destroy(h)
+
+
+@pytest.mark.parametrize("nrhs", [4, 8, 12, 16])
+def test_fp32_multi_rhs_apply_tf32x3(amg, fp32case, nrhs):
+    """The FP32 apply tolerance (1e-5 against FP64) although the products run on TF32 tensor cores
+    (three split products: each term carries about 2^-21 relative error, which the cancellation in
+    D_c x amplifies to a few 1e-6), and the one-column SIMT FP32 path agrees to 1e-5."""
+    c = fp32case
+    Vc = int(np.prod(c["Lc"]))
+    xc = si.coarse_vector(606 + nrhs, c["ntv"], nrhs, np.arange(Vc)).astype(np.complex64)
+    xd = torch.from_numpy(xc).cuda()
+    y = torch.empty_like(xd)
+    amg.amg_coarse_apply(c["h"], xd, y, nrhs, c["st"])
+    got = y.cpu().numpy().astype(np.complex128)
+    ref = coarse.coarse_apply(c["Dc"], xc.astype(np.complex128), c["Lc"])
+    assert H.rel(got, ref) < 1e-5
+    cols = []
+    for r in range(nrhs):
+        x1 = xd[..., r:r + 1].contiguous()
+        y1 = torch.empty_like(x1)
+        amg.amg_coarse_apply(c["h"], x1, y1, 1, c["st"])
+        cols.append(y1.cpu().numpy())
+    simt = np.concatenate(cols, axis=-1).astype(np.complex128)
+    assert H.rel(got, simt) < 1e-5
+    assert amg.amg_sync_status(c["h"]) == amg.AMG_OK
