@@ -13,23 +13,52 @@
 
 namespace {
 
-// per right-hand side |v_r|^2 of a coarse FP32 vector with nrhs columns: one CTA per column
-__global__ void __launch_bounds__(1024) k_colnorm2(const float2* __restrict__ v, long long rows, int nrhs,
-                                                   double* __restrict__ out) {
-  __shared__ double red[32];
-  const int r = blockIdx.x;
-  double s = 0;
-  for (long long e = threadIdx.x; e < rows; e += blockDim.x) {
-    const float2 a = v[e * nrhs + r];
-    s += (double)a.x * a.x + (double)a.y * a.y;
+// per right-hand side |v_r|^2 of a coarse FP32 vector [rows][nrhs]: a grid-stride pass over the
+// rows with coalesced reads (a thread keeps one partial sum per column it meets: element e belongs
+// to column e % nrhs), CTA reductions per column, one double atomicAdd per CTA and column into out
+// (zeroed by the caller).
+__global__ void __launch_bounds__(256) k_colnorm2(const float2* __restrict__ v, long long rows, int nrhs,
+                                                  double* __restrict__ out) {
+  __shared__ double red[16][8];
+  double acc[16];
+#pragma unroll
+  for (int r = 0; r < 16; ++r) acc[r] = 0.0;
+  const long long n = rows * nrhs;
+  const long long stride = (long long)gridDim.x * blockDim.x;  // a multiple of 16, so e % nrhs is fixed per thread
+  long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int col = (int)(e % nrhs);
+  double s = 0.0;
+  if (stride % nrhs == 0) {
+    for (; e < n; e += stride) {
+      const float2 a = v[e];
+      s += (double)a.x * a.x + (double)a.y * a.y;
+    }
+  } else {
+    for (; e < n; e += stride) {
+      const float2 a = v[e];
+      const double q = (double)a.x * a.x + (double)a.y * a.y;
+#pragma unroll
+      for (int r = 0; r < 16; ++r)
+        if (r == (int)(e % nrhs)) acc[r] += q;
+    }
   }
-  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  if (stride % nrhs == 0) {
+#pragma unroll
+    for (int r = 0; r < 16; ++r) acc[r] = r == col ? s : 0.0;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    if (r >= nrhs) break;
+    double t = acc[r];
+    for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) red[r][warp] = t;
+  }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-    out[r] = t;
+  if (threadIdx.x < nrhs) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[threadIdx.x][w];
+    atomicAdd(out + threadIdx.x, t);
   }
 }
 
@@ -88,7 +117,8 @@ extern "C" amg_status amg_coarse_solve_mixed(amg_handle ho, amg_handle hi, const
   std::vector<double> bn(nrhs), rn(nrhs), inner(nrhs, 0.0), outer(nrhs, 0.0);
   std::vector<int> kp(nrhs, 1);
   std::vector<double> sub(2 * nrhs);
-  k_colnorm2<<<nrhs, 1024, 0, st>>>(b, rows, nrhs, nrm);
+  AMG_CUDA_TRY(cudaMemsetAsync(nrm, 0, nrhs * sizeof(double), st));
+  k_colnorm2<<<2 * 152, 256, 0, st>>>(b, rows, nrhs, nrm);
   AMG_LAUNCH_CHECK();
   ho->launches++;
   AMG_CUDA_TRY(cudaMemcpyAsync(bn.data(), nrm, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -118,7 +148,8 @@ extern "C" amg_status amg_coarse_solve_mixed(amg_handle ho, amg_handle hi, const
     for (int q = 0; q < nrhs; ++q) kp[q] = 1;
     AMG_CUDA_TRY(cudaMemcpyAsync(keep, kp.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, st));
     k_resid<<<4 * 152, 256, 0, st>>>(r, b, w, keep, n, nrhs);
-    k_colnorm2<<<nrhs, 1024, 0, st>>>(r, rows, nrhs, nrm);
+    AMG_CUDA_TRY(cudaMemsetAsync(nrm, 0, nrhs * sizeof(double), st));
+    k_colnorm2<<<2 * 152, 256, 0, st>>>(r, rows, nrhs, nrm);
     AMG_LAUNCH_CHECK();
     ho->launches += 2;
     AMG_CUDA_TRY(cudaMemcpyAsync(rn.data(), nrm, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
