@@ -16,6 +16,8 @@
 #include "amg_internal.cuh"
 #include "pipe.cuh"
 
+#include <type_traits>
+
 namespace {
 using namespace amgpipe;
 
@@ -252,6 +254,168 @@ __global__ void __launch_bounds__(288) apply_tma_kernel(const ApplyArgs<LT, NR> 
       a.y[(i * nc + e / NR) * a.ld + a.r0 + e % NR] = sum;
     }
     if (inext < Vc) finish(inext, xnext);
+    consumer_sync(nct);
+  }
+}
+
+// ------------------------------------------------------------------ coarse operator, many columns
+// One pass over D_c for nrhs = 4, 8, 12 or 16 right-hand sides (FP32 or FP16-scaled storage); the
+// column-chunked apply_tma_kernel would stream D_c once per 4 columns.  The stage of chunk (i, d)
+// holds the stencil block (column-major, as in apply_tma_kernel) and the FP32 rows of x_c(nbr(i, d))
+// (nc x NR values, contiguous in the coarse vector), both by bulk copy.  Consumer thread
+// (cg, qg, rg) keeps rows rg*CPL .. rg*CPL + CPL - 1 and right-hand sides 4 qg .. 4 qg + 3 in
+// registers and walks the stencil-block columns b = cg, cg + G, ...; per site a shared-memory sum
+// over the G column groups.  The FGMRES extras: xscale[r] multiplies column r as it is read (the
+// FP16 block scale too), and the scaled own rows (d = 0) go to vout.
+template <typename LT, int NR>
+struct MrhsArgs {
+  const LT* D;
+  const float* dscale;
+  const int* nbr;
+  const float2* x;
+  float2* y;
+  float2* vout;
+  const double* xscale;
+  const int* skip;
+  unsigned* err;
+  Geom g;
+  int ns, G;
+};
+
+template <typename LT, int NR>
+__global__ void __launch_bounds__(288) apply_mrhs_kernel(const MrhsArgs<LT, NR> a) {
+  constexpr int CPL = Vec16<LT>::CPL;
+  constexpr int QG = NR / 4;
+  if (a.skip && *a.skip) return;
+  extern __shared__ __align__(128) unsigned char sm[];
+  Pipe* pp = reinterpret_cast<Pipe*>(sm);
+  const int nc = a.g.nc, ns = a.ns;
+  const long long nc2 = (long long)nc * nc;
+  const unsigned dbytes = (unsigned)(nc2 * sizeof(LT)), xbytes = (unsigned)(nc * NR * sizeof(float2));
+  const unsigned chunk = dbytes + xbytes;
+  unsigned char* stages = sm + kPipeBytes;
+  float2* red = reinterpret_cast<float2*>(stages + (size_t)ns * chunk);  // [G][NR][nc + 1]
+  const int ncw = (blockDim.x - 32) >> 5;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < ns; ++s) {
+      mbar_init(&pp->full[s], 1);
+      mbar_init(&pp->empty[s], ncw);
+    }
+    pp->abort = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const long long Vc = a.g.Vc;
+  if (threadIdx.x < 32) {
+    if (threadIdx.x == 0) {
+      long long c = 0;
+      int s = 0;
+      unsigned ph = 0;
+      int nb[9], nx[9];
+      if (blockIdx.x < Vc)
+        for (int d = 0; d < 9; ++d) nx[d] = __ldg(a.nbr + blockIdx.x * 9LL + d);
+      for (long long i = blockIdx.x; i < Vc && !pp->abort; i += gridDim.x) {
+#pragma unroll
+        for (int d = 0; d < 9; ++d) nb[d] = nx[d];
+        if (i + gridDim.x < Vc)
+#pragma unroll
+          for (int d = 0; d < 9; ++d) nx[d] = __ldg(a.nbr + (i + gridDim.x) * 9 + d);
+        bool ok = true;
+#pragma unroll
+        for (int d = 0; d < 9; ++d) {
+          if (c >= ns && !wait_phase(&pp->empty[s], ph ^ 1u, pp)) {
+            abort_cta(pp, a.err);
+            ok = false;
+            break;
+          }
+          mbar_expect_tx(&pp->full[s], chunk);
+          unsigned char* st = stages + (size_t)s * chunk;
+          bulk_load(st, a.D + (i * 9 + d) * nc2, dbytes, &pp->full[s]);
+          bulk_load(st + dbytes, a.x + (long long)nb[d] * nc * NR, xbytes, &pp->full[s]);
+          ++c;
+          if (++s == ns) {
+            s = 0;
+            ph ^= 1u;
+          }
+        }
+        if (!ok) break;
+      }
+      drain(pp, c, ns);
+    }
+    return;
+  }
+  const int t = threadIdx.x - 32, nct = blockDim.x - 32;
+  const int Gc = nc / CPL, per = Gc * QG;
+  const int cg = t / per, rem = t % per, rg = rem % Gc, qg = rem / Gc;
+  const bool active = cg < a.G;
+  float sc[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) sc[u] = a.xscale ? (float)a.xscale[4 * qg + u] : 1.f;
+  int s = 0;
+  unsigned ph = 0;
+  for (long long i = blockIdx.x; i < Vc; i += gridDim.x) {
+    float2 acc[CPL][4];
+#pragma unroll
+    for (int q = 0; q < CPL; ++q)
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc[q][u] = make_float2(0.f, 0.f);
+    for (int d = 0; d < 9; ++d) {
+      bool ok = !pp->abort;
+      if (ok && !wait_phase(&pp->full[s], ph, pp)) {
+        abort_cta(pp, a.err);
+        ok = false;
+      }
+      const unsigned char* st = stages + (size_t)s * chunk;
+      const float2* Xs = reinterpret_cast<const float2*>(st + dbytes);
+      if (ok && active) {
+        const LT* blk = reinterpret_cast<const LT*>(st) + rg * CPL;
+        const float f = a.dscale ? a.dscale[i * 9 + d] : 1.f;
+        float fs[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) fs[u] = f * sc[u];
+#pragma unroll 2
+        for (int b = cg; b < nc; b += a.G) {
+          float2 v[CPL];
+          Vec16<LT>::ld(blk + (size_t)b * nc, v);
+          const float4 x01 = *reinterpret_cast<const float4*>(Xs + b * NR + 4 * qg);
+          const float4 x23 = *reinterpret_cast<const float4*>(Xs + b * NR + 4 * qg + 2);
+          const float2 xv[4] = {make_float2(x01.x * fs[0], x01.y * fs[0]), make_float2(x01.z * fs[1], x01.w * fs[1]),
+                                make_float2(x23.x * fs[2], x23.y * fs[2]), make_float2(x23.z * fs[3], x23.w * fs[3])};
+#pragma unroll
+          for (int q = 0; q < CPL; ++q)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) cfma(acc[q][u], v[q], xv[u]);
+        }
+      }
+      if (d == 0 && a.vout && ok)  // the own rows, scaled, for the Krylov basis
+        for (int e = t; e < nc * NR; e += nct) {
+          const float2 v = Xs[e];
+          const float f = a.xscale ? (float)a.xscale[e % NR] : 1.f;
+          a.vout[i * nc * NR + e] = make_float2(v.x * f, v.y * f);
+        }
+      __syncwarp();
+      if ((t & 31) == 0) mbar_arrive(&pp->empty[s]);
+      if (++s == ns) {
+        s = 0;
+        ph ^= 1u;
+      }
+    }
+    if (active)
+#pragma unroll
+      for (int q = 0; q < CPL; ++q)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) red[((size_t)cg * NR + 4 * qg + u) * (nc + 1) + rg * CPL + q] = acc[q][u];
+    consumer_sync(nct);
+    for (int e = t; e < nc * NR; e += nct) {
+      const int row = e / NR, col = e % NR;
+      float2 sum = make_float2(0.f, 0.f);
+      for (int gg = 0; gg < a.G; ++gg) {
+        const float2 v = red[((size_t)gg * NR + col) * (nc + 1) + row];
+        sum.x += v.x;
+        sum.y += v.y;
+      }
+      a.y[i * nc * NR + e] = sum;
+    }
     consumer_sync(nct);
   }
 }
@@ -652,6 +816,32 @@ amg_status launch_apply_tma(amg_coarse* h, const LT* D, const float* dscale, con
   return AMG_OK;
 }
 
+template <typename LT, int NR>
+amg_status launch_apply_mrhs(amg_coarse* h, const LT* D, const float* dscale, const void* x, void* y, cudaStream_t st,
+                             const int* skip, const double* xscale, void* vout) {
+  constexpr int CPL = Vec16<LT>::CPL;
+  const int nc = h->g.nc;
+  if (nc % CPL) return AMG_ERR_UNSUPPORTED;
+  const int per = (nc / CPL) * (NR / 4);
+  int G = 256 / per;
+  if (G < 1) return AMG_ERR_UNSUPPORTED;
+  if (G > nc) G = nc;
+  const int threads = 32 + ((G * per + 31) / 32) * 32;
+  const size_t chunk = (size_t)nc * nc * sizeof(LT) + (size_t)nc * NR * sizeof(float2);
+  int ns = (int)((48 * 1024) / chunk);
+  ns = ns < 2 ? 2 : (ns > 4 ? 4 : ns);
+  const size_t smem = kPipeBytes + ns * chunk + (size_t)G * NR * (nc + 1) * sizeof(float2);
+  if (smem > 227 * 1024) return AMG_ERR_UNSUPPORTED;
+  int grid = 0;
+  amg_status s = grid_for(apply_mrhs_kernel<LT, NR>, threads, smem, h->g.Vc, &grid);
+  if (s != AMG_OK) return s;
+  MrhsArgs<LT, NR> a{D, dscale, h->nbr, (const float2*)x, (float2*)y, (float2*)vout, xscale, skip, h->err, h->g, ns, G};
+  apply_mrhs_kernel<LT, NR><<<grid, threads, smem, st>>>(a);
+  AMG_LAUNCH_CHECK();
+  h->launches++;
+  return AMG_OK;
+}
+
 struct EoCall {
   int parity, d0, d1, inv0, sc0, sc1, post_inv;
   const void *s0, *s1, *vadd;
@@ -746,6 +936,12 @@ amg_status for_rhs_chunks(int nrhs, F&& f) {
 template <typename LT>
 amg_status apply_prec(amg_coarse* h, const LT* D, const float* dscale, const void* x, void* y, int nrhs,
                       cudaStream_t s, const int* skip, const double* xscale, void* vout) {
+  if constexpr (!std::is_same<LT, double2>::value) {  // FP32 coarse vectors: one pass for 4..16 columns
+    if (nrhs == 4) return launch_apply_mrhs<LT, 4>(h, D, dscale, x, y, s, skip, xscale, vout);
+    if (nrhs == 8) return launch_apply_mrhs<LT, 8>(h, D, dscale, x, y, s, skip, xscale, vout);
+    if (nrhs == 12) return launch_apply_mrhs<LT, 12>(h, D, dscale, x, y, s, skip, xscale, vout);
+    if (nrhs == 16) return launch_apply_mrhs<LT, 16>(h, D, dscale, x, y, s, skip, xscale, vout);
+  }
   return for_rhs_chunks(nrhs, [&](int r0, int nr) {
     if (nr == 4) return launch_apply_tma<LT, 4>(h, D, dscale, x, y, nrhs, r0, s, skip, xscale, vout);
     if (nr == 2) return launch_apply_tma<LT, 2>(h, D, dscale, x, y, nrhs, r0, s, skip, xscale, vout);
@@ -809,7 +1005,9 @@ amg_status amg_internal_apply_ex(amg_coarse* h, const void* xc, void* yc, int nr
       return apply_prec<double2>(h, (const double2*)h->Dq, nullptr, xc, yc, nrhs, s, skip, xscale, vout);
     case AMG_FP32:
       if (h->p.vec_prec == AMG_FP64) return AMG_ERR_UNSUPPORTED;
-      if (h->Dtf && (nrhs == 4 || nrhs == 8 || nrhs == 12 || nrhs == 16))  // one pass for all columns
+      // 4..16 columns: one pass on the tensor cores with split-TF32 operands (measured faster than
+      // the one-pass SIMT kernel for FP32 storage)
+      if (h->Dtf && (nrhs == 4 || nrhs == 8 || nrhs == 12 || nrhs == 16))
         return amg_internal_apply_tf32(h, xc, yc, nrhs, s, skip, xscale, vout);
       return apply_prec<float2>(h, (const float2*)h->Dq, nullptr, xc, yc, nrhs, s, skip, xscale, vout);
     case AMG_FP16_SCALED:

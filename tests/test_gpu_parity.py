@@ -154,7 +154,7 @@ def test_applies_fp32_ragged(amg, ragged32, nrhs):
 
 def test_fp16_scaled_within_bound(amg):
     L, B, ntv = (8, 8, 8, 8), (4, 4, 4, 4), 24
-    c = Case(amg, L, B, ntv, 0.3, 7, amg.AMG_FP16_SCALED, amg.AMG_FP32)
+    c = Case(amg, L, B, ntv, 0.3, 7, amg.AMG_FP16_SCALED, amg.AMG_FP32, max_nrhs=16)
     try:
         stored = _export(amg, amg.amg_export_Dc_stored, c.h, (c.Vc, 9, 48, 48))
         # element-wise quantisation error: |re|, |im| each within 2^-11 relative (or subnormal step)
@@ -162,7 +162,7 @@ def test_fp16_scaled_within_bound(amg):
         tol = 2.0 ** -11 * np.maximum(np.abs(c.Dc.real), np.abs(c.Dc.imag)) + 2.0 ** -24 * scale[..., None, None]
         assert np.all(np.abs(stored.real - c.Dc.real) <= tol * 1.0001)
         assert np.all(np.abs(stored.imag - c.Dc.imag) <= tol * 1.0001)
-        for nrhs in (1, 4):
+        for nrhs in (1, 4, 8, 12, 16):  # 8 .. 16 columns take the one-pass multi-column kernel
             xc = c.coarse_vec(nrhs, 11)
             zc = torch.empty((c.Vc, 2, ntv, nrhs), dtype=torch.complex64, device="cuda")
             amg.amg_coarse_apply(c.h, c.dev(xc), zc, nrhs, c.stream)
