@@ -258,13 +258,15 @@ __global__ void __launch_bounds__(288) apply_tma_kernel(const ApplyArgs<LT, NR> 
   }
 }
 
-// ------------------------------------------------------------------ coarse operator, many columns
-// One pass over D_c for nrhs = 4, 8, 12 or 16 right-hand sides (FP32 or FP16-scaled storage); the
-// column-chunked apply_tma_kernel would stream D_c once per 4 columns.  The stage of chunk (i, d)
+// ------------------------------------------------------------------ coarse operator, FP32 vectors
+// One pass over D_c for nrhs = 1 .. 4, 8, 12 or 16 right-hand sides (FP32 or FP16-scaled storage);
+// the column-chunked apply_tma_kernel (kept for FP64 and other column counts) streams D_c once per
+// 4 columns and stages the neighbour vectors in a separate per-site gather.  The stage of chunk (i, d)
 // holds the stencil block (column-major, as in apply_tma_kernel) and the FP32 rows of x_c(nbr(i, d))
 // (nc x NR values, contiguous in the coarse vector), both by bulk copy.  Consumer thread
-// (cg, qg, rg) keeps rows rg*CPL .. rg*CPL + CPL - 1 and right-hand sides 4 qg .. 4 qg + 3 in
-// registers and walks the stencil-block columns b = cg, cg + G, ...; per site a shared-memory sum
+// (cg, qg, rg) keeps rows rg*CPL .. rg*CPL + CPL - 1 and right-hand sides RW qg .. RW qg + RW - 1
+// (RW = min(4, nrhs)) in registers and walks the stencil-block columns b = cg, cg + G, ...; per
+// site a shared-memory sum
 // over the G column groups.  The FGMRES extras: xscale[r] multiplies column r as it is read (the
 // FP16 block scale too), and the scaled own rows (d = 0) go to vout.
 template <typename LT, int NR>
@@ -285,7 +287,8 @@ struct MrhsArgs {
 template <typename LT, int NR>
 __global__ void __launch_bounds__(288) apply_mrhs_kernel(const MrhsArgs<LT, NR> a) {
   constexpr int CPL = Vec16<LT>::CPL;
-  constexpr int QG = NR / 4;
+  constexpr int RW = NR < 4 ? NR : 4;  // right-hand sides per thread
+  constexpr int QG = NR / RW;
   if (a.skip && *a.skip) return;
   extern __shared__ __align__(128) unsigned char sm[];
   Pipe* pp = reinterpret_cast<Pipe*>(sm);
@@ -348,17 +351,17 @@ __global__ void __launch_bounds__(288) apply_mrhs_kernel(const MrhsArgs<LT, NR> 
   const int Gc = nc / CPL, per = Gc * QG;
   const int cg = t / per, rem = t % per, rg = rem % Gc, qg = rem / Gc;
   const bool active = cg < a.G;
-  float sc[4];
+  float sc[RW];
 #pragma unroll
-  for (int u = 0; u < 4; ++u) sc[u] = a.xscale ? (float)a.xscale[4 * qg + u] : 1.f;
+  for (int u = 0; u < RW; ++u) sc[u] = a.xscale ? (float)a.xscale[RW * qg + u] : 1.f;
   int s = 0;
   unsigned ph = 0;
   for (long long i = blockIdx.x; i < Vc; i += gridDim.x) {
-    float2 acc[CPL][4];
+    float2 acc[CPL][RW];
 #pragma unroll
     for (int q = 0; q < CPL; ++q)
 #pragma unroll
-      for (int u = 0; u < 4; ++u) acc[q][u] = make_float2(0.f, 0.f);
+      for (int u = 0; u < RW; ++u) acc[q][u] = make_float2(0.f, 0.f);
     for (int d = 0; d < 9; ++d) {
       bool ok = !pp->abort;
       if (ok && !wait_phase(&pp->full[s], ph, pp)) {
@@ -370,21 +373,31 @@ __global__ void __launch_bounds__(288) apply_mrhs_kernel(const MrhsArgs<LT, NR> 
       if (ok && active) {
         const LT* blk = reinterpret_cast<const LT*>(st) + rg * CPL;
         const float f = a.dscale ? a.dscale[i * 9 + d] : 1.f;
-        float fs[4];
+        float fs[RW];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) fs[u] = f * sc[u];
+        for (int u = 0; u < RW; ++u) fs[u] = f * sc[u];
 #pragma unroll 2
         for (int b = cg; b < nc; b += a.G) {
           float2 v[CPL];
           Vec16<LT>::ld(blk + (size_t)b * nc, v);
-          const float4 x01 = *reinterpret_cast<const float4*>(Xs + b * NR + 4 * qg);
-          const float4 x23 = *reinterpret_cast<const float4*>(Xs + b * NR + 4 * qg + 2);
-          const float2 xv[4] = {make_float2(x01.x * fs[0], x01.y * fs[0]), make_float2(x01.z * fs[1], x01.w * fs[1]),
-                                make_float2(x23.x * fs[2], x23.y * fs[2]), make_float2(x23.z * fs[3], x23.w * fs[3])};
+          float2 xv[RW];
+          if constexpr (RW == 4) {
+            const float4 x01 = *reinterpret_cast<const float4*>(Xs + b * NR + 4 * qg);
+            const float4 x23 = *reinterpret_cast<const float4*>(Xs + b * NR + 4 * qg + 2);
+            xv[0] = make_float2(x01.x, x01.y);
+            xv[1] = make_float2(x01.z, x01.w);
+            xv[2] = make_float2(x23.x, x23.y);
+            xv[3] = make_float2(x23.z, x23.w);
+          } else {
+#pragma unroll
+            for (int u = 0; u < RW; ++u) xv[u] = Xs[b * NR + RW * qg + u];
+          }
+#pragma unroll
+          for (int u = 0; u < RW; ++u) xv[u] = make_float2(xv[u].x * fs[u], xv[u].y * fs[u]);
 #pragma unroll
           for (int q = 0; q < CPL; ++q)
 #pragma unroll
-            for (int u = 0; u < 4; ++u) cfma(acc[q][u], v[q], xv[u]);
+            for (int u = 0; u < RW; ++u) cfma(acc[q][u], v[q], xv[u]);
         }
       }
       if (d == 0 && a.vout && ok)  // the own rows, scaled, for the Krylov basis
@@ -404,7 +417,7 @@ __global__ void __launch_bounds__(288) apply_mrhs_kernel(const MrhsArgs<LT, NR> 
 #pragma unroll
       for (int q = 0; q < CPL; ++q)
 #pragma unroll
-        for (int u = 0; u < 4; ++u) red[((size_t)cg * NR + 4 * qg + u) * (nc + 1) + rg * CPL + q] = acc[q][u];
+        for (int u = 0; u < RW; ++u) red[((size_t)cg * NR + RW * qg + u) * (nc + 1) + rg * CPL + q] = acc[q][u];
     consumer_sync(nct);
     for (int e = t; e < nc * NR; e += nct) {
       const int row = e / NR, col = e % NR;
@@ -822,7 +835,7 @@ amg_status launch_apply_mrhs(amg_coarse* h, const LT* D, const float* dscale, co
   constexpr int CPL = Vec16<LT>::CPL;
   const int nc = h->g.nc;
   if (nc % CPL) return AMG_ERR_UNSUPPORTED;
-  const int per = (nc / CPL) * (NR / 4);
+  const int per = (nc / CPL) * (NR < 4 ? 1 : NR / 4);
   int G = 256 / per;
   if (G < 1) return AMG_ERR_UNSUPPORTED;
   if (G > nc) G = nc;
@@ -936,7 +949,10 @@ amg_status for_rhs_chunks(int nrhs, F&& f) {
 template <typename LT>
 amg_status apply_prec(amg_coarse* h, const LT* D, const float* dscale, const void* x, void* y, int nrhs,
                       cudaStream_t s, const int* skip, const double* xscale, void* vout) {
-  if constexpr (!std::is_same<LT, double2>::value) {  // FP32 coarse vectors: one pass for 4..16 columns
+  if constexpr (!std::is_same<LT, double2>::value) {  // FP32 coarse vectors: one pass for these counts
+    if (nrhs == 1) return launch_apply_mrhs<LT, 1>(h, D, dscale, x, y, s, skip, xscale, vout);
+    if (nrhs == 2) return launch_apply_mrhs<LT, 2>(h, D, dscale, x, y, s, skip, xscale, vout);
+    if (nrhs == 3) return launch_apply_mrhs<LT, 3>(h, D, dscale, x, y, s, skip, xscale, vout);
     if (nrhs == 4) return launch_apply_mrhs<LT, 4>(h, D, dscale, x, y, s, skip, xscale, vout);
     if (nrhs == 8) return launch_apply_mrhs<LT, 8>(h, D, dscale, x, y, s, skip, xscale, vout);
     if (nrhs == 12) return launch_apply_mrhs<LT, 12>(h, D, dscale, x, y, s, skip, xscale, vout);
