@@ -918,7 +918,7 @@ template <typename ST, int NR>
 amg_status launch_prolong_tma(amg_coarse* h, const ST* R, const ST* xc, ST* x, int ld, int r0, cudaStream_t st) {
   using AT = typename Acc<ST>::type;
   const int threads = 32 + 4 * 32;
-  const int ns = 4;
+  const int ns = (threads - 32) / 32;  // one stage per consumer warp: the kernel derives it the same way
   const int nch = prolong_chunk<ST>(h->g);
   if (nch == 0) return AMG_ERR_UNSUPPORTED;
   const size_t chunk = (size_t)h->g.ntv * nch * sizeof(ST);
