@@ -240,7 +240,7 @@ __device__ __noinline__ RingPos tc_job(const LatDesc& L, int phase, long long i0
 // TC: the batch holds tensor-core lattices (160 threads: one producer warp, four consumer warps);
 // otherwise only SIMT jobs run and the thread count is free (autotuned).
 template <bool TC>
-__global__ void __launch_bounds__(TC ? kBatchThreads : 512, TC ? 3 : 1) batch_kernel(const BatchArgs a) {
+__global__ void __launch_bounds__(TC ? kBatchThreads : 512, TC ? 4 : 1) batch_kernel(const BatchArgs a) {
   extern __shared__ __align__(128) unsigned char sm[];
   __shared__ unsigned job_s;
   __shared__ int ok_s;
@@ -484,7 +484,7 @@ amg_status amg_internal_batch(amg_coarse* const* hs, int n, const void* const* y
   const bool tc = batch_has_tc(hs, n, nrhs);
   const int threads = tc ? kBatchThreads : (bw.threads ? bw.threads : 256);
   const int ns = bw.ns ? bw.ns : 3;
-  const int per_sm = bw.per_sm ? bw.per_sm : (tc ? 3 : 2);
+  const int per_sm = bw.per_sm ? bw.per_sm : (tc ? 4 : 2);
   Prepared pr;
   amg_status st = prepare(hs, n, y, x, nrhs, s, tc ? ns : 0, threads, &pr);
   if (st != AMG_OK) return st;
