@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(160, 1) restrict_tc_kernel(const TcRPArgs a, i
 }
 
 template <int NRHS>
-__global__ void __launch_bounds__(160, 1) prolong_tc_kernel(const TcRPArgs a, int ns) {
+__global__ void __launch_bounds__(160, 4) prolong_tc_kernel(const TcRPArgs a, int ns) {
   extern __shared__ __align__(128) unsigned char sm[];
   Pipe* pp = reinterpret_cast<Pipe*>(sm);
   ring_init(pp, ns, (int)(blockDim.x >> 5) - 1);
@@ -85,7 +85,8 @@ amg_status launch_rp_tc(amg_coarse* h, const void* in, void* out, cudaStream_t s
   const Geom& g = h->g;
   const int threads = 32 + 64 * ((NRHS + 7) / 8);
   const size_t chunk = RESTRICT ? tc_restrict_chunk(g.ntv, NRHS) : tc_prolong_chunk(g.ntv);
-  int ns = (int)((60 * 1024) / chunk);
+  // the prolongation: 4 stages and a register cap for 4 CTAs per SM (measured best)
+  int ns = RESTRICT ? (int)((60 * 1024) / chunk) : 4;
   ns = ns < 2 ? 2 : (ns > 8 ? 8 : ns);
   const size_t smem = kPipeBytes + ns * chunk;
   if (smem > 227 * 1024) return AMG_ERR_UNSUPPORTED;
