@@ -91,6 +91,26 @@ __device__ inline double2 warp_sum_partials(const double2* part, int nblk, int n
   return sum;
 }
 
+// ---- flat forms for nrhs dividing 32 (2, 4, 8, 16): the loops run over e = row * nrhs + r with
+// consecutive threads on consecutive elements (coalesced), and since the stride and every warp's
+// first element are multiples of 32, a thread only ever meets column e % nrhs = lane % nrhs.
+// Per-column sums: xor shuffles over the lanes of equal column, then over the warps.
+__device__ inline void cta_col_sum_store(double2 v, int nrhs, double2* out) {
+  __shared__ double2 sm[ST_T / 32][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int o = 16; o >= nrhs; o >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+  }
+  if (lane < nrhs) sm[warp][lane] = v;
+  __syncthreads();
+  if (threadIdx.x < nrhs) {
+    double2 t = make_double2(0, 0);
+    for (int w = 0; w < ST_T / 32; ++w) t = cadd(t, sm[w][threadIdx.x]);
+    out[threadIdx.x] = t;
+  }
+}
+
 // Givens rotation and convergence test of Arnoldi step j for right-hand side r, given |w|^2.
 __device__ void arnoldi_step(FState& s, int r, int j, double n2, int* any) {
   if (!s.active[r]) {
@@ -219,6 +239,65 @@ __global__ void __launch_bounds__(ST_T) k_update(FState s, CT* __restrict__ w, c
   if (threadIdx.x == 0 && !any) *s.done = 1;
 }
 
+template <typename CT>
+__global__ void __launch_bounds__(ST_T) k_dots_flat(FState s, const CT* __restrict__ w, const CT* __restrict__ V,
+                                                    long long vstride, int j) {
+  if (*s.done) return;
+  const int i = blockIdx.y;
+  const CT* Vi = V + i * vstride;
+  const long long n = s.rows * s.nrhs;
+  CT a = CT{0, 0};
+  for (long long e = blockIdx.x * (long long)ST_T + threadIdx.x; e < n; e += (long long)s.nblk * ST_T)
+    cfmac(a, Vi[e], w[e]);
+  cta_col_sum_store(to_d(a), s.nrhs, s.part + ((long long)i * s.nblk + blockIdx.x) * s.nrhs);
+  if (!last_block(s.counter, s.nblk * (j + 1))) return;
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int t = warp; t < (j + 1) * s.nrhs; t += nw) {
+    const double2 sum = warp_sum_partials(s.part, s.nblk, s.nrhs, t);
+    const int ii = t / s.nrhs, r = t % s.nrhs;
+    if ((threadIdx.x & 31) == 0) s.H[((long long)r * (s.m + 1) + ii) * s.m + j] = s.active[r] ? sum : make_double2(0, 0);
+  }
+}
+
+template <typename CT>
+__global__ void __launch_bounds__(ST_T) k_update_flat(FState s, CT* __restrict__ w, const CT* __restrict__ V,
+                                                      long long vstride, int j) {
+  if (*s.done) return;
+  __shared__ CT hc[AMG_MAX_NTV + 1][MAXR];
+  for (int e = threadIdx.x; e < (j + 1) * s.nrhs; e += ST_T) {
+    const int i = e / s.nrhs, r = e % s.nrhs;
+    hc[i][r] = from_d<CT>(ld_cg(s.H + ((long long)r * (s.m + 1) + i) * s.m + j));
+  }
+  __syncthreads();
+  const int col = threadIdx.x % s.nrhs;
+  const long long n = s.rows * s.nrhs;
+  decltype(CT{}.x) acc = 0;
+  for (long long e = blockIdx.x * (long long)ST_T + threadIdx.x; e < n; e += (long long)s.nblk * ST_T) {
+    CT v = w[e];
+    for (int i = 0; i <= j; ++i) {
+      const CT q = V[i * vstride + e];
+      const CT c = hc[i][col];
+      v.x -= c.x * q.x - c.y * q.y;
+      v.y -= c.x * q.y + c.y * q.x;
+    }
+    w[e] = v;
+    acc += v.x * v.x + v.y * v.y;
+  }
+  cta_col_sum_store(make_double2((double)acc, 0.0), s.nrhs, s.part + (long long)blockIdx.x * s.nrhs);
+  if (!last_block(s.counter, s.nblk)) return;
+  __shared__ int any;
+  __shared__ double n2s[MAXR];
+  if (threadIdx.x == 0) any = 0;
+  for (int r = threadIdx.x >> 5; r < s.nrhs; r += blockDim.x >> 5) {
+    const double2 v = warp_sum_partials(s.part, s.nblk, s.nrhs, r);
+    if ((threadIdx.x & 31) == 0) n2s[r] = v.x;
+  }
+  __syncthreads();
+  if (threadIdx.x < s.nrhs) arnoldi_step(s, threadIdx.x, j, n2s[threadIdx.x], &any);
+  __syncthreads();
+  if (threadIdx.x == 0 && !any) *s.done = 1;
+}
+
 // End of a cycle: every CTA solves the small triangular systems (one thread per right-hand
 // side), then x += sum_i y_i V_i over the columns built in the cycle.  The last CTA resets the
 // column counts, so a repeated call adds nothing.
@@ -276,28 +355,44 @@ __global__ void __launch_bounds__(ST_T) k_xupdate(FState s, CT* __restrict__ x, 
 template <typename CT>
 __global__ void __launch_bounds__(ST_T) k_residual(FState s, CT* __restrict__ w, const CT* __restrict__ b, int first) {
   if (*s.done) return;
-  CT a[MAXR];
-#pragma unroll
-  for (int r = 0; r < MAXR; ++r) a[r] = CT{0, 0};
-  for (long long row = blockIdx.x * (long long)ST_T + threadIdx.x; row < s.rows;
-       row += (long long)s.nblk * ST_T) {
-#pragma unroll
-    for (int r = 0; r < MAXR; ++r) {
-      if (r >= s.nrhs) break;
-      CT v = b[row * s.nrhs + r];
+  if (s.nrhs > 1 && 32 % s.nrhs == 0) {  // flat, coalesced (see k_dots_flat)
+    const long long n = s.rows * s.nrhs;
+    decltype(CT{}.x) acc = 0;
+    for (long long e = blockIdx.x * (long long)ST_T + threadIdx.x; e < n; e += (long long)s.nblk * ST_T) {
+      CT v = b[e];
       if (!first) {
-        const CT q = w[row * s.nrhs + r];
+        const CT q = w[e];
         v.x -= q.x;
         v.y -= q.y;
       }
-      w[row * s.nrhs + r] = v;
-      a[r].x += v.x * v.x + v.y * v.y;
+      w[e] = v;
+      acc += v.x * v.x + v.y * v.y;
     }
-  }
-  double2 acc[MAXR];
+    cta_col_sum_store(make_double2((double)acc, 0.0), s.nrhs, s.part + (long long)blockIdx.x * s.nrhs);
+  } else {
+    CT a[MAXR];
 #pragma unroll
-  for (int r = 0; r < MAXR; ++r) acc[r] = to_d(a[r]);
-  cta_sum_store(acc, s.nrhs, s.part + (long long)blockIdx.x * s.nrhs);
+    for (int r = 0; r < MAXR; ++r) a[r] = CT{0, 0};
+    for (long long row = blockIdx.x * (long long)ST_T + threadIdx.x; row < s.rows;
+         row += (long long)s.nblk * ST_T) {
+#pragma unroll
+      for (int r = 0; r < MAXR; ++r) {
+        if (r >= s.nrhs) break;
+        CT v = b[row * s.nrhs + r];
+        if (!first) {
+          const CT q = w[row * s.nrhs + r];
+          v.x -= q.x;
+          v.y -= q.y;
+        }
+        w[row * s.nrhs + r] = v;
+        a[r].x += v.x * v.x + v.y * v.y;
+      }
+    }
+    double2 acc[MAXR];
+#pragma unroll
+    for (int r = 0; r < MAXR; ++r) acc[r] = to_d(a[r]);
+    cta_sum_store(acc, s.nrhs, s.part + (long long)blockIdx.x * s.nrhs);
+  }
   if (!last_block(s.counter, s.nblk)) return;
   __shared__ int any;
   __shared__ double n2s[MAXR];
@@ -342,6 +437,7 @@ template <typename CT>
 amg_status solve_impl(amg_coarse* h, long long rows, amg_apply_fn op, const CT* b, CT* x, int nrhs, double tol, int m,
                       int max_applies, cudaStream_t st, double* info, unsigned char* ws, bool poll) {
   const long long vstride = rows * nrhs;
+  const bool flat = nrhs > 1 && 32 % nrhs == 0;  // coalesced flat loops (see k_dots_flat)
   FState s;
   s.m = m;
   s.nrhs = nrhs;
@@ -404,8 +500,13 @@ amg_status solve_impl(amg_coarse* h, long long rows, amg_apply_fn op, const CT* 
       // V_j = cur / h_{j,j-1} is written by the application itself, which reads cur scaled
       amg_status status = op(h, cur, nxt, nrhs, st, s.done, s.invh, V + j * vstride);
       if (status != AMG_OK) return status;
-      k_dots<CT><<<dim3(NBLK, j + 1), ST_T, 0, st>>>(s, nxt, V, vstride, j);
-      k_update<CT><<<NBLK, ST_T, 0, st>>>(s, nxt, V, vstride, j);
+      if (flat) {
+        k_dots_flat<CT><<<dim3(NBLK, j + 1), ST_T, 0, st>>>(s, nxt, V, vstride, j);
+        k_update_flat<CT><<<NBLK, ST_T, 0, st>>>(s, nxt, V, vstride, j);
+      } else {
+        k_dots<CT><<<dim3(NBLK, j + 1), ST_T, 0, st>>>(s, nxt, V, vstride, j);
+        k_update<CT><<<NBLK, ST_T, 0, st>>>(s, nxt, V, vstride, j);
+      }
       AMG_LAUNCH_CHECK();
       h->launches += 2;
       std::swap(cur, nxt);
