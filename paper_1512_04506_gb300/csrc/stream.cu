@@ -627,6 +627,185 @@ __global__ void __launch_bounds__(288) eo_apply_kernel(const EoArgs<LT, NR> a) {
   }
 }
 
+// The even/odd pieces for FP32 storage in the one-pass form of apply_mrhs_kernel: each stage holds
+// one block (hop block, self block or stored inverse) and, for a hop or the self block, the
+// source rows (s1 rows of the neighbour's half index, or the own s0 rows), both by bulk copy.
+// Meaning of the arguments as for eo_apply_kernel (EoArgs).  With post_inv the hop sum (plus
+// delta vadd) is reduced into shared memory and multiplied by the inverse block that the
+// producer streams after the hops.
+template <int NR>
+__global__ void __launch_bounds__(288) eo_mrhs_kernel(const EoArgs<float2, NR> a) {
+  constexpr int CPL = 2;
+  constexpr int RW = NR < 4 ? NR : 4;
+  constexpr int QG = NR / RW;
+  if (a.skip && *a.skip) return;
+  extern __shared__ __align__(128) unsigned char sm[];
+  Pipe* pp = reinterpret_cast<Pipe*>(sm);
+  const int nc = a.g.nc, ns = a.ns;
+  const long long nc2 = (long long)nc * nc;
+  const unsigned dbytes = (unsigned)(nc2 * sizeof(float2)), xbytes = (unsigned)(nc * NR * sizeof(float2));
+  const unsigned chunk = dbytes + xbytes;
+  unsigned char* stages = sm + kPipeBytes;
+  float2* red = reinterpret_cast<float2*>(stages + (size_t)ns * chunk);  // [G][NR][nc + 1]
+  float2* zb = red + (size_t)a.G * NR * (nc + 1);                        // [nc][NR] hop sum (post_inv)
+  const int ncw = (blockDim.x - 32) >> 5;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < ns; ++s) {
+      mbar_init(&pp->full[s], 1);
+      mbar_init(&pp->empty[s], ncw);
+    }
+    pp->abort = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const long long Vh = a.g.Vc / 2;
+  const int dend = a.d1 + (a.post_inv ? 1 : 0);  // chunk d1 (post_inv): the inverse block
+  if (threadIdx.x < 32) {
+    if (threadIdx.x == 0) {
+      long long c = 0;
+      int s = 0;
+      unsigned ph = 0;
+      for (long long h = blockIdx.x; h < Vh && !pp->abort; h += gridDim.x) {
+        const long long site = __ldg(a.site_of + h);
+        bool ok = true;
+        for (int d = a.d0; d < dend; ++d) {
+          if (c >= ns && !wait_phase(&pp->empty[s], ph ^ 1u, pp)) {
+            abort_cta(pp, a.err);
+            ok = false;
+            break;
+          }
+          const bool post = d == a.d1;
+          mbar_expect_tx(&pp->full[s], post ? dbytes : chunk);
+          unsigned char* st = stages + (size_t)s * chunk;
+          const float2* blk = post ? a.Dinv + h * nc2
+                                   : (d == 0 ? (a.inv0 ? a.Dinv + h * nc2 : a.D + site * 9 * nc2)
+                                             : a.D + (site * 9 + d) * nc2);
+          bulk_load(st, blk, dbytes, &pp->full[s]);
+          if (!post) {
+            const float2* src = d == 0 ? a.s0 + h * nc * NR
+                                       : a.s1 + (long long)(__ldg(a.nbr + site * 9 + d) >> 1) * nc * NR;
+            bulk_load(st + dbytes, src, xbytes, &pp->full[s]);
+          }
+          ++c;
+          if (++s == ns) {
+            s = 0;
+            ph ^= 1u;
+          }
+        }
+        if (!ok) break;
+      }
+      drain(pp, c, ns);
+    }
+    return;
+  }
+  const int t = threadIdx.x - 32, nct = blockDim.x - 32;
+  const int Gc = nc / CPL, per = Gc * QG;
+  const int cg = t / per, rem = t % per, rg = rem % Gc, qg = rem / Gc;
+  const bool active = cg < a.G;
+  float sx[RW];
+#pragma unroll
+  for (int u = 0; u < RW; ++u) sx[u] = a.xscale ? (float)a.xscale[RW * qg + u] : 1.f;
+  int s = 0;
+  unsigned ph = 0;
+  for (long long h = blockIdx.x; h < Vh; h += gridDim.x) {
+    float2 acc[CPL][RW];
+    auto zero = [&]() {
+#pragma unroll
+      for (int q = 0; q < CPL; ++q)
+#pragma unroll
+        for (int u = 0; u < RW; ++u) acc[q][u] = make_float2(0.f, 0.f);
+    };
+    // one chunk with source rows X (nc x NR) scaled per column by fs
+    auto consume = [&](const float2* X, const float (&fs)[RW], bool own) {
+      bool ok = !pp->abort;
+      if (ok && !wait_phase(&pp->full[s], ph, pp)) {
+        abort_cta(pp, a.err);
+        ok = false;
+      }
+      const unsigned char* st = stages + (size_t)s * chunk;
+      const float2* Xs = X ? X : reinterpret_cast<const float2*>(st + dbytes);
+      if (ok && active) {
+        const float2* blk = reinterpret_cast<const float2*>(st) + rg * CPL;
+#pragma unroll 2
+        for (int b = cg; b < nc; b += a.G) {
+          float2 v[CPL];
+          Vec16<float2>::ld(blk + (size_t)b * nc, v);
+          float2 xv[RW];
+#pragma unroll
+          for (int u = 0; u < RW; ++u) {
+            const float2 x = Xs[b * NR + RW * qg + u];
+            xv[u] = make_float2(x.x * fs[u], x.y * fs[u]);
+          }
+#pragma unroll
+          for (int q = 0; q < CPL; ++q)
+#pragma unroll
+            for (int u = 0; u < RW; ++u) cfma(acc[q][u], v[q], xv[u]);
+        }
+      }
+      if (own && a.vout && ok)  // the own rows, scaled, for the Krylov basis
+        for (int e = t; e < nc * NR; e += nct) {
+          const float2 v = Xs[e];
+          const float f = a.xscale ? (float)a.xscale[e % NR] : 1.f;
+          a.vout[h * nc * NR + e] = make_float2(v.x * f, v.y * f);
+        }
+      __syncwarp();
+      if ((t & 31) == 0) mbar_arrive(&pp->empty[s]);
+      if (++s == ns) {
+        s = 0;
+        ph ^= 1u;
+      }
+    };
+    // sum over column groups into out [nc][NR] (shared) or y (+ delta vadd when add)
+    auto reduce_to = [&](float2* out, bool add) {
+      if (active)
+#pragma unroll
+        for (int q = 0; q < CPL; ++q)
+#pragma unroll
+          for (int u = 0; u < RW; ++u) red[((size_t)cg * NR + RW * qg + u) * (nc + 1) + rg * CPL + q] = acc[q][u];
+      consumer_sync(nct);
+      for (int e = t; e < nc * NR; e += nct) {
+        const int row = e / NR, col = e % NR;
+        float2 sum = make_float2(0.f, 0.f);
+        for (int gg = 0; gg < a.G; ++gg) {
+          const float2 v = red[((size_t)gg * NR + col) * (nc + 1) + row];
+          sum.x += v.x;
+          sum.y += v.y;
+        }
+        const long long o = h * nc * NR + e;
+        if (add && a.vadd) {
+          const float2 w = a.vadd[o];
+          sum.x += (float)a.delta * w.x;
+          sum.y += (float)a.delta * w.y;
+        }
+        if (out) out[e] = sum;
+        else a.y[o] = sum;
+      }
+      consumer_sync(nct);
+    };
+    zero();
+    for (int d = a.d0; d < a.d1; ++d) {
+      float fs[RW];
+#pragma unroll
+      for (int u = 0; u < RW; ++u) {
+        const float base = d == 0 ? 1.f : (float)a.c1;
+        fs[u] = ((d == 0 ? a.sc0 : a.sc1) ? sx[u] : 1.f) * base;
+      }
+      consume(nullptr, fs, d == 0);
+    }
+    if (a.post_inv) {
+      reduce_to(zb, true);
+      zero();
+      float one[RW];
+#pragma unroll
+      for (int u = 0; u < RW; ++u) one[u] = 1.f;
+      consume(zb, one, false);
+      reduce_to(nullptr, false);
+    } else {
+      reduce_to(nullptr, true);
+    }
+  }
+}
+
 // ------------------------------------------------------------------ restriction
 // One CTA per block, launched in block order, so the CTAs resident at any time read neighbouring
 // blocks.  y on the block is staged as ys[h][n][r]; warp w computes rows (h, j) of R_i^h y_i^h,
@@ -864,6 +1043,34 @@ struct EoCall {
   const int* skip;
 };
 
+template <int NR>
+amg_status launch_eo_mrhs(amg_coarse* h, const EoCall& e, cudaStream_t st) {
+  const int nc = h->g.nc;
+  if (nc % 2) return AMG_ERR_UNSUPPORTED;
+  const int per = (nc / 2) * (NR < 4 ? 1 : NR / 4);
+  int G = 256 / per;
+  if (G < 1) return AMG_ERR_UNSUPPORTED;
+  if (G > nc) G = nc;
+  const int threads = 32 + ((G * per + 31) / 32) * 32;
+  const size_t chunk = (size_t)nc * nc * sizeof(float2) + (size_t)nc * NR * sizeof(float2);
+  int ns = (int)((48 * 1024) / chunk);
+  ns = ns < 2 ? 2 : (ns > 4 ? 4 : ns);
+  const size_t smem =
+      kPipeBytes + ns * chunk + (size_t)G * NR * (nc + 1) * sizeof(float2) + (size_t)nc * NR * sizeof(float2);
+  if (smem > 227 * 1024) return AMG_ERR_UNSUPPORTED;
+  int grid = 0;
+  amg_status s = grid_for(eo_mrhs_kernel<NR>, threads, smem, h->g.Vc / 2, &grid);
+  if (s != AMG_OK) return s;
+  EoArgs<float2, NR> a{(const float2*)h->Dq, (const float2*)h->Dinvq, h->nbr,
+                       h->eo_site + (size_t)e.parity * (h->g.Vc / 2), (const float2*)e.s0, (const float2*)e.s1,
+                       (const float2*)e.vadd, (float2*)e.y, (float2*)e.vout, e.xscale, e.skip, h->err, h->g, NR, 0, ns,
+                       G, e.d0, e.d1, e.inv0, e.sc0, e.sc1, e.post_inv, e.c1, e.delta};
+  eo_mrhs_kernel<NR><<<grid, threads, smem, st>>>(a);
+  AMG_LAUNCH_CHECK();
+  h->launches++;
+  return AMG_OK;
+}
+
 template <typename LT, int NR>
 amg_status launch_eo(amg_coarse* h, const EoCall& e, int ld, int r0, cudaStream_t st) {
   using AT = typename Acc<LT>::type;
@@ -1050,6 +1257,18 @@ amg_status amg_internal_eo_apply(amg_coarse* h, int parity, int d0, int d1, bool
       if (nr == 2) return launch_eo<double2, 2>(h, e, nrhs, r0, st);
       return launch_eo<double2, 1>(h, e, nrhs, r0, st);
     });
+  if (h->p.link_prec == AMG_FP32 && h->p.vec_prec != AMG_FP64) {
+    switch (nrhs) {  // one pass: blocks and source rows through the ring
+      case 1: return launch_eo_mrhs<1>(h, e, st);
+      case 2: return launch_eo_mrhs<2>(h, e, st);
+      case 3: return launch_eo_mrhs<3>(h, e, st);
+      case 4: return launch_eo_mrhs<4>(h, e, st);
+      case 8: return launch_eo_mrhs<8>(h, e, st);
+      case 12: return launch_eo_mrhs<12>(h, e, st);
+      case 16: return launch_eo_mrhs<16>(h, e, st);
+      default: break;
+    }
+  }
   if (h->p.link_prec == AMG_FP32 && h->p.vec_prec != AMG_FP64)
     return for_rhs_chunks(nrhs, [&](int r0, int nr) {
       if (nr == 4) return launch_eo<float2, 4>(h, e, nrhs, r0, st);
