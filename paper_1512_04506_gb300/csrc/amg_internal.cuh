@@ -104,7 +104,9 @@ struct SolveWork {
   static constexpr int kRing = 16;
   void* buf = nullptr;
   size_t bytes = 0;
-  int* hflag = nullptr;
+  int* hflag = nullptr;     // mapped pinned word: ticket of the last solve found converged
+  int* hdone_dev = nullptr;  // its device address
+  int ticket = 0;
   cudaEvent_t ev[kRing] = {};
 };
 

@@ -1,16 +1,17 @@
 // Coarse-grid solve of Alg. 2: restarted FGMRES(m) on D_c with classical Gram-Schmidt Arnoldi
-// ("BLAS-like linear algebra (mainly Gram-Schmidt)") and Givens rotations, one independent
-// Krylov space per right-hand side.  Vectors stay in the coarse layout [Vc][2][ntv][nrhs]; all
-// scalars (Hessenberg matrix, rotations, residual estimates, convergence flags) live on the
-// device, so the host only launches kernels.
+// and Givens rotations, one independent Krylov space per right-hand side.  Vectors stay in the
+// coarse layout [Vc][2][ntv][nrhs]; all scalars (Hessenberg matrix, rotations, residual
+// estimates, convergence flags) live on the device, so the host only launches kernels.
 //
-// One Arnoldi step is three launches: w = D_c V_j (the application reads the unnormalised
-// vector times 1/h_{j,j-1} and stores V_j on the way), the dots <V_i, w> (whose last CTA reduces
-// the partial sums into column j of H), and the update w -= sum H_ij V_i with |w|^2 (whose last
-// CTA does the Givens rotation and the convergence test).  Once
-// every right-hand side has converged the device flag `done` makes every later kernel return at
-// once.  The host either learns of it through an event one step behind the launch front (so
-// the GPU never waits for the host) or, without events, launches the whole budget.
+// One Arnoldi step is two launches for nrhs in {1, 2, 4, 8, 16}: w = D_c V_j (the application
+// reads the unnormalised vector times 1/h_{j,j-1} and stores V_j on the way), then the
+// cooperative k_arnoldi (dots <V_i, w>, column j of H, w -= sum H_ij V_i with |w|^2, Givens
+// rotation and convergence test, phases separated by grid barriers).  Other column counts take
+// three launches (k_dots, then k_update, each ending in a last-CTA reduction).  Once every
+// right-hand side has converged the device flag `done` makes every later kernel return at once
+// and a mapped host word receives the solve's ticket; the host reads it after an event one step
+// behind the launch front (so the GPU never waits for the host) or, without polling, launches
+// the whole budget.
 #include "amg_internal.cuh"
 
 #include <algorithm>
@@ -29,7 +30,18 @@ struct FState {
   double *bnorm, *relres, *invh;
   int *active, *kcnt, *applies, *done;
   unsigned* counter;
+  unsigned* bar;     // grid barrier of k_arnoldi: [0] arrivals, [1] generation
+  unsigned* err;     // device error word
+  volatile int* hdone;  // mapped host word: set to `ticket` when every right-hand side has converged
+  int ticket;
 };
+
+// Every right-hand side has converged: later kernels of this solve return at once, and the host
+// (which polls the mapped word after an event) stops launching.
+__device__ inline void mark_done(FState& s) {
+  *s.done = 1;
+  if (s.hdone) *s.hdone = s.ticket;
+}
 
 __device__ inline double2 to_d(float2 v) { return make_double2(v.x, v.y); }
 __device__ inline double2 to_d(double2 v) { return v; }
@@ -111,52 +123,68 @@ __device__ inline void cta_col_sum_store(double2 v, int nrhs, double2* out) {
   }
 }
 
-// Givens rotation and convergence test of Arnoldi step j for right-hand side r, given |w|^2.
-__device__ void arnoldi_step(FState& s, int r, int j, double n2, int* any) {
-  if (!s.active[r]) {
-    s.invh[r] = 0;
-    return;
-  }
-  const double hnext = sqrt(n2);
-  double2* Hc = s.H + (long long)r * (s.m + 1) * s.m;  // Hc[i * m + j]
+__device__ inline double2 shfl_d2(double2 v, int src) {
+  return make_double2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+
+// Givens rotation and convergence test of Arnoldi step j for right-hand side r, given |w|^2,
+// by one warp (restart length <= 64): lane l fetches entries l and l + 32 of the new
+// Hessenberg column and of the earlier rotations in one round of loads; the rotations then run
+// as a chain whose carried entry every lane holds, and lane i % 32 keeps the finished entry i.
+__device__ void arnoldi_step_warp(FState& s, int r, int j, double n2, int* any) {
+  const int lane = threadIdx.x & 31;
+  const double2 z = make_double2(0, 0);
+  double2* Hc = s.H + (long long)r * (s.m + 1) * s.m;
   double2* cs = s.cs + (long long)r * s.m;
   double2* sn = s.sn + (long long)r * s.m;
   double2* gv = s.gv + (long long)r * (s.m + 1);
-  // gather the column and the earlier rotations first (independent loads), rotate locally
-  double2 col[AMG_MAX_NTV + 1], c_[AMG_MAX_NTV], s_[AMG_MAX_NTV];
-  for (int i = 0; i <= j; ++i) col[i] = __ldcg(Hc + i * s.m + j);
-  for (int i = 0; i < j; ++i) {
-    c_[i] = __ldcg(cs + i);
-    s_[i] = __ldcg(sn + i);
+  const int act = __ldcg(s.active + r);
+  const double bn = __ldcg(s.bnorm + r);
+  const double2 gj = ld_cg(gv + j);
+  const double2 col0 = lane <= j ? ld_cg(Hc + lane * s.m + j) : z;
+  const double2 col1 = lane + 32 <= j ? ld_cg(Hc + (lane + 32) * s.m + j) : z;
+  const double2 c0 = lane < j ? ld_cg(cs + lane) : z, s0 = lane < j ? ld_cg(sn + lane) : z;
+  const double2 c1 = lane + 32 < j ? ld_cg(cs + lane + 32) : z, s1 = lane + 32 < j ? ld_cg(sn + lane + 32) : z;
+  if (!act) {
+    if (lane == 0) s.invh[r] = 0;
+    return;
   }
-  const double2 gj = __ldcg(gv + j);
-  col[j + 1] = make_double2(hnext, 0);
+  const double hnext = sqrt(n2);
+  double2 carry = shfl_d2(col0, 0), f0 = z, f1 = z;
   for (int i = 0; i < j; ++i) {
-    const double2 a = col[i], b = col[i + 1];
-    col[i] = cadd(cmul(c_[i], a), cmul(s_[i], b));
-    col[i + 1] = csub(cmul(cconj(c_[i]), b), cmul(cconj(s_[i]), a));
+    const double2 b = shfl_d2(i + 1 < 32 ? col0 : col1, (i + 1) & 31);
+    const double2 ci = shfl_d2(i < 32 ? c0 : c1, i & 31), si = shfl_d2(i < 32 ? s0 : s1, i & 31);
+    const double2 fin = cadd(cmul(ci, carry), cmul(si, b));
+    carry = csub(cmul(cconj(ci), b), cmul(cconj(si), carry));
+    if (lane == (i & 31)) {
+      if (i < 32) f0 = fin;
+      else f1 = fin;
+    }
   }
-  const double2 a = col[j];
-  const double den = sqrt(a.x * a.x + a.y * a.y + hnext * hnext);
-  const double2 c = den > 0 ? cscale(cconj(a), 1.0 / den) : make_double2(1, 0);
-  const double2 sv = den > 0 ? make_double2(hnext / den, 0) : make_double2(0, 0);
-  col[j] = make_double2(den, 0);
-  col[j + 1] = make_double2(0, 0);
-  for (int i = 0; i <= j + 1; ++i) Hc[i * s.m + j] = col[i];
-  cs[j] = c;
-  sn[j] = sv;
-  gv[j + 1] = cscale(cmul(cconj(sv), gj), -1.0);
-  gv[j] = cmul(c, gj);
-  const double rel = sqrt(gv[j + 1].x * gv[j + 1].x + gv[j + 1].y * gv[j + 1].y) / s.bnorm[r];
-  s.relres[r] = rel;
-  s.kcnt[r] = j + 1;
-  s.applies[r] += 1;
-  if (rel <= s.tol || hnext == 0) {
-    s.active[r] = 0;
-    s.invh[r] = 0;
-  } else {
-    s.invh[r] = 1.0 / hnext;
-    atomicOr(any, 1);
+  const double den = sqrt(carry.x * carry.x + carry.y * carry.y + hnext * hnext);
+  const double2 c = den > 0 ? cscale(cconj(carry), 1.0 / den) : make_double2(1, 0);
+  const double2 sv = den > 0 ? make_double2(hnext / den, 0) : z;
+  if (lane < j) Hc[lane * s.m + j] = f0;
+  if (lane + 32 < j) Hc[(lane + 32) * s.m + j] = f1;
+  if (lane == 0) {
+    Hc[j * s.m + j] = make_double2(den, 0);
+    Hc[(j + 1) * s.m + j] = z;
+    cs[j] = c;
+    sn[j] = sv;
+    const double2 g1 = cscale(cmul(cconj(sv), gj), -1.0);
+    gv[j + 1] = g1;
+    gv[j] = cmul(c, gj);
+    const double rel = sqrt(g1.x * g1.x + g1.y * g1.y) / bn;
+    s.relres[r] = rel;
+    s.kcnt[r] = j + 1;
+    s.applies[r] += 1;
+    if (rel <= s.tol || hnext == 0) {
+      s.active[r] = 0;
+      s.invh[r] = 0;
+    } else {
+      s.invh[r] = 1.0 / hnext;
+      atomicOr(any, 1);
+    }
   }
 }
 
@@ -191,7 +219,7 @@ __global__ void __launch_bounds__(ST_T) k_dots(FState s, const CT* __restrict__ 
   }
 }
 
-// w -= sum_{i<=j} H[r][i][j] V_i and |w|^2; the last CTA does the Givens step (arnoldi_step).
+// w -= sum_{i<=j} H[r][i][j] V_i and |w|^2; the last CTA does the Givens step (arnoldi_step_warp).
 template <typename CT>
 __global__ void __launch_bounds__(ST_T) k_update(FState s, CT* __restrict__ w, const CT* __restrict__ V,
                                                  long long vstride, int j) {
@@ -234,9 +262,9 @@ __global__ void __launch_bounds__(ST_T) k_update(FState s, CT* __restrict__ w, c
     if ((threadIdx.x & 31) == 0) n2s[r] = v.x;
   }
   __syncthreads();
-  if (threadIdx.x < s.nrhs) arnoldi_step(s, threadIdx.x, j, n2s[threadIdx.x], &any);
+  for (int r = threadIdx.x >> 5; r < s.nrhs; r += ST_T / 32) arnoldi_step_warp(s, r, j, n2s[r], &any);
   __syncthreads();
-  if (threadIdx.x == 0 && !any) *s.done = 1;
+  if (threadIdx.x == 0 && !any) mark_done(s);
 }
 
 template <typename CT>
@@ -293,14 +321,143 @@ __global__ void __launch_bounds__(ST_T) k_update_flat(FState s, CT* __restrict__
     if ((threadIdx.x & 31) == 0) n2s[r] = v.x;
   }
   __syncthreads();
-  if (threadIdx.x < s.nrhs) arnoldi_step(s, threadIdx.x, j, n2s[threadIdx.x], &any);
+  for (int r = threadIdx.x >> 5; r < s.nrhs; r += ST_T / 32) arnoldi_step_warp(s, r, j, n2s[r], &any);
   __syncthreads();
-  if (threadIdx.x == 0 && !any) *s.done = 1;
+  if (threadIdx.x == 0 && !any) mark_done(s);
+}
+
+// ---- fused Arnoldi step for nrhs in {1, 2, 4, 8, 16} (flat element loops as above): one
+// cooperative launch, one CTA per SM, does the dots, the Hessenberg column, the update with |w|^2
+// and the Givens step, with two grid barriers in place of a kernel boundary and a last-CTA
+// hand-off.  The vectors of the coarse solve are small (Vc * 2 Ntv rows), so each of these
+// phases is a few memory round trips and the launch and barrier latencies set the time.
+constexpr int AR_T = 512;
+constexpr int AR_W = AR_T / 32;
+constexpr int AR_IC = 4;  // dot products reduced per CTA round
+constexpr long long kBarCycles = 2000000000LL;  // about one second at GB300 clocks
+
+// Bounded grid barrier (every CTA resident: cooperative launch).  Thread 0 reads the generation
+// before it arrives; the last arrival resets the count and advances the generation.  A wait that
+// runs out sets AMG_EBIT_TIMEOUT and returns false.
+__device__ bool grid_sync(unsigned* bar, unsigned* err) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = bar + 1;
+    const unsigned g = *gen;
+    int good = 1;
+    __threadfence();
+    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*gen == g) {
+        if (clock64() - t0 > kBarCycles) {
+          atomicOr(err, AMG_EBIT_TIMEOUT);
+          good = 0;
+          break;
+        }
+      }
+      __threadfence();
+    }
+    ok = good;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+template <typename CT>
+__global__ void __launch_bounds__(AR_T) k_arnoldi(FState s, CT* __restrict__ w, const CT* __restrict__ V,
+                                                  long long vstride, int j) {
+  using RT = decltype(CT{}.x);
+  if (*s.done) return;
+  __shared__ double2 red[AR_IC][AR_W][MAXR];
+  __shared__ CT hc[AMG_MAX_NTV + 1][MAXR];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nr = s.nrhs, G = gridDim.x;
+  const long long n = s.rows * nr;
+  const long long e0 = (long long)blockIdx.x * AR_T + threadIdx.x, es = (long long)G * AR_T;
+  // 1. per-CTA partial sums of <V_i, w>, i = 0..j (lane l only ever meets column l % nr)
+  for (int i0 = 0; i0 <= j; i0 += AR_IC) {
+    const int ni = min(AR_IC, j + 1 - i0);
+    for (int ii = 0; ii < ni; ++ii) {
+      const CT* Vi = V + (i0 + ii) * vstride;
+      CT a = CT{0, 0};
+      for (long long e = e0; e < n; e += es) cfmac(a, Vi[e], w[e]);
+      double2 v = to_d(a);
+      for (int o = 16; o >= nr; o >>= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+      }
+      if (lane < nr) red[ii][warp][lane] = v;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < ni * nr; t += AR_T) {
+      const int ii = t / nr, r = t % nr;
+      double2 sum = make_double2(0, 0);
+      for (int wp = 0; wp < AR_W; ++wp) sum = cadd(sum, red[ii][wp][r]);
+      s.part[((long long)(i0 + ii) * G + blockIdx.x) * nr + r] = sum;
+    }
+    __syncthreads();
+  }
+  if (!grid_sync(s.bar, s.err)) return;
+  // 2. column j of H: one warp per (i, r) sums the G partials
+  const int P = (j + 1) * nr;
+  for (int t = blockIdx.x * AR_W + warp; t < P; t += G * AR_W) {
+    const double2 sum = warp_sum_partials(s.part, G, nr, t);
+    const int i = t / nr, r = t % nr;
+    if (lane == 0) s.H[((long long)r * (s.m + 1) + i) * s.m + j] = __ldcg(s.active + r) ? sum : make_double2(0, 0);
+  }
+  if (!grid_sync(s.bar, s.err)) return;
+  // 3. w -= sum_i H[r][i][j] V_i and the partial sums of |w|^2 (into row 0 of the partials,
+  // whose reads in 2. are complete)
+  for (int t = threadIdx.x; t < P; t += AR_T) {
+    const int i = t / nr, r = t % nr;
+    hc[i][r] = from_d<CT>(ld_cg(s.H + ((long long)r * (s.m + 1) + i) * s.m + j));
+  }
+  __syncthreads();
+  const int col = lane % nr;
+  RT acc = 0;
+  for (long long e = e0; e < n; e += es) {
+    CT v = w[e];
+    for (int i = 0; i <= j; ++i) {
+      const CT q = V[i * vstride + e];
+      const CT c = hc[i][col];
+      v.x -= c.x * q.x - c.y * q.y;
+      v.y -= c.x * q.y + c.y * q.x;
+    }
+    w[e] = v;
+    acc += v.x * v.x + v.y * v.y;
+  }
+  double v2 = (double)acc;
+  for (int o = 16; o >= nr; o >>= 1) v2 += __shfl_xor_sync(0xffffffffu, v2, o);
+  if (lane < nr) red[0][warp][lane] = make_double2(v2, 0);
+  __syncthreads();
+  if (threadIdx.x < nr) {
+    double sum = 0;
+    for (int wp = 0; wp < AR_W; ++wp) sum += red[0][wp][threadIdx.x].x;
+    s.part[(long long)blockIdx.x * nr + threadIdx.x] = make_double2(sum, 0);
+  }
+  // 4. the last CTA: |w|^2 per column and the Givens step, one warp per right-hand side
+  if (!last_block(s.counter, G)) return;
+  __shared__ int any;
+  __shared__ double n2s[MAXR];
+  if (threadIdx.x == 0) any = 0;
+  for (int r = warp; r < nr; r += AR_W) {
+    const double2 v = warp_sum_partials(s.part, G, nr, r);
+    if (lane == 0) n2s[r] = v.x;
+  }
+  __syncthreads();
+  for (int r = warp; r < nr; r += AR_W) arnoldi_step_warp(s, r, j, n2s[r], &any);
+  __syncthreads();
+  if (threadIdx.x == 0 && !any) mark_done(s);
 }
 
 // End of a cycle: every CTA solves the small triangular systems (one thread per right-hand
 // side), then x += sum_i y_i V_i over the columns built in the cycle.  The last CTA resets the
-// column counts, so a repeated call adds nothing.
+// column counts, so a repeated call adds nothing (after convergence the restart residual returns
+// at once and does not reset them).
 template <typename CT>
 __global__ void __launch_bounds__(ST_T) k_xupdate(FState s, CT* __restrict__ x, const CT* __restrict__ V,
                                                   long long vstride) {
@@ -427,7 +584,23 @@ __global__ void __launch_bounds__(ST_T) k_residual(FState s, CT* __restrict__ w,
     }
   }
   __syncthreads();
-  if (threadIdx.x == 0 && !any) *s.done = 1;
+  if (threadIdx.x == 0 && !any) mark_done(s);
+}
+
+// Grid of the cooperative k_arnoldi: one CTA per SM (at most NBLK, the partial-sum rows'
+// length); 0 when the device cannot hold it resident.
+template <typename CT>
+int arnoldi_grid() {
+  static int g = -1;
+  if (g < 0) {
+    int dev = 0, sms = 0, per = 0, coop = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_arnoldi<CT>, AR_T, 0);
+    g = (coop && per > 0) ? std::min(sms, NBLK) : 0;
+  }
+  return g;
 }
 
 size_t align256(size_t b) { return (b + 255) / 256 * 256; }
@@ -438,6 +611,8 @@ amg_status solve_impl(amg_coarse* h, long long rows, amg_apply_fn op, const CT* 
                       int max_applies, cudaStream_t st, double* info, unsigned char* ws, bool poll) {
   const long long vstride = rows * nrhs;
   const bool flat = nrhs > 1 && 32 % nrhs == 0;  // coalesced flat loops (see k_dots_flat)
+  const int ar_grid = 32 % nrhs == 0 ? arnoldi_grid<CT>() : 0;  // fused step (k_arnoldi) when > 0
+  SolveWork& sw = h->sw;
   FState s;
   s.m = m;
   s.nrhs = nrhs;
@@ -471,27 +646,29 @@ amg_status solve_impl(amg_coarse* h, long long rows, amg_apply_fn op, const CT* 
   s.applies = fl + 2 * nrhs;
   s.done = fl + 3 * nrhs;
   s.counter = (unsigned*)(fl + 3 * nrhs + 4);
+  s.bar = (unsigned*)(fl + 3 * nrhs + 5);
+  s.err = h->err;
+  s.hdone = poll ? sw.hdone_dev : nullptr;
+  s.ticket = poll ? ++sw.ticket : 0;
   const unsigned egrid = 4 * 152;
   AMG_CUDA_TRY(cudaMemsetAsync(fl, 0, (4 * (size_t)nrhs + 8) * sizeof(int), st));
   AMG_CUDA_TRY(cudaMemsetAsync(x, 0, (size_t)vstride * sizeof(CT), st));
   k_residual<CT><<<NBLK, ST_T, 0, st>>>(s, cur, b, 1);
   AMG_LAUNCH_CHECK();
   h->launches += 1;
-  SolveWork& sw = h->sw;
+  // The kernel that finds every right-hand side converged writes this solve's ticket into the
+  // mapped host word; the host stays at most one step ahead of the device (an event per step).
   int issued = 0, polled = 0;
   bool stop = false;
   auto poll_point = [&]() {
     if (!poll) return;
-    const int slot = issued % SolveWork::kRing;
-    cudaMemcpyAsync(sw.hflag + slot, s.done, sizeof(int), cudaMemcpyDeviceToHost, st);
-    cudaEventRecord(sw.ev[slot], st);
+    cudaEventRecord(sw.ev[issued % SolveWork::kRing], st);
     ++issued;
     while (issued - polled > 1) {
-      const int ps = polled % SolveWork::kRing;
-      cudaEventSynchronize(sw.ev[ps]);
-      if (sw.hflag[ps]) stop = true;
+      cudaEventSynchronize(sw.ev[polled % SolveWork::kRing]);
       ++polled;
     }
+    if (*(volatile int*)sw.hflag == s.ticket) stop = true;
   };
   int launched = 0;
   while (launched < max_applies && !stop) {
@@ -500,15 +677,23 @@ amg_status solve_impl(amg_coarse* h, long long rows, amg_apply_fn op, const CT* 
       // V_j = cur / h_{j,j-1} is written by the application itself, which reads cur scaled
       amg_status status = op(h, cur, nxt, nrhs, st, s.done, s.invh, V + j * vstride);
       if (status != AMG_OK) return status;
-      if (flat) {
-        k_dots_flat<CT><<<dim3(NBLK, j + 1), ST_T, 0, st>>>(s, nxt, V, vstride, j);
-        k_update_flat<CT><<<NBLK, ST_T, 0, st>>>(s, nxt, V, vstride, j);
+      if (ar_grid > 0) {
+        const CT* Vr = V;
+        int jj = j;
+        void* args[] = {&s, &nxt, &Vr, (void*)&vstride, &jj};
+        AMG_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_arnoldi<CT>, dim3(ar_grid), dim3(AR_T), args, 0, st));
+        h->launches += 1;
       } else {
-        k_dots<CT><<<dim3(NBLK, j + 1), ST_T, 0, st>>>(s, nxt, V, vstride, j);
-        k_update<CT><<<NBLK, ST_T, 0, st>>>(s, nxt, V, vstride, j);
+        if (flat) {
+          k_dots_flat<CT><<<dim3(NBLK, j + 1), ST_T, 0, st>>>(s, nxt, V, vstride, j);
+          k_update_flat<CT><<<NBLK, ST_T, 0, st>>>(s, nxt, V, vstride, j);
+        } else {
+          k_dots<CT><<<dim3(NBLK, j + 1), ST_T, 0, st>>>(s, nxt, V, vstride, j);
+          k_update<CT><<<NBLK, ST_T, 0, st>>>(s, nxt, V, vstride, j);
+        }
+        AMG_LAUNCH_CHECK();
+        h->launches += 2;
       }
-      AMG_LAUNCH_CHECK();
-      h->launches += 2;
       std::swap(cur, nxt);
       ++launched;
       poll_point();
@@ -571,7 +756,9 @@ amg_status ensure_solve_work(amg_coarse* h, int nrhs, int restart, cudaStream_t 
     sw.bytes = need;
   }
   if (!sw.hflag) {
-    AMG_CUDA_TRY(cudaHostAlloc((void**)&sw.hflag, SolveWork::kRing * sizeof(int), cudaHostAllocDefault));
+    AMG_CUDA_TRY(cudaHostAlloc((void**)&sw.hflag, sizeof(int), cudaHostAllocMapped));
+    *sw.hflag = 0;
+    AMG_CUDA_TRY(cudaHostGetDevicePointer((void**)&sw.hdone_dev, sw.hflag, 0));
     for (int k = 0; k < SolveWork::kRing; ++k)
       AMG_CUDA_TRY(cudaEventCreateWithFlags(&sw.ev[k], cudaEventDisableTiming));
   }
@@ -596,20 +783,6 @@ amg_status amg_internal_solve_op(amg_coarse* h, long long rows, amg_apply_fn op,
 amg_status amg_internal_solve(amg_coarse* h, const void* b, void* x, int nrhs, double tol, int restart,
                               int max_applies, cudaStream_t s, double* info) {
   if (nrhs > MAXR || restart < 1 || restart > AMG_MAX_NTV || max_applies < 1) return AMG_ERR_INVALID_ARG;
-  SolveWork& sw = h->sw;
-  const size_t need = amg_internal_solve_bytes(h, nrhs, restart);
-  if (need > sw.bytes) {
-    AMG_CUDA_TRY(cudaStreamSynchronize(s));
-    cudaFree(sw.buf);
-    sw.buf = nullptr;
-    sw.bytes = 0;
-    AMG_CUDA_TRY(cudaMalloc(&sw.buf, need));
-    sw.bytes = need;
-  }
-  if (!sw.hflag) {
-    AMG_CUDA_TRY(cudaHostAlloc((void**)&sw.hflag, SolveWork::kRing * sizeof(int), cudaHostAllocDefault));
-    for (int k = 0; k < SolveWork::kRing; ++k)
-      AMG_CUDA_TRY(cudaEventCreateWithFlags(&sw.ev[k], cudaEventDisableTiming));
-  }
-  return amg_internal_solve_ws(h, b, x, nrhs, tol, restart, max_applies, s, info, sw.buf, true);
+  AMG_TRY_INTERNAL(ensure_solve_work(h, nrhs, restart, s));
+  return amg_internal_solve_ws(h, b, x, nrhs, tol, restart, max_applies, s, info, h->sw.buf, true);
 }
