@@ -9,9 +9,9 @@
 // rotation and convergence test, phases separated by grid barriers).  Other column counts take
 // three launches (k_dots, then k_update, each ending in a last-CTA reduction).  Once every
 // right-hand side has converged the device flag `done` makes every later kernel return at once
-// and a mapped host word receives the solve's ticket; the host reads it after an event one step
-// behind the launch front (so the GPU never waits for the host) or, without polling, launches
-// the whole budget.
+// and a mapped host word receives the solve's ticket; the host reads it after the next
+// application is queued (so the GPU never waits for the host) or, without polling, launches the
+// whole budget.
 #include "amg_internal.cuh"
 
 #include <algorithm>
@@ -510,7 +510,8 @@ __global__ void __launch_bounds__(ST_T) k_xupdate(FState s, CT* __restrict__ x, 
 // w = b - w (restart residual; first = 1: w = b) and |w|^2; the last CTA starts the cycle:
 // beta = |r|, convergence test, g = (beta, 0, ...), invh = 1 / beta.
 template <typename CT>
-__global__ void __launch_bounds__(ST_T) k_residual(FState s, CT* __restrict__ w, const CT* __restrict__ b, int first) {
+__global__ void __launch_bounds__(ST_T) k_residual(FState s, CT* __restrict__ w, const CT* __restrict__ b, int first,
+                                                   CT* __restrict__ xzero) {
   if (*s.done) return;
   if (s.nrhs > 1 && 32 % s.nrhs == 0) {  // flat, coalesced (see k_dots_flat)
     const long long n = s.rows * s.nrhs;
@@ -523,6 +524,7 @@ __global__ void __launch_bounds__(ST_T) k_residual(FState s, CT* __restrict__ w,
         v.y -= q.y;
       }
       w[e] = v;
+      if (xzero) xzero[e] = CT{0, 0};
       acc += v.x * v.x + v.y * v.y;
     }
     cta_col_sum_store(make_double2((double)acc, 0.0), s.nrhs, s.part + (long long)blockIdx.x * s.nrhs);
@@ -542,6 +544,7 @@ __global__ void __launch_bounds__(ST_T) k_residual(FState s, CT* __restrict__ w,
           v.y -= q.y;
         }
         w[row * s.nrhs + r] = v;
+        if (xzero) xzero[row * s.nrhs + r] = CT{0, 0};
         a[r].x += v.x * v.x + v.y * v.y;
       }
     }
@@ -652,31 +655,39 @@ amg_status solve_impl(amg_coarse* h, long long rows, amg_apply_fn op, const CT* 
   s.ticket = poll ? ++sw.ticket : 0;
   const unsigned egrid = 4 * 152;
   AMG_CUDA_TRY(cudaMemsetAsync(fl, 0, (4 * (size_t)nrhs + 8) * sizeof(int), st));
-  AMG_CUDA_TRY(cudaMemsetAsync(x, 0, (size_t)vstride * sizeof(CT), st));
-  k_residual<CT><<<NBLK, ST_T, 0, st>>>(s, cur, b, 1);
+  k_residual<CT><<<NBLK, ST_T, 0, st>>>(s, cur, b, 1, x);  // also x = 0
   AMG_LAUNCH_CHECK();
   h->launches += 1;
   // The kernel that finds every right-hand side converged writes this solve's ticket into the
-  // mapped host word; the host stays at most one step ahead of the device (an event per step).
-  int issued = 0, polled = 0;
-  bool stop = false;
-  auto poll_point = [&]() {
+  // mapped host word.  An event follows each Arnoldi step (and each restart residual); once the
+  // next application is queued the host waits for that event and reads the word, so the device
+  // always has an application in hand while the host decides, and a converged solve launches no
+  // further Arnoldi step (its one speculative application returns at once on the device flag).
+  int pending = -1;
+  auto record = [&]() {
     if (!poll) return;
-    cudaEventRecord(sw.ev[issued % SolveWork::kRing], st);
-    ++issued;
-    while (issued - polled > 1) {
-      cudaEventSynchronize(sw.ev[polled % SolveWork::kRing]);
-      ++polled;
-    }
-    if (*(volatile int*)sw.hflag == s.ticket) stop = true;
+    pending = (pending + 1) % SolveWork::kRing;
+    cudaEventRecord(sw.ev[pending], st);
   };
+  auto converged = [&]() -> bool {
+    if (!poll) return false;
+    cudaEventSynchronize(sw.ev[pending]);
+    return *(volatile int*)sw.hflag == s.ticket;
+  };
+  record();
+  bool stop = false;
   int launched = 0;
   while (launched < max_applies && !stop) {
     const int mc = std::min(m, max_applies - launched);
-    for (int j = 0; j < mc && !stop; ++j) {
+    for (int j = 0; j < mc; ++j) {
       // V_j = cur / h_{j,j-1} is written by the application itself, which reads cur scaled
       amg_status status = op(h, cur, nxt, nrhs, st, s.done, s.invh, V + j * vstride);
       if (status != AMG_OK) return status;
+      ++launched;
+      if (converged()) {
+        stop = true;
+        break;
+      }
       if (ar_grid > 0) {
         const CT* Vr = V;
         int jj = j;
@@ -695,8 +706,7 @@ amg_status solve_impl(amg_coarse* h, long long rows, amg_apply_fn op, const CT* 
         h->launches += 2;
       }
       std::swap(cur, nxt);
-      ++launched;
-      poll_point();
+      record();
     }
     k_xupdate<CT><<<egrid, ST_T, 0, st>>>(s, x, V, vstride);
     AMG_LAUNCH_CHECK();
@@ -705,10 +715,10 @@ amg_status solve_impl(amg_coarse* h, long long rows, amg_apply_fn op, const CT* 
     amg_status status = op(h, x, cur, nrhs, st, s.done, nullptr, nullptr);
     if (status != AMG_OK) return status;
     ++launched;
-    k_residual<CT><<<NBLK, ST_T, 0, st>>>(s, cur, b, 0);
+    k_residual<CT><<<NBLK, ST_T, 0, st>>>(s, cur, b, 0, (CT*)nullptr);
     AMG_LAUNCH_CHECK();
     h->launches += 1;
-    poll_point();
+    record();
   }
   if (info) {
     int applies[MAXR];
