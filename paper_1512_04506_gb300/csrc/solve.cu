@@ -334,6 +334,7 @@ __global__ void __launch_bounds__(ST_T) k_update_flat(FState s, CT* __restrict__
 constexpr int AR_T = 512;
 constexpr int AR_W = AR_T / 32;
 constexpr int AR_IC = 4;  // dot products reduced per CTA round
+constexpr int AR_U = 4;   // elements per thread whose loads are issued together (long vectors)
 constexpr long long kBarCycles = 2000000000LL;  // about one second at GB300 clocks
 
 // Bounded grid barrier (every CTA resident: cooperative launch).  Thread 0 reads the generation
@@ -381,16 +382,35 @@ __global__ void __launch_bounds__(AR_T) k_arnoldi(FState s, CT* __restrict__ w, 
   // 1. per-CTA partial sums of <V_i, w>, i = 0..j (lane l only ever meets column l % nr)
   for (int i0 = 0; i0 <= j; i0 += AR_IC) {
     const int ni = min(AR_IC, j + 1 - i0);
-    for (int ii = 0; ii < ni; ++ii) {
-      const CT* Vi = V + (i0 + ii) * vstride;
-      CT a = CT{0, 0};
-      for (long long e = e0; e < n; e += es) cfmac(a, Vi[e], w[e]);
-      double2 v = to_d(a);
-      for (int o = 16; o >= nr; o >>= 1) {
-        v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
-        v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+    CT a[AR_IC];
+#pragma unroll
+    for (int ii = 0; ii < AR_IC; ++ii) a[ii] = CT{0, 0};
+    for (long long eb = e0; eb < n; eb += AR_U * es) {
+      CT wv[AR_U];
+#pragma unroll
+      for (int u = 0; u < AR_U; ++u) wv[u] = eb + u * es < n ? w[eb + u * es] : CT{0, 0};
+#pragma unroll
+      for (int ii = 0; ii < AR_IC; ++ii) {
+        if (ii < ni) {
+          const CT* Vi = V + (i0 + ii) * vstride;
+          CT vv[AR_U];
+#pragma unroll
+          for (int u = 0; u < AR_U; ++u) vv[u] = eb + u * es < n ? Vi[eb + u * es] : CT{0, 0};
+#pragma unroll
+          for (int u = 0; u < AR_U; ++u) cfmac(a[ii], vv[u], wv[u]);
+        }
       }
-      if (lane < nr) red[ii][warp][lane] = v;
+    }
+#pragma unroll
+    for (int ii = 0; ii < AR_IC; ++ii) {
+      if (ii < ni) {
+        double2 v = to_d(a[ii]);
+        for (int o = 16; o >= nr; o >>= 1) {
+          v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+          v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+        }
+        if (lane < nr) red[ii][warp][lane] = v;
+      }
     }
     __syncthreads();
     for (int t = threadIdx.x; t < ni * nr; t += AR_T) {
@@ -419,16 +439,27 @@ __global__ void __launch_bounds__(AR_T) k_arnoldi(FState s, CT* __restrict__ w, 
   __syncthreads();
   const int col = lane % nr;
   RT acc = 0;
-  for (long long e = e0; e < n; e += es) {
-    CT v = w[e];
+  for (long long eb = e0; eb < n; eb += AR_U * es) {
+    CT v[AR_U];
+#pragma unroll
+    for (int u = 0; u < AR_U; ++u) v[u] = eb + u * es < n ? w[eb + u * es] : CT{0, 0};
     for (int i = 0; i <= j; ++i) {
-      const CT q = V[i * vstride + e];
       const CT c = hc[i][col];
-      v.x -= c.x * q.x - c.y * q.y;
-      v.y -= c.x * q.y + c.y * q.x;
+      CT q[AR_U];
+#pragma unroll
+      for (int u = 0; u < AR_U; ++u) q[u] = eb + u * es < n ? V[i * vstride + eb + u * es] : CT{0, 0};
+#pragma unroll
+      for (int u = 0; u < AR_U; ++u) {
+        v[u].x -= c.x * q[u].x - c.y * q[u].y;
+        v[u].y -= c.x * q[u].y + c.y * q[u].x;
+      }
     }
-    w[e] = v;
-    acc += v.x * v.x + v.y * v.y;
+#pragma unroll
+    for (int u = 0; u < AR_U; ++u)
+      if (eb + u * es < n) {
+        w[eb + u * es] = v[u];
+        acc += v[u].x * v[u].x + v[u].y * v[u].y;
+      }
   }
   double v2 = (double)acc;
   for (int o = 16; o >= nr; o >>= 1) v2 += __shfl_xor_sync(0xffffffffu, v2, o);
