@@ -683,7 +683,8 @@ amg_status solve_impl(amg_coarse* h, long long rows, amg_apply_fn op, const CT* 
   s.bar = (unsigned*)(fl + 3 * nrhs + 5);
   s.err = h->err;
   s.hdone = poll ? sw.hdone_dev : nullptr;
-  s.ticket = poll ? ++sw.ticket : 0;
+  if (poll) sw.ticket = sw.ticket >= (1 << 30) ? 1 : sw.ticket + 1;  // never 0, the word's initial value
+  s.ticket = poll ? sw.ticket : 0;
   const unsigned egrid = 4 * 152;
   AMG_CUDA_TRY(cudaMemsetAsync(fl, 0, (4 * (size_t)nrhs + 8) * sizeof(int), st));
   k_residual<CT><<<NBLK, ST_T, 0, st>>>(s, cur, b, 1, x);  // also x = 0
