@@ -34,6 +34,21 @@ __device__ inline void bulk_load(void* dst, const void* src, unsigned bytes, uin
                "l"(src), "r"(bytes), "r"(smem_addr(bar))
                : "memory");
 }
+// L2 policy for data streamed once (a coarse operator larger than L2): evict first, so that the
+// small vectors around it (the Krylov basis of the coarse solve) stay resident.
+__device__ inline uint64_t l2_evict_first_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+// bulk_load with an L2 cache policy
+__device__ inline void bulk_load_hint(void* dst, const void* src, unsigned bytes, uint64_t* bar, uint64_t pol) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(pol)
+      : "memory");
+}
 __device__ inline void consumer_sync(int nthreads) { asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory"); }
 
 constexpr long long kWaitCycles = 2000000000LL;  // about one second at GB300 clocks

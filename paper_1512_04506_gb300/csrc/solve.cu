@@ -333,7 +333,8 @@ __global__ void __launch_bounds__(ST_T) k_update_flat(FState s, CT* __restrict__
 // phases is a few memory round trips and the launch and barrier latencies set the time.
 constexpr int AR_T = 512;
 constexpr int AR_W = AR_T / 32;
-constexpr int AR_IC = 4;  // dot products reduced per CTA round
+template <typename CT>
+constexpr int ar_ic() { return sizeof(CT) == 8 ? 8 : 4; }  // dot products reduced per CTA round
 constexpr int AR_U = 4;   // elements per thread whose loads are issued together (long vectors)
 constexpr long long kBarCycles = 2000000000LL;  // about one second at GB300 clocks
 
@@ -374,6 +375,7 @@ __global__ void __launch_bounds__(AR_T) k_arnoldi(FState s, CT* __restrict__ w, 
                                                   long long vstride, int j) {
   using RT = decltype(CT{}.x);
   if (*s.done) return;
+  constexpr int AR_IC = ar_ic<CT>();
   __shared__ double2 red[AR_IC][AR_W][MAXR];
   __shared__ CT hc[AMG_MAX_NTV + 1][MAXR];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nr = s.nrhs, G = gridDim.x;
@@ -443,7 +445,25 @@ __global__ void __launch_bounds__(AR_T) k_arnoldi(FState s, CT* __restrict__ w, 
     CT v[AR_U];
 #pragma unroll
     for (int u = 0; u < AR_U; ++u) v[u] = eb + u * es < n ? w[eb + u * es] : CT{0, 0};
-    for (int i = 0; i <= j; ++i) {
+    // four basis vectors per round of loads
+    int i = 0;
+    for (; i + 4 <= j + 1; i += 4) {
+      CT q[4][AR_U];
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int u = 0; u < AR_U; ++u) q[k][u] = eb + u * es < n ? V[(i + k) * vstride + eb + u * es] : CT{0, 0};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const CT c = hc[i + k][col];
+#pragma unroll
+        for (int u = 0; u < AR_U; ++u) {
+          v[u].x -= c.x * q[k][u].x - c.y * q[k][u].y;
+          v[u].y -= c.x * q[k][u].y + c.y * q[k][u].x;
+        }
+      }
+    }
+    for (; i <= j; ++i) {
       const CT c = hc[i][col];
       CT q[AR_U];
 #pragma unroll
@@ -485,32 +505,52 @@ __global__ void __launch_bounds__(AR_T) k_arnoldi(FState s, CT* __restrict__ w, 
   if (threadIdx.x == 0 && !any) mark_done(s);
 }
 
-// End of a cycle: every CTA solves the small triangular systems (one thread per right-hand
-// side), then x += sum_i y_i V_i over the columns built in the cycle.  The last CTA resets the
-// column counts, so a repeated call adds nothing (after convergence the restart residual returns
-// at once and does not reset them).
+// End of a cycle: every CTA solves the small triangular systems R y = g (one warp per right-hand
+// side, column by column from the last: lane l holds the residual entries l and l + 32 of g, and
+// the next column's loads are issued before the current one is used), then x += sum_i y_i V_i
+// over the columns built in the cycle.  The last CTA resets the column counts, so a repeated call
+// adds nothing (after convergence the restart residual returns at once and does not reset them).
 template <typename CT>
 __global__ void __launch_bounds__(ST_T) k_xupdate(FState s, CT* __restrict__ x, const CT* __restrict__ V,
                                                   long long vstride) {
   __shared__ double2 yd[MAXR][AMG_MAX_NTV];
   __shared__ CT yc[AMG_MAX_NTV][MAXR];
   __shared__ int kmax;
+  const int lane = threadIdx.x & 31;
+  const double2 z = make_double2(0, 0);
   if (threadIdx.x == 0) kmax = 0;
   __syncthreads();
-  if (threadIdx.x < s.nrhs) {
-    const int r = threadIdx.x;
+  for (int r = threadIdx.x >> 5; r < s.nrhs; r += ST_T / 32) {
     const int k = __ldcg(s.kcnt + r);
     const double2* Hc = s.H + (long long)r * (s.m + 1) * s.m;
     const double2* gv = s.gv + (long long)r * (s.m + 1);
-    for (int i = k - 1; i >= 0; --i) {
-      double2 t = ld_cg(gv + i);
-      for (int l = i + 1; l < k; ++l) t = csub(t, cmul(ld_cg(Hc + i * s.m + l), yd[r][l]));
-      const double2 d = ld_cg(Hc + i * s.m + i);
-      const double dd = d.x * d.x + d.y * d.y;
-      yd[r][i] = dd > 0 ? cscale(cmulc(d, t), 1.0 / dd) : make_double2(0, 0);
+    double2 t0 = lane < k ? ld_cg(gv + lane) : z, t1 = lane + 32 < k ? ld_cg(gv + lane + 32) : z;
+    for (int i = k + lane; i < s.m; i += 32) yd[r][i] = z;
+    int i = k - 1;
+    double2 h0 = z, h1 = z, dg = z;
+    if (i >= 0) {
+      h0 = lane < i ? ld_cg(Hc + lane * s.m + i) : z;
+      h1 = lane + 32 < i ? ld_cg(Hc + (lane + 32) * s.m + i) : z;
+      dg = ld_cg(Hc + i * s.m + i);
     }
-    for (int i = k; i < s.m; ++i) yd[r][i] = make_double2(0, 0);
-    atomicMax(&kmax, k);
+    for (; i >= 0; --i) {
+      double2 n0 = z, n1 = z, nd = z;
+      if (i > 0) {
+        n0 = lane < i - 1 ? ld_cg(Hc + lane * s.m + i - 1) : z;
+        n1 = lane + 32 < i - 1 ? ld_cg(Hc + (lane + 32) * s.m + i - 1) : z;
+        nd = ld_cg(Hc + (i - 1) * s.m + i - 1);
+      }
+      const double2 ti = shfl_d2(i < 32 ? t0 : t1, i & 31);
+      const double dd = dg.x * dg.x + dg.y * dg.y;
+      const double2 yi = dd > 0 ? cscale(cmulc(dg, ti), 1.0 / dd) : z;
+      if (lane == 0) yd[r][i] = yi;
+      if (lane < i) t0 = csub(t0, cmul(h0, yi));
+      if (lane + 32 < i) t1 = csub(t1, cmul(h1, yi));
+      h0 = n0;
+      h1 = n1;
+      dg = nd;
+    }
+    if (lane == 0) atomicMax(&kmax, k);
   }
   __syncthreads();
   for (int e = threadIdx.x; e < s.m * s.nrhs; e += blockDim.x) {
@@ -525,7 +565,19 @@ __global__ void __launch_bounds__(ST_T) k_xupdate(FState s, CT* __restrict__ x, 
          e += (long long)gridDim.x * blockDim.x) {
       const int r = (int)(e % s.nrhs);
       CT v = x[e];
-      for (int i = 0; i < km; ++i) {
+      int i = 0;
+      for (; i + 4 <= km; i += 4) {  // four basis vectors per round of loads
+        CT q[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) q[k] = V[(i + k) * vstride + e];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const CT c = yc[i + k][r];
+          v.x += c.x * q[k].x - c.y * q[k].y;
+          v.y += c.x * q[k].y + c.y * q[k].x;
+        }
+      }
+      for (; i < km; ++i) {
         const CT q = V[i * vstride + e];
         const CT c = yc[i][r];
         v.x += c.x * q.x - c.y * q.y;

@@ -316,6 +316,7 @@ __global__ void __launch_bounds__(288) apply_mrhs_kernel(const MrhsArgs<LT, NR> 
       int s = 0;
       unsigned ph = 0;
       int nb[9], nx[9];
+      const uint64_t pol = l2_evict_first_policy();  // D_c is streamed once per application
       if (blockIdx.x < Vc)
         for (int d = 0; d < 9; ++d) nx[d] = __ldg(a.nbr + blockIdx.x * 9LL + d);
       for (long long i = blockIdx.x; i < Vc && !pp->abort; i += gridDim.x) {
@@ -334,7 +335,7 @@ __global__ void __launch_bounds__(288) apply_mrhs_kernel(const MrhsArgs<LT, NR> 
           }
           mbar_expect_tx(&pp->full[s], chunk);
           unsigned char* st = stages + (size_t)s * chunk;
-          bulk_load(st, a.D + (i * 9 + d) * nc2, dbytes, &pp->full[s]);
+          bulk_load_hint(st, a.D + (i * 9 + d) * nc2, dbytes, &pp->full[s], pol);
           bulk_load(st + dbytes, a.x + (long long)nb[d] * nc * NR, xbytes, &pp->full[s]);
           ++c;
           if (++s == ns) {
