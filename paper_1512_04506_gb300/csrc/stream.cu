@@ -166,7 +166,8 @@ __global__ void __launch_bounds__(288) apply_tma_kernel(const ApplyArgs<LT, NR> 
             break;
           }
           mbar_expect_tx(&pp->full[s], chunk);
-          bulk_load(stages + (size_t)s * chunk, a.D + (i * 9 + d) * (long long)nc * nc, chunk, &pp->full[s]);
+          bulk_load_hint(stages + (size_t)s * chunk, a.D + (i * 9 + d) * (long long)nc * nc, chunk, &pp->full[s],
+                         l2_evict_first_policy());
         }
       }
       drain(pp, c, ns);
@@ -507,7 +508,7 @@ __global__ void __launch_bounds__(288) eo_apply_kernel(const EoArgs<LT, NR> a) {
           const LT* src = d == a.d1 ? a.Dinv + h * nc2
                                     : (d == 0 ? (a.inv0 ? a.Dinv + h * nc2 : a.D + site * 9 * nc2)
                                               : a.D + (site * 9 + d) * nc2);
-          bulk_load(stages + (size_t)s * chunk, src, chunk, &pp->full[s]);
+          bulk_load_hint(stages + (size_t)s * chunk, src, chunk, &pp->full[s], l2_evict_first_policy());
         }
       }
       drain(pp, c, ns);
@@ -682,7 +683,7 @@ __global__ void __launch_bounds__(288) eo_mrhs_kernel(const EoArgs<float2, NR> a
           const float2* blk = post ? a.Dinv + h * nc2
                                    : (d == 0 ? (a.inv0 ? a.Dinv + h * nc2 : a.D + site * 9 * nc2)
                                              : a.D + (site * 9 + d) * nc2);
-          bulk_load(st, blk, dbytes, &pp->full[s]);
+          bulk_load_hint(st, blk, dbytes, &pp->full[s], l2_evict_first_policy());
           if (!post) {
             const float2* src = d == 0 ? a.s0 + h * nc * NR
                                        : a.s1 + (long long)(__ldg(a.nbr + site * 9 + d) >> 1) * nc * NR;
@@ -911,8 +912,9 @@ __global__ void __launch_bounds__(160) prolong_tma_kernel(const ProlongArgs<ST, 
         if (!ok) break;
         // lanes issue the ntv row copies; all complete on the stage's full barrier
         for (int j = threadIdx.x; j < ntv; j += 32)
-          bulk_load(stages + (size_t)s * chunk + (size_t)j * rowb,
-                    a.R + ((blk * 2 + hh) * ntv + j) * (long long)nagg + n0, rowb, &pp->full[s]);
+          bulk_load_hint(stages + (size_t)s * chunk + (size_t)j * rowb,
+                         a.R + ((blk * 2 + hh) * ntv + j) * (long long)nagg + n0, rowb, &pp->full[s],
+                         l2_evict_first_policy());
         __syncwarp();
       }
     }

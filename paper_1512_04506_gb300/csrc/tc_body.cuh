@@ -196,7 +196,7 @@ __device__ void apply_tc_items(const TcApplyArgs& a, const Ring& rg, long long i
         for (int d = 0; d < 9; ++d) {
           unsigned char* st = ring_acquire(rg, rp, dbytes + xbytes, a.err, ok);
           if (!ok) break;
-          bulk_load(st, a.D + (i * 9 + d) * 2LL * nc * nc, dbytes, &pp->full[rp.s]);
+          bulk_load_hint(st, a.D + (i * 9 + d) * 2LL * nc * nc, dbytes, &pp->full[rp.s], l2_evict_first_policy());
           bulk_load(st + dbytes, reinterpret_cast<const unsigned char*>(a.X) + (long long)nb[d] * xbytes, xbytes,
                     &pp->full[rp.s]);
           rp.advance(rg.ns);
@@ -317,7 +317,8 @@ __device__ void restrict_tc_items(const TcRPArgs& a, const Ring& rg, long long i
         for (int cc = 0; cc < cpb; ++cc) {
           unsigned char* st = ring_acquire(rg, rp, rbytes + 8 * 48 * NRHS, a.err, ok);
           if (!ok) break;
-          bulk_load(st, a.R + (blk * cpb + cc) * (long long)(rbytes / sizeof(bf16)), rbytes, &pp->full[rp.s]);
+          bulk_load_hint(st, a.R + (blk * cpb + cc) * (long long)(rbytes / sizeof(bf16)), rbytes, &pp->full[rp.s],
+                         l2_evict_first_policy());
           for (int sl = 0; sl < 8; ++sl) {
             const long long site = block_site_fast(a.g, origin, 8 * cc + sl);
             bulk_load(st + rbytes + sl * YSITE, Y + site * 48 * NRHS, 48 * NRHS, &pp->full[rp.s]);
@@ -426,7 +427,8 @@ __device__ void prolong_tc_items(const TcRPArgs& a, const Ring& rg, long long i0
         for (int cc = 0; cc < cpb; ++cc) {
           unsigned char* st = ring_acquire(rg, rp, chunk, a.err, ok);
           if (!ok) break;
-          bulk_load(st, a.R + (blk * cpb + cc) * (long long)(chunk / sizeof(bf16)), chunk, &pp->full[rp.s]);
+          bulk_load_hint(st, a.R + (blk * cpb + cc) * (long long)(chunk / sizeof(bf16)), chunk, &pp->full[rp.s],
+                         l2_evict_first_policy());
           rp.advance(rg.ns);
         }
         if (!ok) break;
@@ -614,7 +616,7 @@ __device__ void apply_tf32_items(const TfApplyArgs& a, const Ring& rg, long long
         for (int d = 0; d < 9; ++d) {
           unsigned char* st = ring_acquire(rg, rp, dbytes + xbytes, a.err, ok);
           if (!ok) break;
-          bulk_load(st, a.D + (i * 9 + d) * 2LL * nc * nc, dbytes, &pp->full[rp.s]);
+          bulk_load_hint(st, a.D + (i * 9 + d) * 2LL * nc * nc, dbytes, &pp->full[rp.s], l2_evict_first_policy());
           bulk_load(st + dbytes, reinterpret_cast<const unsigned char*>(a.X) + (long long)nb[d] * xbytes, xbytes,
                     &pp->full[rp.s]);
           rp.advance(rg.ns);
