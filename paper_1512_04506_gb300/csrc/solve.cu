@@ -127,10 +127,34 @@ __device__ inline double2 shfl_d2(double2 v, int src) {
   return make_double2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
 }
 
-// Givens rotation and convergence test of Arnoldi step j for right-hand side r, given |w|^2,
-// by one warp (restart length <= 64): lane l fetches entries l and l + 32 of the new
-// Hessenberg column and of the earlier rotations in one round of loads; the rotations then run
-// as a chain whose carried entry every lane holds, and lane i % 32 keeps the finished entry i.
+// Givens rotation and convergence test of Arnoldi step j for right-hand side r, given |w|^2 = n2,
+// by one warp (restart length <= 64): lane l fetches entries l and l + 32 of the new Hessenberg
+// column and of the earlier rotations in one round of loads.  Applying the earlier rotations to
+// the column is a linear recurrence in the entry carried from rotation i to i + 1:
+// carry_{i+1} = conj(c_i) col[i+1] - conj(s_i) carry_i, carry_0 = col[0], and the finished
+// entries are c_i carry_i + s_i col[i+1].  The carries are a prefix composition of the complex
+// affine maps x -> A_i + B_i x, taken as a warp scan (five shuffle rounds per 32 rotations)
+// instead of a chain of j dependent steps.
+__device__ inline void givens_scan_half(const double2& ci, const double2& si, const double2& b, bool valid, double2 x0,
+                                        double2& carry_i, double2& carry_next) {
+  const int lane = threadIdx.x & 31;
+  double2 A = valid ? cmulc(ci, b) : make_double2(0, 0);               // conj(c_i) b
+  double2 Bm = valid ? make_double2(-si.x, si.y) : make_double2(1, 0);  // -conj(s_i)
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double2 Ap = make_double2(__shfl_up_sync(0xffffffffu, A.x, o), __shfl_up_sync(0xffffffffu, A.y, o));
+    const double2 Bp = make_double2(__shfl_up_sync(0xffffffffu, Bm.x, o), __shfl_up_sync(0xffffffffu, Bm.y, o));
+    if (lane >= o) {
+      A = cadd(A, cmul(Bm, Ap));
+      Bm = cmul(Bm, Bp);
+    }
+  }
+  carry_next = cadd(A, cmul(Bm, x0));
+  const double2 prev = make_double2(__shfl_up_sync(0xffffffffu, carry_next.x, 1),
+                                    __shfl_up_sync(0xffffffffu, carry_next.y, 1));
+  carry_i = lane == 0 ? x0 : prev;
+}
+
 __device__ void arnoldi_step_warp(FState& s, int r, int j, double n2, int* any) {
   const int lane = threadIdx.x & 31;
   const double2 z = make_double2(0, 0);
@@ -150,16 +174,22 @@ __device__ void arnoldi_step_warp(FState& s, int r, int j, double n2, int* any) 
     return;
   }
   const double hnext = sqrt(n2);
-  double2 carry = shfl_d2(col0, 0), f0 = z, f1 = z;
-  for (int i = 0; i < j; ++i) {
-    const double2 b = shfl_d2(i + 1 < 32 ? col0 : col1, (i + 1) & 31);
-    const double2 ci = shfl_d2(i < 32 ? c0 : c1, i & 31), si = shfl_d2(i < 32 ? s0 : s1, i & 31);
-    const double2 fin = cadd(cmul(ci, carry), cmul(si, b));
-    carry = csub(cmul(cconj(ci), b), cmul(cconj(si), carry));
-    if (lane == (i & 31)) {
-      if (i < 32) f0 = fin;
-      else f1 = fin;
-    }
+  // col[i + 1] for rotation i = lane (first half) and i = lane + 32 (second half)
+  const double2 c32 = shfl_d2(col1, 0);
+  double2 b0 = make_double2(__shfl_down_sync(0xffffffffu, col0.x, 1), __shfl_down_sync(0xffffffffu, col0.y, 1));
+  if (lane == 31) b0 = c32;
+  const double2 b1 = make_double2(__shfl_down_sync(0xffffffffu, col1.x, 1), __shfl_down_sync(0xffffffffu, col1.y, 1));
+  const double2 x0 = shfl_d2(col0, 0);
+  double2 ci0, cn0, carry = x0, f0 = z, f1 = z;
+  givens_scan_half(c0, s0, b0, lane < j, x0, ci0, cn0);
+  if (lane < j) f0 = cadd(cmul(c0, ci0), cmul(s0, b0));
+  if (j > 0 && j <= 32) carry = shfl_d2(cn0, j - 1);
+  if (j > 32) {
+    const double2 x32 = shfl_d2(cn0, 31);
+    double2 ci1, cn1;
+    givens_scan_half(c1, s1, b1, lane + 32 < j, x32, ci1, cn1);
+    if (lane + 32 < j) f1 = cadd(cmul(c1, ci1), cmul(s1, b1));
+    carry = shfl_d2(cn1, j - 33);
   }
   const double den = sqrt(carry.x * carry.x + carry.y * carry.y + hnext * hnext);
   const double2 c = den > 0 ? cscale(cconj(carry), 1.0 / den) : make_double2(1, 0);
@@ -388,30 +418,30 @@ __global__ void __launch_bounds__(AR_T) k_arnoldi(FState s, CT* __restrict__ w, 
 #pragma unroll
     for (int ii = 0; ii < AR_IC; ++ii) a[ii] = CT{0, 0};
     for (long long eb = e0; eb < n; eb += AR_U * es) {
-      CT wv[AR_U];
+      // every load of the round first (predicated), then the arithmetic
+      CT wv[AR_U], vv[AR_IC][AR_U];
 #pragma unroll
       for (int u = 0; u < AR_U; ++u) wv[u] = eb + u * es < n ? w[eb + u * es] : CT{0, 0};
 #pragma unroll
-      for (int ii = 0; ii < AR_IC; ++ii) {
-        if (ii < ni) {
-          const CT* Vi = V + (i0 + ii) * vstride;
-          CT vv[AR_U];
+      for (int ii = 0; ii < AR_IC; ++ii)
 #pragma unroll
-          for (int u = 0; u < AR_U; ++u) vv[u] = eb + u * es < n ? Vi[eb + u * es] : CT{0, 0};
+        for (int u = 0; u < AR_U; ++u)
+          vv[ii][u] = (ii < ni && eb + u * es < n) ? V[(i0 + ii) * vstride + eb + u * es] : CT{0, 0};
 #pragma unroll
-          for (int u = 0; u < AR_U; ++u) cfmac(a[ii], vv[u], wv[u]);
-        }
-      }
+      for (int ii = 0; ii < AR_IC; ++ii)
+#pragma unroll
+        for (int u = 0; u < AR_U; ++u) cfmac(a[ii], vv[ii][u], wv[u]);
     }
+    // warp sums in the vectors' own precision (FP64 arithmetic is scarce on this GPU), then FP64
 #pragma unroll
     for (int ii = 0; ii < AR_IC; ++ii) {
       if (ii < ni) {
-        double2 v = to_d(a[ii]);
+        CT v = a[ii];
         for (int o = 16; o >= nr; o >>= 1) {
           v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
           v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
         }
-        if (lane < nr) red[ii][warp][lane] = v;
+        if (lane < nr) red[ii][warp][lane] = to_d(v);
       }
     }
     __syncthreads();
@@ -481,9 +511,8 @@ __global__ void __launch_bounds__(AR_T) k_arnoldi(FState s, CT* __restrict__ w, 
         acc += v[u].x * v[u].x + v[u].y * v[u].y;
       }
   }
-  double v2 = (double)acc;
-  for (int o = 16; o >= nr; o >>= 1) v2 += __shfl_xor_sync(0xffffffffu, v2, o);
-  if (lane < nr) red[0][warp][lane] = make_double2(v2, 0);
+  for (int o = 16; o >= nr; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane < nr) red[0][warp][lane] = make_double2((double)acc, 0);
   __syncthreads();
   if (threadIdx.x < nr) {
     double sum = 0;
