@@ -590,29 +590,46 @@ __global__ void __launch_bounds__(ST_T) k_xupdate(FState s, CT* __restrict__ x, 
   const int km = kmax;
   const long long n = s.rows * s.nrhs;
   if (km > 0) {
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
-         e += (long long)gridDim.x * blockDim.x) {
-      const int r = (int)(e % s.nrhs);
-      CT v = x[e];
+    // four elements per thread and four basis vectors per round of loads
+    const long long es = (long long)gridDim.x * blockDim.x;
+    for (long long eb = blockIdx.x * (long long)blockDim.x + threadIdx.x; eb < n; eb += 4 * es) {
+      CT v[4];
+      int rr[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        v[u] = eb + u * es < n ? x[eb + u * es] : CT{0, 0};
+        rr[u] = (int)((eb + u * es) % s.nrhs);
+      }
       int i = 0;
-      for (; i + 4 <= km; i += 4) {  // four basis vectors per round of loads
-        CT q[4];
+      for (; i + 4 <= km; i += 4) {
+        CT q[4][4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) q[k] = V[(i + k) * vstride + e];
+        for (int k = 0; k < 4; ++k)
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const CT c = yc[i + k][r];
-          v.x += c.x * q[k].x - c.y * q[k].y;
-          v.y += c.x * q[k].y + c.y * q[k].x;
-        }
+          for (int u = 0; u < 4; ++u) q[k][u] = eb + u * es < n ? V[(i + k) * vstride + eb + u * es] : CT{0, 0};
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const CT c = yc[i + k][rr[u]];
+            v[u].x += c.x * q[k][u].x - c.y * q[k][u].y;
+            v[u].y += c.x * q[k][u].y + c.y * q[k][u].x;
+          }
       }
       for (; i < km; ++i) {
-        const CT q = V[i * vstride + e];
-        const CT c = yc[i][r];
-        v.x += c.x * q.x - c.y * q.y;
-        v.y += c.x * q.y + c.y * q.x;
+        CT q[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) q[u] = eb + u * es < n ? V[i * vstride + eb + u * es] : CT{0, 0};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const CT c = yc[i][rr[u]];
+          v[u].x += c.x * q[u].x - c.y * q[u].y;
+          v[u].y += c.x * q[u].y + c.y * q[u].x;
+        }
       }
-      x[e] = v;
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (eb + u * es < n) x[eb + u * es] = v[u];
     }
   }
   if (!last_block(s.counter, gridDim.x)) return;
@@ -625,19 +642,30 @@ template <typename CT>
 __global__ void __launch_bounds__(ST_T) k_residual(FState s, CT* __restrict__ w, const CT* __restrict__ b, int first,
                                                    CT* __restrict__ xzero) {
   if (*s.done) return;
-  if (s.nrhs > 1 && 32 % s.nrhs == 0) {  // flat, coalesced (see k_dots_flat)
-    const long long n = s.rows * s.nrhs;
+  if (32 % s.nrhs == 0) {  // flat, coalesced (see k_dots_flat; one column included)
+    const long long n = s.rows * s.nrhs, es = (long long)s.nblk * ST_T;
     decltype(CT{}.x) acc = 0;
-    for (long long e = blockIdx.x * (long long)ST_T + threadIdx.x; e < n; e += (long long)s.nblk * ST_T) {
-      CT v = b[e];
-      if (!first) {
-        const CT q = w[e];
-        v.x -= q.x;
-        v.y -= q.y;
+    for (long long eb = blockIdx.x * (long long)ST_T + threadIdx.x; eb < n; eb += 4 * es) {  // 4 elements per round
+      CT v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const long long e = eb + u * es;
+        v[u] = e < n ? b[e] : CT{0, 0};
+        if (!first && e < n) {
+          const CT q = w[e];
+          v[u].x -= q.x;
+          v[u].y -= q.y;
+        }
       }
-      w[e] = v;
-      if (xzero) xzero[e] = CT{0, 0};
-      acc += v.x * v.x + v.y * v.y;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const long long e = eb + u * es;
+        if (e < n) {
+          w[e] = v[u];
+          if (xzero) xzero[e] = CT{0, 0};
+          acc += v[u].x * v[u].x + v[u].y * v[u].y;
+        }
+      }
     }
     cta_col_sum_store(make_double2((double)acc, 0.0), s.nrhs, s.part + (long long)blockIdx.x * s.nrhs);
   } else {
