@@ -163,7 +163,8 @@ __device__ void arnoldi_step_warp(FState& s, int r, int j, double n2, int* any) 
   double2* sn = s.sn + (long long)r * s.m;
   double2* gv = s.gv + (long long)r * (s.m + 1);
   const int act = __ldcg(s.active + r);
-  const double bn = __ldcg(s.bnorm + r);
+  const double rel_j = __ldcg(s.relres + r);  // |g_j| / |b|
+  const int napp = __ldcg(s.applies + r);
   const double2 gj = ld_cg(gv + j);
   const double2 col0 = lane <= j ? ld_cg(Hc + lane * s.m + j) : z;
   const double2 col1 = lane + 32 <= j ? ld_cg(Hc + (lane + 32) * s.m + j) : z;
@@ -191,9 +192,11 @@ __device__ void arnoldi_step_warp(FState& s, int r, int j, double n2, int* any) 
     if (lane + 32 < j) f1 = cadd(cmul(c1, ci1), cmul(s1, b1));
     carry = shfl_d2(cn1, j - 33);
   }
-  const double den = sqrt(carry.x * carry.x + carry.y * carry.y + hnext * hnext);
-  const double2 c = den > 0 ? cscale(cconj(carry), 1.0 / den) : make_double2(1, 0);
-  const double2 sv = den > 0 ? make_double2(hnext / den, 0) : z;
+  const double den2 = carry.x * carry.x + carry.y * carry.y + n2;
+  const double inv_den = den2 > 0 ? 1.0 / sqrt(den2) : 0.0;
+  const double den = den2 * inv_den;
+  const double2 c = den2 > 0 ? cscale(cconj(carry), inv_den) : make_double2(1, 0);
+  const double2 sv = make_double2(hnext * inv_den, 0);
   if (lane < j) Hc[lane * s.m + j] = f0;
   if (lane + 32 < j) Hc[(lane + 32) * s.m + j] = f1;
   if (lane == 0) {
@@ -204,10 +207,10 @@ __device__ void arnoldi_step_warp(FState& s, int r, int j, double n2, int* any) 
     const double2 g1 = cscale(cmul(cconj(sv), gj), -1.0);
     gv[j + 1] = g1;
     gv[j] = cmul(c, gj);
-    const double rel = sqrt(g1.x * g1.x + g1.y * g1.y) / bn;
+    const double rel = rel_j * sv.x;  // |g_{j+1}| = |s_j| |g_j|
     s.relres[r] = rel;
     s.kcnt[r] = j + 1;
-    s.applies[r] += 1;
+    s.applies[r] = napp + 1;
     if (rel <= s.tol || hnext == 0) {
       s.active[r] = 0;
       s.invh[r] = 0;
