@@ -225,6 +225,15 @@ amg_status amg_batch_autotune(const amg_handle *hs, int n, const void *const *d_
  */
 amg_status amg_batch_test_hook(amg_handle h0, int extra_need);
 
+/*
+ * amg_solve_test_hook -- test hook for the bounded grid barriers of the coarse solve's fused Arnoldi
+ * step (1, 2, 4, 8 or 16 right-hand sides): the next solves on h expect extra_arrivals more CTAs at
+ * each barrier than exist, so every CTA's wait runs out after its limit (about one second), the
+ * step ends early and amg_sync_status reports AMG_ERR_TIMEOUT.  extra_arrivals = 0 restores normal
+ * operation.  AMG_ERR_INVALID_ARG for a null handle or a negative count.
+ */
+amg_status amg_solve_test_hook(amg_handle h, int extra_arrivals);
+
 /* R as [Nblock][2][ntv][6 Vb] complex double (row j of R_i^h = v_j^dagger on A_i^h), device or host out. */
 amg_status amg_export_R(amg_handle h, void *out);
 /* D_c as [Vc][9][2 ntv][2 ntv] complex double, FP64 as assembled; directions 0,+x,-x,+y,-y,+z,-z,+t,-t. */

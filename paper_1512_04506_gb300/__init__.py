@@ -75,6 +75,7 @@ _proto = {
     "amg_batch_autotune": [ctypes.POINTER(_vp), _i, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                            ctypes.POINTER(_i), _vp, ctypes.POINTER(_d)],
     "amg_batch_test_hook": [_vp, _i],
+    "amg_solve_test_hook": [_vp, _i],
     "amg_export_R": [_vp, _vp],
     "amg_export_Dc": [_vp, _vp],
     "amg_export_clover": [_vp, _vp],
@@ -265,6 +266,10 @@ def amg_batch_autotune(hs, ys, xs, nrhs, stream=None):
 
 def amg_batch_test_hook(h0, extra_need):
     return _check(lib.amg_batch_test_hook(h0, extra_need), "amg_batch_test_hook")
+
+
+def amg_solve_test_hook(h, extra_arrivals):
+    return _check(lib.amg_solve_test_hook(h, extra_arrivals), "amg_solve_test_hook")
 
 
 def amg_export_R(h, out):

@@ -107,6 +107,7 @@ struct SolveWork {
   int* hflag = nullptr;     // mapped pinned word: ticket of the last solve found converged
   int* hdone_dev = nullptr;  // its device address
   int ticket = 0;
+  unsigned test_extra_arrivals = 0;  // test hook: arrivals the Arnoldi step's grid barrier waits for in vain
   cudaEvent_t ev[kRing] = {};
 };
 

@@ -34,6 +34,7 @@ struct FState {
   unsigned* err;     // device error word
   volatile int* hdone;  // mapped host word: set to `ticket` when every right-hand side has converged
   int ticket;
+  unsigned bar_extra;  // 0, or the test hook's arrivals that never come
 };
 
 // Every right-hand side has converged: later kernels of this solve return at once, and the host
@@ -373,8 +374,9 @@ constexpr long long kBarCycles = 2000000000LL;  // about one second at GB300 clo
 
 // Bounded grid barrier (every CTA resident: cooperative launch).  Thread 0 reads the generation
 // before it arrives; the last arrival resets the count and advances the generation.  A wait that
-// runs out sets AMG_EBIT_TIMEOUT and returns false.
-__device__ bool grid_sync(unsigned* bar, unsigned* err) {
+// runs out sets AMG_EBIT_TIMEOUT and returns false.  `extra` > 0 (a test hook) expects arrivals
+// that never come, so that every wait runs out.
+__device__ bool grid_sync(unsigned* bar, unsigned* err, unsigned extra) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -382,7 +384,7 @@ __device__ bool grid_sync(unsigned* bar, unsigned* err) {
     const unsigned g = *gen;
     int good = 1;
     __threadfence();
-    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+    if (atomicAdd(bar, 1u) == gridDim.x - 1 + extra) {
       atomicExch(bar, 0u);
       __threadfence();
       atomicAdd(bar + 1, 1u);
@@ -456,7 +458,7 @@ __global__ void __launch_bounds__(AR_T) k_arnoldi(FState s, CT* __restrict__ w, 
     }
     __syncthreads();
   }
-  if (!grid_sync(s.bar, s.err)) return;
+  if (!grid_sync(s.bar, s.err, s.bar_extra)) return;
   // 2. column j of H: one warp per (i, r) sums the G partials
   const int P = (j + 1) * nr;
   for (int t = blockIdx.x * AR_W + warp; t < P; t += G * AR_W) {
@@ -464,7 +466,7 @@ __global__ void __launch_bounds__(AR_T) k_arnoldi(FState s, CT* __restrict__ w, 
     const int i = t / nr, r = t % nr;
     if (lane == 0) s.H[((long long)r * (s.m + 1) + i) * s.m + j] = __ldcg(s.active + r) ? sum : make_double2(0, 0);
   }
-  if (!grid_sync(s.bar, s.err)) return;
+  if (!grid_sync(s.bar, s.err, s.bar_extra)) return;
   // 3. w -= sum_i H[r][i][j] V_i and the partial sums of |w|^2 (into row 0 of the partials,
   // whose reads in 2. are complete)
   for (int t = threadIdx.x; t < P; t += AR_T) {
@@ -795,6 +797,7 @@ amg_status solve_impl(amg_coarse* h, long long rows, amg_apply_fn op, const CT* 
   s.bar = (unsigned*)(fl + 3 * nrhs + 5);
   s.err = h->err;
   s.hdone = poll ? sw.hdone_dev : nullptr;
+  s.bar_extra = sw.test_extra_arrivals;
   if (poll) sw.ticket = sw.ticket >= (1 << 30) ? 1 : sw.ticket + 1;  // never 0, the word's initial value
   s.ticket = poll ? sw.ticket : 0;
   const unsigned egrid = 4 * 152;
@@ -939,4 +942,10 @@ amg_status amg_internal_solve(amg_coarse* h, const void* b, void* x, int nrhs, d
   if (nrhs > MAXR || restart < 1 || restart > AMG_MAX_NTV || max_applies < 1) return AMG_ERR_INVALID_ARG;
   AMG_TRY_INTERNAL(ensure_solve_work(h, nrhs, restart, s));
   return amg_internal_solve_ws(h, b, x, nrhs, tol, restart, max_applies, s, info, h->sw.buf, true);
+}
+
+extern "C" amg_status amg_solve_test_hook(amg_handle h, int extra_arrivals) {
+  if (!h || extra_arrivals < 0) return AMG_ERR_INVALID_ARG;
+  h->sw.test_extra_arrivals = (unsigned)extra_arrivals;
+  return AMG_OK;
 }

@@ -199,6 +199,31 @@ def test_coarse_solve_fp64_matches_oracle_fgmres(amg, tiny64):
     assert true <= 1.05e-9
 
 
+def test_arnoldi_bounded_barrier_reports_timeout(amg, tiny64):
+    """The fused Arnoldi step's grid barrier expects one more arrival than there are CTAs: every
+    CTA's wait runs out (about one second), the step ends early, the status says so once, and the
+    handle and the context stay usable (the next solve gives the oracle's iterate)."""
+    c = tiny64
+    b = c.coarse_vec(1, 23)
+    x = torch.empty((c.Vc, 2, c.ntv, 1), dtype=c.cdt, device="cuda")
+    amg.amg_solve_test_hook(c.h, 1)
+    try:
+        amg.amg_coarse_solve(c.h, c.dev(b), x, 1, tol=0.0, restart=4, max_applies=1, stream=c.stream, info=False)
+        assert amg.amg_sync_status(c.h) == amg.AMG_ERR_TIMEOUT
+    finally:
+        amg.amg_solve_test_hook(c.h, 0)
+    info = amg.amg_coarse_solve(c.h, c.dev(b), x, 1, tol=1e-12, restart=6, max_applies=4, stream=c.stream)
+    ref, hist, n = krylov.fgmres(lambda v: coarse.coarse_apply(c.Dc, v, c.Lc), b, tol=1e-12, restart=6,
+                                 max_applies=4)
+    assert info[0][0] == n == 4
+    assert H.rel(x.cpu().numpy(), ref) < 1e-10
+    assert amg.amg_sync_status(c.h) == amg.AMG_OK
+    a = torch.ones(1000, device="cuda")
+    assert float(a.sum()) == 1000.0
+    with pytest.raises(amg.AmgError):
+        amg.amg_solve_test_hook(c.h, -1)
+
+
 @pytest.mark.parametrize("nrhs", [1, 3])
 def test_coarse_solve_fp32_reaches_tolerance(amg, ragged32, nrhs):
     c = ragged32
