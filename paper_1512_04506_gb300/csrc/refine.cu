@@ -14,45 +14,47 @@
 namespace {
 
 // per right-hand side |v_r|^2 of a coarse FP32 vector [rows][nrhs]: a grid-stride pass over the
-// rows with coalesced reads (a thread keeps one partial sum per column it meets: element e belongs
-// to column e % nrhs), CTA reductions per column, one double atomicAdd per CTA and column into out
-// (zeroed by the caller).
+// rows with coalesced reads, four elements' loads issued together.  When the stride is a multiple
+// of nrhs (nrhs = 1, 2, 4, 8, 16) a thread only meets column e % nrhs: its partial sum stays in
+// FP32 (a few dozen terms) and is summed over the lanes of equal column in FP32, over the warps
+// and CTAs in FP64 (one double atomicAdd per CTA and column into out, zeroed by the caller).
+// Other column counts keep one FP64 partial per column.
 __global__ void __launch_bounds__(256) k_colnorm2(const float2* __restrict__ v, long long rows, int nrhs,
                                                   double* __restrict__ out) {
   __shared__ double red[16][8];
-  double acc[16];
-#pragma unroll
-  for (int r = 0; r < 16; ++r) acc[r] = 0.0;
   const long long n = rows * nrhs;
-  const long long stride = (long long)gridDim.x * blockDim.x;  // a multiple of 16, so e % nrhs is fixed per thread
-  long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const int col = (int)(e % nrhs);
-  double s = 0.0;
-  if (stride % nrhs == 0) {
-    for (; e < n; e += stride) {
-      const float2 a = v[e];
-      s += (double)a.x * a.x + (double)a.y * a.y;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long e0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (stride % nrhs == 0 && 32 % nrhs == 0) {
+    float s = 0.f;
+    for (long long eb = e0; eb < n; eb += 4 * stride) {
+      float2 a[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) a[u] = eb + u * stride < n ? v[eb + u * stride] : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) s += a[u].x * a[u].x + a[u].y * a[u].y;
     }
+    for (int o = 16; o >= nrhs; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane < nrhs) red[lane][warp] = (double)s;
   } else {
-    for (; e < n; e += stride) {
+    double acc[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) acc[r] = 0.0;
+    for (long long e = e0; e < n; e += stride) {
       const float2 a = v[e];
       const double q = (double)a.x * a.x + (double)a.y * a.y;
 #pragma unroll
       for (int r = 0; r < 16; ++r)
         if (r == (int)(e % nrhs)) acc[r] += q;
     }
-  }
-  if (stride % nrhs == 0) {
 #pragma unroll
-    for (int r = 0; r < 16; ++r) acc[r] = r == col ? s : 0.0;
-  }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int r = 0; r < 16; ++r) {
-    if (r >= nrhs) break;
-    double t = acc[r];
-    for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (lane == 0) red[r][warp] = t;
+    for (int r = 0; r < 16; ++r) {
+      if (r >= nrhs) break;
+      double t = acc[r];
+      for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0) red[r][warp] = t;
+    }
   }
   __syncthreads();
   if (threadIdx.x < nrhs) {
@@ -62,18 +64,39 @@ __global__ void __launch_bounds__(256) k_colnorm2(const float2* __restrict__ v, 
   }
 }
 
-// x += e; r = b - w (w = D_c x from the accurate operator), columns with keep[r] == 0 zeroed in r
+// x += e; r = b - w (w = D_c x from the accurate operator), columns with keep[r] == 0 zeroed in r;
+// four elements' loads per round
 __global__ void k_axpy(float2* __restrict__ x, const float2* __restrict__ e, long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const float2 a = x[i], b = e[i];
-    x[i] = make_float2(a.x + b.x, a.y + b.y);
+  const long long es = (long long)gridDim.x * blockDim.x;
+  for (long long ib = blockIdx.x * (long long)blockDim.x + threadIdx.x; ib < n; ib += 4 * es) {
+    float2 a[4], b[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const long long i = ib + u * es;
+      a[u] = i < n ? x[i] : make_float2(0.f, 0.f);
+      b[u] = i < n ? e[i] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (ib + u * es < n) x[ib + u * es] = make_float2(a[u].x + b[u].x, a[u].y + b[u].y);
   }
 }
 __global__ void k_resid(float2* __restrict__ r, const float2* __restrict__ b, const float2* __restrict__ w,
                         const int* __restrict__ keep, long long n, int nrhs) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const float2 u = b[i], v = w[i];
-    r[i] = keep[i % nrhs] ? make_float2(u.x - v.x, u.y - v.y) : make_float2(0.f, 0.f);
+  const long long es = (long long)gridDim.x * blockDim.x;
+  for (long long ib = blockIdx.x * (long long)blockDim.x + threadIdx.x; ib < n; ib += 4 * es) {
+    float2 u[4], v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const long long i = ib + k * es;
+      u[k] = i < n ? b[i] : make_float2(0.f, 0.f);
+      v[k] = i < n ? w[i] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const long long i = ib + k * es;
+      if (i < n) r[i] = keep[i % nrhs] ? make_float2(u[k].x - v[k].x, u[k].y - v[k].y) : make_float2(0.f, 0.f);
+    }
   }
 }
 
