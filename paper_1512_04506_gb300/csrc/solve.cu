@@ -369,7 +369,13 @@ constexpr int AR_T = 512;
 constexpr int AR_W = AR_T / 32;
 template <typename CT>
 constexpr int ar_ic() { return sizeof(CT) == 8 ? 8 : 4; }  // dot products reduced per CTA round
-constexpr int AR_U = 4;   // elements per thread whose loads are issued together (long vectors)
+// Round shapes of k_arnoldi: IC basis vectors per dot-product round, U elements per thread whose
+// loads are issued together, KQ basis vectors per update round.  Vectors of more than
+// AR_LONG elements (16 columns at 32^3 x 64 and up) take fewer basis vectors and more elements
+// per round, for more loads in flight per thread at the same register count.
+constexpr long long AR_LONG = 1LL << 20;
+template <typename CT>
+constexpr int ar_ulong() { return sizeof(CT) == 8 ? 16 : 8; }
 constexpr long long kBarCycles = 2000000000LL;  // about one second at GB300 clocks
 
 // Bounded grid barrier (every CTA resident: cooperative launch).  Thread 0 reads the generation
@@ -405,12 +411,11 @@ __device__ bool grid_sync(unsigned* bar, unsigned* err, unsigned extra) {
   return ok != 0;
 }
 
-template <typename CT>
+template <typename CT, int AR_IC, int AR_U, int KQ>
 __global__ void __launch_bounds__(AR_T) k_arnoldi(FState s, CT* __restrict__ w, const CT* __restrict__ V,
                                                   long long vstride, int j) {
   using RT = decltype(CT{}.x);
   if (*s.done) return;
-  constexpr int AR_IC = ar_ic<CT>();
   __shared__ double2 red[AR_IC][AR_W][MAXR];
   __shared__ CT hc[AMG_MAX_NTV + 1][MAXR];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nr = s.nrhs, G = gridDim.x;
@@ -480,16 +485,16 @@ __global__ void __launch_bounds__(AR_T) k_arnoldi(FState s, CT* __restrict__ w, 
     CT v[AR_U];
 #pragma unroll
     for (int u = 0; u < AR_U; ++u) v[u] = eb + u * es < n ? w[eb + u * es] : CT{0, 0};
-    // four basis vectors per round of loads
+    // KQ basis vectors per round of loads
     int i = 0;
-    for (; i + 4 <= j + 1; i += 4) {
-      CT q[4][AR_U];
+    for (; i + KQ <= j + 1; i += KQ) {
+      CT q[KQ][AR_U];
 #pragma unroll
-      for (int k = 0; k < 4; ++k)
+      for (int k = 0; k < KQ; ++k)
 #pragma unroll
         for (int u = 0; u < AR_U; ++u) q[k][u] = eb + u * es < n ? V[(i + k) * vstride + eb + u * es] : CT{0, 0};
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
+      for (int k = 0; k < KQ; ++k) {
         const CT c = hc[i + k][col];
 #pragma unroll
         for (int u = 0; u < AR_U; ++u) {
@@ -745,7 +750,10 @@ int arnoldi_grid() {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_arnoldi<CT>, AR_T, 0);
+    int per_long = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_arnoldi<CT, ar_ic<CT>(), 4, 4>, AR_T, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_long, k_arnoldi<CT, 2, ar_ulong<CT>(), 1>, AR_T, 0);
+    per = std::min(per, per_long);
     g = (coop && per > 0) ? std::min(sms, NBLK) : 0;
   }
   return g;
@@ -839,7 +847,9 @@ amg_status solve_impl(amg_coarse* h, long long rows, amg_apply_fn op, const CT* 
         const CT* Vr = V;
         int jj = j;
         void* args[] = {&s, &nxt, &Vr, (void*)&vstride, &jj};
-        AMG_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_arnoldi<CT>, dim3(ar_grid), dim3(AR_T), args, 0, st));
+        const void* kern = rows * nrhs > AR_LONG ? (const void*)k_arnoldi<CT, 2, ar_ulong<CT>(), 1>
+                                                 : (const void*)k_arnoldi<CT, ar_ic<CT>(), 4, 4>;
+        AMG_CUDA_TRY(cudaLaunchCooperativeKernel(kern, dim3(ar_grid), dim3(AR_T), args, 0, st));
         h->launches += 1;
       } else {
         if (flat) {
