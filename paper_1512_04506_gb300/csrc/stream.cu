@@ -286,9 +286,10 @@ struct MrhsArgs {
   int ns, G;
 };
 
-template <typename LT, int NR>
+template <typename LT, int NR, int LPR>
 __global__ void __launch_bounds__(288) apply_mrhs_kernel(const MrhsArgs<LT, NR> a) {
   constexpr int CPL = Vec16<LT>::CPL;
+  constexpr int ROWS = CPL * LPR;  // rows per thread: LPR 16-byte loads of a block column
   constexpr int RW = NR < 4 ? NR : 4;  // right-hand sides per thread
   constexpr int QG = NR / RW;
   if (a.skip && *a.skip) return;
@@ -351,7 +352,7 @@ __global__ void __launch_bounds__(288) apply_mrhs_kernel(const MrhsArgs<LT, NR> 
     return;
   }
   const int t = threadIdx.x - 32, nct = blockDim.x - 32;
-  const int Gc = nc / CPL, per = Gc * QG;
+  const int Gc = nc / ROWS, per = Gc * QG;
   const int cg = t / per, rem = t % per, rg = rem % Gc, qg = rem / Gc;
   const bool active = cg < a.G;
   float sc[RW];
@@ -360,9 +361,9 @@ __global__ void __launch_bounds__(288) apply_mrhs_kernel(const MrhsArgs<LT, NR> 
   int s = 0;
   unsigned ph = 0;
   for (long long i = blockIdx.x; i < Vc; i += gridDim.x) {
-    float2 acc[CPL][RW];
+    float2 acc[ROWS][RW];
 #pragma unroll
-    for (int q = 0; q < CPL; ++q)
+    for (int q = 0; q < ROWS; ++q)
 #pragma unroll
       for (int u = 0; u < RW; ++u) acc[q][u] = make_float2(0.f, 0.f);
     for (int d = 0; d < 9; ++d) {
@@ -374,15 +375,21 @@ __global__ void __launch_bounds__(288) apply_mrhs_kernel(const MrhsArgs<LT, NR> 
       const unsigned char* st = stages + (size_t)s * chunk;
       const float2* Xs = reinterpret_cast<const float2*>(st + dbytes);
       if (ok && active) {
-        const LT* blk = reinterpret_cast<const LT*>(st) + rg * CPL;
+        const LT* blk = reinterpret_cast<const LT*>(st) + rg * ROWS;
         const float f = a.dscale ? a.dscale[i * 9 + d] : 1.f;
         float fs[RW];
 #pragma unroll
         for (int u = 0; u < RW; ++u) fs[u] = f * sc[u];
 #pragma unroll 2
         for (int b = cg; b < nc; b += a.G) {
-          float2 v[CPL];
-          Vec16<LT>::ld(blk + (size_t)b * nc, v);
+          float2 v[ROWS];
+#pragma unroll
+          for (int l = 0; l < LPR; ++l) {
+            float2 vl[CPL];
+            Vec16<LT>::ld(blk + (size_t)b * nc + l * CPL, vl);
+#pragma unroll
+            for (int q = 0; q < CPL; ++q) v[l * CPL + q] = vl[q];
+          }
           float2 xv[RW];
           if constexpr (RW == 4) {
             const float4 x01 = *reinterpret_cast<const float4*>(Xs + b * NR + 4 * qg);
@@ -398,7 +405,7 @@ __global__ void __launch_bounds__(288) apply_mrhs_kernel(const MrhsArgs<LT, NR> 
 #pragma unroll
           for (int u = 0; u < RW; ++u) xv[u] = make_float2(xv[u].x * fs[u], xv[u].y * fs[u]);
 #pragma unroll
-          for (int q = 0; q < CPL; ++q)
+          for (int q = 0; q < ROWS; ++q)
 #pragma unroll
             for (int u = 0; u < RW; ++u) cfma(acc[q][u], v[q], xv[u]);
         }
@@ -418,9 +425,9 @@ __global__ void __launch_bounds__(288) apply_mrhs_kernel(const MrhsArgs<LT, NR> 
     }
     if (active)
 #pragma unroll
-      for (int q = 0; q < CPL; ++q)
+      for (int q = 0; q < ROWS; ++q)
 #pragma unroll
-        for (int u = 0; u < RW; ++u) red[((size_t)cg * NR + RW * qg + u) * (nc + 1) + rg * CPL + q] = acc[q][u];
+        for (int u = 0; u < RW; ++u) red[((size_t)cg * NR + RW * qg + u) * (nc + 1) + rg * ROWS + q] = acc[q][u];
     consumer_sync(nct);
     for (int e = t; e < nc * NR; e += nct) {
       const int row = e / NR, col = e % NR;
@@ -1012,13 +1019,13 @@ amg_status launch_apply_tma(amg_coarse* h, const LT* D, const float* dscale, con
   return AMG_OK;
 }
 
-template <typename LT, int NR>
-amg_status launch_apply_mrhs(amg_coarse* h, const LT* D, const float* dscale, const void* x, void* y, cudaStream_t st,
-                             const int* skip, const double* xscale, void* vout) {
-  constexpr int CPL = Vec16<LT>::CPL;
+template <typename LT, int NR, int LPR>
+amg_status launch_apply_mrhs_rows(amg_coarse* h, const LT* D, const float* dscale, const void* x, void* y,
+                                  cudaStream_t st, const int* skip, const double* xscale, void* vout) {
+  constexpr int ROWS = Vec16<LT>::CPL * LPR;
   const int nc = h->g.nc;
-  if (nc % CPL) return AMG_ERR_UNSUPPORTED;
-  const int per = (nc / CPL) * (NR < 4 ? 1 : NR / 4);
+  if (nc % ROWS) return AMG_ERR_UNSUPPORTED;
+  const int per = (nc / ROWS) * (NR < 4 ? 1 : NR / 4);
   int G = 256 / per;
   if (G < 1) return AMG_ERR_UNSUPPORTED;
   if (G > nc) G = nc;
@@ -1029,13 +1036,24 @@ amg_status launch_apply_mrhs(amg_coarse* h, const LT* D, const float* dscale, co
   const size_t smem = kPipeBytes + ns * chunk + (size_t)G * NR * (nc + 1) * sizeof(float2);
   if (smem > 227 * 1024) return AMG_ERR_UNSUPPORTED;
   int grid = 0;
-  amg_status s = grid_for(apply_mrhs_kernel<LT, NR>, threads, smem, h->g.Vc, &grid);
+  amg_status s = grid_for(apply_mrhs_kernel<LT, NR, LPR>, threads, smem, h->g.Vc, &grid);
   if (s != AMG_OK) return s;
   MrhsArgs<LT, NR> a{D, dscale, h->nbr, (const float2*)x, (float2*)y, (float2*)vout, xscale, skip, h->err, h->g, ns, G};
-  apply_mrhs_kernel<LT, NR><<<grid, threads, smem, st>>>(a);
+  apply_mrhs_kernel<LT, NR, LPR><<<grid, threads, smem, st>>>(a);
   AMG_LAUNCH_CHECK();
   h->launches++;
   return AMG_OK;
+}
+
+// FP32 storage with 4 or more columns: four rows per thread (two 16-byte loads of a block column)
+// so that each thread's 16 complex products share 64 bytes of shared-memory loads.
+template <typename LT, int NR>
+amg_status launch_apply_mrhs(amg_coarse* h, const LT* D, const float* dscale, const void* x, void* y, cudaStream_t st,
+                             const int* skip, const double* xscale, void* vout) {
+  if constexpr (std::is_same<LT, float2>::value && NR >= 4) {
+    if (h->g.nc % 4 == 0) return launch_apply_mrhs_rows<LT, NR, 2>(h, D, dscale, x, y, st, skip, xscale, vout);
+  }
+  return launch_apply_mrhs_rows<LT, NR, 1>(h, D, dscale, x, y, st, skip, xscale, vout);
 }
 
 struct EoCall {
