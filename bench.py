@@ -36,10 +36,10 @@ TOL, RESTART, MAX_APPLIES = 0.05, 30, 200
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the 32^4 workload, from
 # the ncu captures of the 24^4 case summarised under profiles/ scaled by the number of blocks /
 # coarse sites (the per-unit work is the same); valid for the kernels as captured.
-TRAFFIC = {"restrict": 2124549284, "prolong": 2124409312, "apply": 485647651}
+TRAFFIC = {"restrict": 2124549284, "prolong": 2124409312, "apply": 483073946}
 # the same for the 48^3 x 96 tensor-core workload (captures of the 24^3 x 48 case, x16; the apply
 # figure is the tensor-core kernel alone, without the FP32 -> BF16 conversion launch)
-TRAFFIC_TC16 = {"restrict": 20641533184, "prolong": 20032036864, "apply": 3793358848}
+TRAFFIC_TC16 = {"restrict": 20641533184, "prolong": 19744555008, "apply": 3677028352}
 METRIC = "coarse-grid correction GB/s & % HBM roofline; batched-mixed vs plain speedup"
 WORKLOAD = "fp32_32^4_b4_ntv20: 32^4 Wilson-clover, 4^4 blocks -> 8^4 coarse, Ntv=20, 1 RHS, " \
            "FP64 setup, FP32 R and D_c; step = R y, FGMRES(30) to 0.05 (<=200 applies), P x_c"
