@@ -363,8 +363,10 @@ __global__ void __launch_bounds__(ST_T) k_update_flat(FState s, CT* __restrict__
 // ---- fused Arnoldi step for nrhs in {1, 2, 4, 8, 16} (flat element loops as above): one
 // cooperative launch, one CTA per SM, does the dots, the Hessenberg column, the update with |w|^2
 // and the Givens step, with two grid barriers in place of a kernel boundary and a last-CTA
-// hand-off.  The vectors of the coarse solve are small (Vc * 2 Ntv rows), so each of these
-// phases is a few memory round trips and the launch and barrier latencies set the time.
+// hand-off.  With one or a few columns the coarse vectors are small (Vc * 2 Ntv rows, about a
+// megabyte), each phase is a few memory round trips and the launch and barrier latencies set the
+// time; with 16 columns they reach hundreds of megabytes and the phases stream, which is what the
+// round shapes below are for.
 constexpr int AR_T = 512;
 constexpr int AR_W = AR_T / 32;
 template <typename CT>
