@@ -54,7 +54,7 @@ def test_fp32_workload_32x4_sampled(amg):
     stream = torch.cuda.current_stream()
     U = sd.links(seed, eps, L)
     tv = sd.test_vectors(seed, ntv, L)
-    p = amg.make_params(L, B, ntv, 1, H.M0, H.CSW, amg.AMG_FP32, amg.AMG_FP32, amg.AMG_FP32)
+    p = amg.make_params(L, B, ntv, 8, H.M0, H.CSW, amg.AMG_FP32, amg.AMG_FP32, amg.AMG_FP32)
     h, _ = amg.amg_setup_coarse(p, U, tv, stream)
     del U, tv
     torch.cuda.empty_cache()
@@ -97,5 +97,18 @@ def test_fp32_workload_32x4_sampled(amg):
             got = x[torch.from_numpy(bs).cuda()].cpu().numpy()[..., 0]
             assert H.rel(got, refx) < 1e-5
         del Rall
+        # FGMRES with 8 columns: coarse vectors of 4096 x 40 x 8 > 2^20 elements take the long
+        # round shape of the fused Arnoldi step (and the split-TF32 apply); every column must give
+        # its single-column solve (short round shape, one-pass FP32 apply) up to FP32 rounding
+        b8 = sd.coarse_vector(seed + 1, ntv, 8, Vc, torch.complex64)
+        x8 = torch.empty_like(b8)
+        info8 = amg.amg_coarse_solve(h, b8, x8, 8, tol=0.0, restart=6, max_applies=8, stream=stream)
+        x1 = torch.empty((Vc, 2, ntv, 1), dtype=torch.complex64, device="cuda")
+        for r in range(8):
+            info1 = amg.amg_coarse_solve(h, b8[..., r:r + 1].contiguous(), x1, 1, tol=0.0, restart=6, max_applies=8,
+                                         stream=stream)
+            assert info8[r][0] == info1[0][0] == 8
+            assert H.rel(x8[..., r].cpu().numpy(), x1[..., 0].cpu().numpy()) < 5e-4
+        assert amg.amg_sync_status(h) == amg.AMG_OK
     finally:
         amg.amg_destroy(h)
