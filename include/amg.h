@@ -117,7 +117,10 @@ amg_status amg_prolong(amg_handle h, const void *d_xc, void *d_x, int nrhs, void
  * applications of D_c have been made; each right-hand side independently.
  * d_b, d_x: coarse vectors with nrhs right-hand sides.  info (host, may be
  * NULL) receives per RHS {applies, final implicit relative residual} as
- * info[2 r], info[2 r + 1]; passing info synchronises the stream.
+ * info[2 r], info[2 r + 1]; passing info synchronises the stream.  To stop
+ * at convergence the host follows the device step by step: after queueing
+ * application j it waits until Arnoldi step j - 1 has completed, so the call
+ * returns shortly after the last step, with the final update of x queued.
  */
 amg_status amg_coarse_solve(amg_handle h, const void *d_b, void *d_x, int nrhs, double tol,
                             int restart, int max_applies, void *stream, double *info);
