@@ -17,7 +17,8 @@ Streams of the counter generator in ``synth.rng``:
 
 Links are U = exp(i eps H) with H = sum_a h_a lambda_a / 2 (traceless
 Hermitian), evaluated here through the eigen-decomposition of H.
-Seeds: 20151204 + workload number (input recipe).
+Seeds: 20151204 + workload number (the offset listed with each workload in
+tests/helpers.py WORKLOADS).
 
 This module holds none of the multigrid method's arithmetic.
 """

@@ -1,7 +1,8 @@
 """Shared test helpers: synthetic inputs in the oracle's array layout.
 
-Workloads (input recipe): each has a fine lattice L (x, y, z,
-t), block B, number of test vectors, link spread eps, mass m0 and c_sw.
+Workloads (WORKLOADS below): each has a fine lattice L (x, y, z, t), block B,
+number of test vectors, link spread eps and a seed offset; the mass m0 and c_sw
+are shared (M0, CSW).
 """
 import numpy as np
 
