@@ -1,8 +1,8 @@
 """Coarse-grid solve of Alg. 2: restarted FGMRES (oracle, complex128).
 
-Alg. 2 solves D_c x_c = y_c "to low precision" (relative residual about
-0.05) by FGMRES; each iteration applies D_c once and then does BLAS-like
-work, mainly Gram-Schmidt.  The reading fixed here: right-preconditioned
+Alg. 2 solves D_c x_c = y_c only roughly (relative residual about 0.05) by
+FGMRES; each iteration applies D_c once, followed by vector work that is
+mostly the Gram-Schmidt orthogonalisation.  The reading fixed here: right-preconditioned
 flexible GMRES with restart length m (Saad, Iterative Methods for Sparse
 Linear Systems, Alg. 9.6), classical Gram-Schmidt in the Arnoldi step (the
 same choice the paper makes for the aggregates), Givens rotations for the
