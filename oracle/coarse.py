@@ -64,11 +64,6 @@ def orthonormalize(tv, B):
     return Q
 
 
-def restriction_blocks(Q):
-    """R_i^h = Q[i, h]^dagger, shape (Vc, 2, N_tv, 6 V_block)."""
-    return np.conj(np.swapaxes(Q, -1, -2))
-
-
 def restrict(Q, y, B):
     """y_c = R y (Eq. R): (y_c)_i^h = R_i^h y|_{A_i^h}."""
     ya = lat.to_aggregates(y, B)

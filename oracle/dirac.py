@@ -203,10 +203,6 @@ def flatten_field(psi):
     return psi.reshape((12 * V,) + psi.shape[6:])
 
 
-def unflatten_field(v, L):
-    return v.reshape((L[3], L[2], L[1], L[0], 4, 3) + v.shape[1:])
-
-
 def gauge_transform(U, G):
     """U_mu(x) -> G(x) U_mu(x) G(x + mu)^dagger."""
     return np.stack([_mm(_mm(G, U[mu]), _dag(lat.shift(G, mu, 1))) for mu in range(4)])
