@@ -198,7 +198,9 @@ amg_status amg_cgc(amg_handle h, const void *d_y, void *d_x, int nrhs, double to
 
 /*
  * amg_batch_cgc -- x_k = P_k D_ck R_k y_k for n lattices (handles hs[k]) in one
- * persistent launch: each lattice's restriction, one D_c application and its
+ * persistent launch [Alg. 2's restriction, coarse operator and prolongation; Sec. 3 runs its
+ * kernels as persistent threads meeting at synchronisation points rather than fork-join]: each
+ * lattice's restriction, one D_c application and its
  * prolongation run as phases separated by per-lattice device barriers with a
  * bounded wait (AMG_ERR_TIMEOUT when a wait runs out).  Each lattice runs in its
  * handle's precision: FP32 R, D_c and vectors (any nrhs), or BF16 R, D_c and fine
@@ -212,7 +214,8 @@ amg_status amg_batch_cgc(const amg_handle *hs, int n, const void *const *d_y, vo
                          const int *nrhs, void *stream);   /* n <= 8 */
 
 /*
- * amg_batch_autotune -- times the fused batch launch for each candidate shape (1, 2, 3 or 4 CTAs
+ * amg_batch_autotune -- (no counterpart in the paper) times the fused batch launch for each
+ * candidate shape (1, 2, 3 or 4 CTAs
  * per SM, capped by occupancy, x 2, 3 or 4 bulk-copy ring stages) on the caller's arguments (same
  * as amg_batch_cgc) and keeps the fastest in hs[0] for later amg_batch_cgc calls.  best_ms (may be
  * NULL) receives its time in milliseconds.  Synchronises the stream.
@@ -237,13 +240,16 @@ amg_status amg_batch_test_hook(amg_handle h0, int extra_need);
  */
 amg_status amg_solve_test_hook(amg_handle h, int extra_arrivals);
 
-/* R as [Nblock][2][ntv][6 Vb] complex double (row j of R_i^h = v_j^dagger on A_i^h), device or host out. */
+/* R as [Nblock][2][ntv][6 Vb] complex double (row j of R_i^h = v_j^dagger on A_i^h, Alg. 5), device or
+ * host out. */
 amg_status amg_export_R(amg_handle h, void *out);
-/* D_c as [Vc][9][2 ntv][2 ntv] complex double, FP64 as assembled; directions 0,+x,-x,+y,-y,+z,-z,+t,-t. */
+/* D_c as [Vc][9][2 ntv][2 ntv] complex double, FP64 as assembled (Eq. cgo, Eq. dagger); directions
+ * 0,+x,-x,+y,-y,+z,-z,+t,-t. */
 amg_status amg_export_Dc(amg_handle h, void *out);
 /* The clover field as [V][2 chirality][6][6] complex double (C^{ll}, C^{rr} of Alg. 7). */
 amg_status amg_export_clover(amg_handle h, void *out);
-/* D_c as stored for the applies, dequantised to [Vc][9][2 ntv][2 ntv] complex double. */
+/* D_c as stored for the applies (Sec. 3's half precision, or FP32 / BF16), dequantised to
+ * [Vc][9][2 ntv][2 ntv] complex double. */
 amg_status amg_export_Dc_stored(amg_handle h, void *out);
 
 /* Per-phase setup times in milliseconds: clover, Gram-Schmidt, assembly, dagger fill+quantise. */
