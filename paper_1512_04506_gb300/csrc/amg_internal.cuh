@@ -98,8 +98,9 @@ __host__ __device__ inline void cfmac(float2& acc, float2 a, float2 b) {
 }
 
 // ---------------------------------------------------------------- handle
-// Workspace of the coarse solve: one device buffer (Krylov basis, partial sums, scalars, flags)
-// plus a ring of pinned flags and events through which the host sees convergence.
+// Workspace of the coarse solve: one device buffer (Krylov basis, partial sums, scalars, flags),
+// a mapped pinned word the device writes when a solve has converged, and a ring of events (one
+// per Arnoldi step) after which the host reads it.
 struct SolveWork {
   static constexpr int kRing = 16;
   void* buf = nullptr;
