@@ -15,6 +15,11 @@ Modules (each function cites the passage of arXiv:1512.04506 it follows):
 * ``krylov``  -- the restarted FGMRES coarse solve of Alg. 2.
 * ``evenodd`` -- the even/odd (Schur complement) reduction of the coarse system
                  that Alg. 2's coarse solve is preconditioned with.
+* ``smoother`` -- the domain-decomposition smoother of Alg. 3 (SAP over two
+                 block colours, exact or minimal-residual block solves).
+* ``mg``      -- the two-level method around the coarse-grid correction: the
+                 V-cycle (Alg. 1), the adaptive setup (Alg. 4) and the outer
+                 FGMRES solve of D u = f (Sec. 1).
 
 All arithmetic is complex128.  Where the paper is silent (gamma basis, sign
 and normalisation of D, the clover term, boundary conditions) the readings
