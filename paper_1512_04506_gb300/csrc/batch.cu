@@ -333,7 +333,9 @@ size_t simt_smem(const Geom& g, int nrhs, int threads) {
   return m > p ? m : p;
 }
 
-bool tc_lattice(const amg_coarse* h, int nrhs) {
+// A lattice runs on the tensor cores when its R, D_c and vectors are all BF16 (prepare checks the
+// column count).
+bool tc_lattice(const amg_coarse* h) {
   return h->p.r_prec == AMG_BF16 && h->p.link_prec == AMG_BF16 && h->p.vec_prec == AMG_BF16;
 }
 
@@ -348,12 +350,12 @@ amg_status prepare(amg_coarse* const* hs, int n, const void* const* y, void* con
   if (n > kMaxLat) return AMG_ERR_UNSUPPORTED;
   BatchWork& bw = hs[0]->bw;
   // items per job: tensor-core restriction / prolongation 2 blocks, apply 8 sites; SIMT 1
-  auto ipj = [&](int k, int p) { return tc_lattice(hs[k], nrhs[k]) ? (p == 1 ? 8 : 2) : 1; };
+  auto ipj = [&](int k, int p) { return tc_lattice(hs[k]) ? (p == 1 ? 8 : 2) : 1; };
   // layout of the work buffer: counters | need | jobs | per lattice coarse scratch
   size_t njobs = 0, coarse_bytes = 0;
   for (int k = 0; k < n; ++k) {
     const amg_coarse* h = hs[k];
-    const bool tc = tc_lattice(h, nrhs[k]);
+    const bool tc = tc_lattice(h);
     if (tc) {
       if (!h->Rtc || !h->Dtc) return AMG_ERR_UNSUPPORTED;
       if (nrhs[k] != 4 && nrhs[k] != 8 && nrhs[k] != 12 && nrhs[k] != 16) return AMG_ERR_UNSUPPORTED;
@@ -378,8 +380,7 @@ amg_status prepare(amg_coarse* const* hs, int n, const void* const* y, void* con
     bw.sig = 0;
   }
   unsigned char* base = (unsigned char*)bw.buf;
-  BatchArgs a;
-  memset(&a, 0, sizeof(a));
+  BatchArgs a{};
   a.nlat = n;
   a.counters = (unsigned*)base;
   a.need = (const int*)(base + 256);
@@ -404,7 +405,7 @@ amg_status prepare(amg_coarse* const* hs, int n, const void* const* y, void* con
     const amg_coarse* h = hs[k];
     LatDesc& L = a.lat[k];
     L.g = h->g;
-    L.tc = tc_lattice(h, nrhs[k]) ? 1 : 0;
+    L.tc = tc_lattice(h) ? 1 : 0;
     L.nrhs = nrhs[k];
     for (int p = 0; p < 3; ++p) L.ipj[p] = ipj(k, p);
     L.nbr = h->nbr;
@@ -452,9 +453,9 @@ amg_status prepare(amg_coarse* const* hs, int n, const void* const* y, void* con
   return AMG_OK;
 }
 
-bool batch_has_tc(amg_coarse* const* hs, int n, const int* nrhs) {
+bool batch_has_tc(amg_coarse* const* hs, int n) {
   for (int k = 0; k < n; ++k)
-    if (tc_lattice(hs[k], nrhs[k])) return true;
+    if (tc_lattice(hs[k])) return true;
   return false;
 }
 
@@ -481,7 +482,7 @@ amg_status launch(const Prepared& pr, int threads, int per_sm, cudaStream_t st, 
 amg_status amg_internal_batch(amg_coarse* const* hs, int n, const void* const* y, void* const* x, const int* nrhs,
                               cudaStream_t s) {
   BatchWork& bw = hs[0]->bw;
-  const bool tc = batch_has_tc(hs, n, nrhs);
+  const bool tc = batch_has_tc(hs, n);
   const int threads = tc ? kBatchThreads : (bw.threads ? bw.threads : 256);
   const int ns = bw.ns ? bw.ns : 3;
   const int per_sm = bw.per_sm ? bw.per_sm : (tc ? 4 : 2);
@@ -499,7 +500,7 @@ extern "C" amg_status amg_batch_autotune(const amg_handle* hs, int n, const void
   cudaStream_t st = (cudaStream_t)stream;
   amg_coarse* const* H = const_cast<amg_coarse* const*>(hs);
   // tensor-core batches: ring stages x CTAs per SM; SIMT-only batches: threads per CTA x CTAs per SM
-  const bool tc = batch_has_tc(H, n, nrhs);
+  const bool tc = batch_has_tc(H, n);
   const int cand_a[3] = {2, 3, 4}, cand_threads[3] = {128, 256, 512};
   const int cand_per_sm[4] = {1, 2, 3, 4};
   float best = 1e30f;
