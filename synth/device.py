@@ -8,8 +8,6 @@ Buffers are torch tensors on the current CUDA device.
 import ctypes
 import os
 
-from .inputs import STREAM_RHS  # noqa: F401  (documented stream layout)
-
 _PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libsynth.so")
 _lib = None
 
