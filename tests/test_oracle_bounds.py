@@ -78,3 +78,22 @@ def test_reduced_precision_bound_holds_and_is_not_vacuous(p, Lc):
     x32 = x.astype(np.complex64).astype(np.complex128)  # the rounded input is the product's input
     bound32 = coarse.reduced_precision_bound(Dc, x32, Lc, 2.0 ** -p + 2.0 ** -24)
     assert err32 <= bound32 + np.linalg.norm(coarse.coarse_apply(Dc, x32 - x, Lc)) / np.linalg.norm(y)
+
+
+@pytest.mark.parametrize("ntv", [2, 4])
+@pytest.mark.parametrize("Lc", [(3, 3, 3, 3), (2, 3, 2, 3)], ids=["no_alias", "alias"])
+def test_accumulation_term_alone_holds_and_is_not_vacuous(ntv, Lc):
+    """Storage exact (D_c and x already FP32 numbers, u_store = 0): the only error left is the FP32
+    arithmetic of the product, so the bound is (K + 2) u_acc || |D||x| || / ||D x|| with the FP32 unit
+    roundoff u_acc = 2^-24, K = 9 * 2 N_tv.  It must hold, and with K = 36 or 72 it must not exceed
+    the measured error by more than a factor 1000 (worst case (K + 2) u against the observed
+    rounding of a few u): a unit roundoff taken 16 times too large (2^-20) fails here."""
+    Dc, x = _random_system(Lc, ntv, 7)
+    D32 = Dc.astype(np.complex64).astype(np.complex128)
+    x32 = x.astype(np.complex64).astype(np.complex128)
+    y = coarse.coarse_apply(D32, x32, Lc)
+    y32 = coarse.coarse_apply(D32.astype(np.complex64), x32.astype(np.complex64), Lc).astype(np.complex128)
+    err = np.linalg.norm(y32 - y) / np.linalg.norm(y)
+    bound = coarse.reduced_precision_bound(D32, x32, Lc, 0.0)
+    assert 0.0 < err <= bound
+    assert bound <= 1000 * err
