@@ -136,8 +136,13 @@ amg_status amg_coarse_solve(amg_handle h, const void *d_b, void *d_x, int nrhs, 
  * with AMG_ERR_INVALID_ARG (amg_last_error() says by how much).  All calls share the array:
  * calls whose kernels overlap on the GPU race and must be serialised by the caller.  The first
  * call on a device looks up the array's device address (with that device current) and should
- * come before any stream capture.  Without info the call does not synchronise; it then
- * launches the whole max_applies budget, kernels after convergence returning at once.
+ * come before any stream capture.  The address is kept for the life of the process: a
+ * cudaDeviceReset (which also invalidates every handle) makes it stale, so a process that resets
+ * a device must not call the library on that device again.  Unlike amg_coarse_solve, this call
+ * never follows the device from the host to stop early, with or without info: it always
+ * launches the whole max_applies budget, and the kernels queued after convergence return at
+ * once (they cost launch latency, no work).  With info it then synchronises the stream and
+ * reports the applications actually made; without info it does not synchronise.
  */
 amg_status amg_coarse_solve_noalloc(amg_handle h, const void *d_b, void *d_x, int nrhs, double tol,
                                     int restart, int max_applies, void *stream, double *info);
@@ -239,6 +244,17 @@ amg_status amg_batch_test_hook(amg_handle h0, int extra_need);
  * operation.  AMG_ERR_INVALID_ARG for a null handle or a negative count.
  */
 amg_status amg_solve_test_hook(amg_handle h, int extra_arrivals);
+
+/*
+ * amg_grid_cap_test_hook -- (no counterpart in the paper) test hook for the persistent grid-stride
+ * kernels (the bulk-copy and tensor-core restrict / apply / prolong, the even/odd passes and, with h
+ * as the first handle, the fused batch): later launches on h use at most max_ctas CTAs, so that a
+ * lattice small enough for a whole-array check sends many sites, blocks or jobs through each CTA's
+ * copy ring, as the full-size workloads do.  The kernels and their results are unchanged; only the
+ * grid is smaller.  max_ctas = 0 restores the occupancy-derived grid (resident CTAs per SM x SMs).
+ * AMG_ERR_INVALID_ARG for a null handle or a negative count.
+ */
+amg_status amg_grid_cap_test_hook(amg_handle h, int max_ctas);
 
 /* R as [Nblock][2][ntv][6 Vb] complex double (row j of R_i^h = v_j^dagger on A_i^h, Alg. 5), device or
  * host out. */

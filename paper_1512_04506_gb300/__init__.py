@@ -76,6 +76,7 @@ _proto = {
                            ctypes.POINTER(_i), _vp, ctypes.POINTER(_d)],
     "amg_batch_test_hook": [_vp, _i],
     "amg_solve_test_hook": [_vp, _i],
+    "amg_grid_cap_test_hook": [_vp, _i],
     "amg_export_R": [_vp, _vp],
     "amg_export_Dc": [_vp, _vp],
     "amg_export_clover": [_vp, _vp],
@@ -270,6 +271,10 @@ def amg_batch_test_hook(h0, extra_need):
 
 def amg_solve_test_hook(h, extra_arrivals):
     return _check(lib.amg_solve_test_hook(h, extra_arrivals), "amg_solve_test_hook")
+
+
+def amg_grid_cap_test_hook(h, max_ctas):
+    return _check(lib.amg_grid_cap_test_hook(h, max_ctas), "amg_grid_cap_test_hook")
 
 
 def amg_export_R(h, out):

@@ -153,7 +153,16 @@ struct amg_coarse {
   void* yc_tmp = nullptr;
   size_t tmp_bytes = 0;
   unsigned long long launches = 0;  // kernels launched through this handle (host-side count)
+  int grid_cap = 0;           // test hook: most CTAs of a grid-stride launch (0: occupancy x SMs)
 };
+
+// Grid of a grid-stride launch over `items` work items with `resident` CTAs resident at once: the
+// smaller of the two, lowered to the handle's test cap when one is set.
+inline int capped_grid(const amg_coarse* h, long long items, long long resident) {
+  long long g = items < resident ? items : resident;
+  if (h->grid_cap > 0 && g > h->grid_cap) g = h->grid_cap;
+  return (int)g;
+}
 
 // ---------------------------------------------------------------- shared host helpers
 // Records the failing CUDA call of the calling thread (read back by amg_last_error()).
@@ -186,6 +195,10 @@ void amg_note_error(const char* fmt, ...);
   } while (0)
 
 inline bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// Streaming multiprocessors of the current device (queried once per device, api.cu); grids of
+// the grid-stride kernels are multiples of it.
+int amg_sm_count();
 
 inline size_t vec_elem_bytes(amg_prec p) {
   return p == AMG_FP64 ? 16 : (p == AMG_FP32 ? 8 : 4);

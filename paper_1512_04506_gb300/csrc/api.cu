@@ -21,6 +21,19 @@ void amg_note_cuda_error(const char* file, int line, cudaError_t e) {
            cudaGetErrorString(e), cudaGetErrorName(e));
 }
 
+int amg_sm_count() {
+  static int cache[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) dev = 0;
+  if (dev >= 64) dev = 63;
+  if (!cache[dev]) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+    cache[dev] = n;
+  }
+  return cache[dev];
+}
+
 namespace {
 
 bool valid_prec(amg_prec p) { return p >= AMG_FP64 && p <= AMG_BF16; }

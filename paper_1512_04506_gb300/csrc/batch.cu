@@ -467,11 +467,9 @@ amg_status launch(const Prepared& pr, int threads, int per_sm, cudaStream_t st, 
   AMG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, pr.smem));
   if (occ < 1) return AMG_ERR_UNSUPPORTED;
   if (per_sm > occ) per_sm = occ;
-  int dev = 0, sms = 0;
-  AMG_CUDA_TRY(cudaGetDevice(&dev));
-  AMG_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const long long resident = (long long)per_sm * amg_sm_count();
   AMG_CUDA_TRY(cudaMemsetAsync(pr.a.counters, 0, 256, st));
-  kern<<<per_sm * sms, threads, pr.smem, st>>>(pr.a);
+  kern<<<capped_grid(h0, resident, resident), threads, pr.smem, st>>>(pr.a);
   AMG_LAUNCH_CHECK();
   h0->launches++;
   return AMG_OK;

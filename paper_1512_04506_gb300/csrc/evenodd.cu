@@ -154,11 +154,11 @@ void* slot(amg_coarse* h, int k, int nrhs) { return (unsigned char*)h->eo_tmp + 
 
 amg_status split_merge(amg_coarse* h, bool split, const void* a, void* b, void* c, int nrhs, cudaStream_t st) {
   if (h->p.vec_prec == AMG_FP64) {
-    if (split) eo_split_kernel<double2><<<4 * 152, 256, 0, st>>>((const double2*)a, (double2*)b, (double2*)c, h->g, nrhs);
-    else eo_merge_kernel<double2><<<4 * 152, 256, 0, st>>>((const double2*)a, (const double2*)b, (double2*)c, h->g, nrhs);
+    if (split) eo_split_kernel<double2><<<4 * amg_sm_count(), 256, 0, st>>>((const double2*)a, (double2*)b, (double2*)c, h->g, nrhs);
+    else eo_merge_kernel<double2><<<4 * amg_sm_count(), 256, 0, st>>>((const double2*)a, (const double2*)b, (double2*)c, h->g, nrhs);
   } else {
-    if (split) eo_split_kernel<float2><<<4 * 152, 256, 0, st>>>((const float2*)a, (float2*)b, (float2*)c, h->g, nrhs);
-    else eo_merge_kernel<float2><<<4 * 152, 256, 0, st>>>((const float2*)a, (const float2*)b, (float2*)c, h->g, nrhs);
+    if (split) eo_split_kernel<float2><<<4 * amg_sm_count(), 256, 0, st>>>((const float2*)a, (float2*)b, (float2*)c, h->g, nrhs);
+    else eo_merge_kernel<float2><<<4 * amg_sm_count(), 256, 0, st>>>((const float2*)a, (const float2*)b, (float2*)c, h->g, nrhs);
   }
   AMG_LAUNCH_CHECK();
   h->launches++;

@@ -16,7 +16,12 @@
 // Host code may not hand the array's name to a kernel: on the host that name is only a
 // stand-in for the device symbol.  The device address is looked up with cudaGetSymbolAddress
 // once per device, with that device current, on the first call made on that device; that first
-// call should therefore come before any stream capture begins.
+// call should therefore come before any stream capture begins.  The looked-up address is kept
+// until the process exits: after a cudaDeviceReset it is stale (as is every handle), so a
+// process that resets a device must not call the library on it again.
+//
+// The call never stops early on the host: it queues every application of the max_applies
+// budget, and kernels queued after convergence return at once.
 #include "amg_internal.cuh"
 
 #include <mutex>

@@ -141,7 +141,7 @@ extern "C" amg_status amg_coarse_solve_mixed(amg_handle ho, amg_handle hi, const
   std::vector<int> kp(nrhs, 1);
   std::vector<double> sub(2 * nrhs);
   AMG_CUDA_TRY(cudaMemsetAsync(nrm, 0, nrhs * sizeof(double), st));
-  k_colnorm2<<<2 * 152, 256, 0, st>>>(b, rows, nrhs, nrm);
+  k_colnorm2<<<2 * amg_sm_count(), 256, 0, st>>>(b, rows, nrhs, nrm);
   AMG_LAUNCH_CHECK();
   ho->launches++;
   AMG_CUDA_TRY(cudaMemcpyAsync(bn.data(), nrm, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -156,23 +156,23 @@ extern "C" amg_status amg_coarse_solve_mixed(amg_handle ho, amg_handle hi, const
     if (all) break;
     if (it > 0) {  // zero the columns that have converged so the inner solve skips them
       AMG_CUDA_TRY(cudaMemcpyAsync(keep, kp.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, st));
-      k_resid<<<4 * 152, 256, 0, st>>>(r, b, w, keep, n, nrhs);
+      k_resid<<<4 * amg_sm_count(), 256, 0, st>>>(r, b, w, keep, n, nrhs);
       AMG_LAUNCH_CHECK();
       ho->launches++;
     }
     amg_status s = amg_internal_solve(hi, r, e, nrhs, inner_tol, restart, max_inner_applies, st, sub.data());
     if (s != AMG_OK) return s;
     for (int q = 0; q < nrhs; ++q) inner[q] += kp[q] ? sub[2 * q] : 0;
-    k_axpy<<<4 * 152, 256, 0, st>>>(x, e, n);
+    k_axpy<<<4 * amg_sm_count(), 256, 0, st>>>(x, e, n);
     AMG_LAUNCH_CHECK();
     ho->launches++;
     s = amg_internal_apply(ho, x, w, nrhs, st);
     if (s != AMG_OK) return s;
     for (int q = 0; q < nrhs; ++q) kp[q] = 1;
     AMG_CUDA_TRY(cudaMemcpyAsync(keep, kp.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, st));
-    k_resid<<<4 * 152, 256, 0, st>>>(r, b, w, keep, n, nrhs);
+    k_resid<<<4 * amg_sm_count(), 256, 0, st>>>(r, b, w, keep, n, nrhs);
     AMG_CUDA_TRY(cudaMemsetAsync(nrm, 0, nrhs * sizeof(double), st));
-    k_colnorm2<<<2 * 152, 256, 0, st>>>(r, rows, nrhs, nrm);
+    k_colnorm2<<<2 * amg_sm_count(), 256, 0, st>>>(r, rows, nrhs, nrm);
     AMG_LAUNCH_CHECK();
     ho->launches += 2;
     AMG_CUDA_TRY(cudaMemcpyAsync(rn.data(), nrm, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));

@@ -20,7 +20,10 @@ namespace {
 
 constexpr int ST_T = 256;
 constexpr int MAXR = 16;
-constexpr int NBLK = 2 * 152;
+constexpr int kMaxPartRows = 1024;  // most CTAs of the partial-sum kernels (rows of FState::part)
+
+// CTAs of the partial-sum kernels (k_dots, k_update, k_residual): two per SM.
+int solve_nblk() { return std::min(2 * amg_sm_count(), kMaxPartRows); }
 
 struct FState {
   int m, nrhs, nblk;
@@ -742,21 +745,28 @@ __global__ void __launch_bounds__(ST_T) k_residual(FState s, CT* __restrict__ w,
   if (threadIdx.x == 0 && !any) mark_done(s);
 }
 
-// Grid of the cooperative k_arnoldi: one CTA per SM (at most NBLK, the partial-sum rows'
-// length); 0 when the device cannot hold it resident.
+// Grid of the cooperative k_arnoldi: one CTA per SM (at most solve_nblk(), the partial-sum rows'
+// length); 0 when the device cannot hold it resident.  Found once per device.
 template <typename CT>
 int arnoldi_grid() {
-  static int g = -1;
+  static int cache[64];
+  static bool init = false;
+  if (!init) {
+    for (int& c : cache) c = -1;
+    init = true;
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) dev = 0;
+  if (dev >= 64) dev = 63;
+  int& g = cache[dev];
   if (g < 0) {
-    int dev = 0, sms = 0, per = 0, coop = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int per = 0, coop = 0;
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
     int per_long = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_arnoldi<CT, ar_ic<CT>(), 4, 4>, AR_T, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_long, k_arnoldi<CT, 2, ar_ulong<CT>(), 1>, AR_T, 0);
     per = std::min(per, per_long);
-    g = (coop && per > 0) ? std::min(sms, NBLK) : 0;
+    g = (coop && per > 0) ? std::min(amg_sm_count(), solve_nblk()) : 0;
   }
   return g;
 }
@@ -774,7 +784,8 @@ amg_status solve_impl(amg_coarse* h, long long rows, amg_apply_fn op, const CT* 
   FState s;
   s.m = m;
   s.nrhs = nrhs;
-  s.nblk = NBLK;
+  const int nblk = solve_nblk();
+  s.nblk = nblk;
   s.rows = rows;
   s.tol = tol;
   unsigned char* p = ws;
@@ -783,7 +794,7 @@ amg_status solve_impl(amg_coarse* h, long long rows, amg_apply_fn op, const CT* 
   CT* nxt = cur + vstride;                  // D_c V_j, orthogonalised in place
   p += align256((size_t)(m + 3) * vstride * sizeof(CT));
   s.part = (double2*)p;
-  p += align256((size_t)(m + 1) * NBLK * nrhs * sizeof(double2));
+  p += align256((size_t)(m + 1) * nblk * nrhs * sizeof(double2));
   double2* d2 = (double2*)p;
   s.H = d2;
   d2 += (size_t)nrhs * (m + 1) * m;
@@ -810,9 +821,9 @@ amg_status solve_impl(amg_coarse* h, long long rows, amg_apply_fn op, const CT* 
   s.bar_extra = sw.test_extra_arrivals;
   if (poll) sw.ticket = sw.ticket >= (1 << 30) ? 1 : sw.ticket + 1;  // never 0, the word's initial value
   s.ticket = poll ? sw.ticket : 0;
-  const unsigned egrid = 4 * 152;
+  const unsigned egrid = 4 * amg_sm_count();
   AMG_CUDA_TRY(cudaMemsetAsync(fl, 0, (4 * (size_t)nrhs + 8) * sizeof(int), st));
-  k_residual<CT><<<NBLK, ST_T, 0, st>>>(s, cur, b, 1, x);  // also x = 0
+  k_residual<CT><<<nblk, ST_T, 0, st>>>(s, cur, b, 1, x);  // also x = 0
   AMG_LAUNCH_CHECK();
   h->launches += 1;
   // The kernel that finds every right-hand side converged writes this solve's ticket into the
@@ -855,11 +866,11 @@ amg_status solve_impl(amg_coarse* h, long long rows, amg_apply_fn op, const CT* 
         h->launches += 1;
       } else {
         if (flat) {
-          k_dots_flat<CT><<<dim3(NBLK, j + 1), ST_T, 0, st>>>(s, nxt, V, vstride, j);
-          k_update_flat<CT><<<NBLK, ST_T, 0, st>>>(s, nxt, V, vstride, j);
+          k_dots_flat<CT><<<dim3(nblk, j + 1), ST_T, 0, st>>>(s, nxt, V, vstride, j);
+          k_update_flat<CT><<<nblk, ST_T, 0, st>>>(s, nxt, V, vstride, j);
         } else {
-          k_dots<CT><<<dim3(NBLK, j + 1), ST_T, 0, st>>>(s, nxt, V, vstride, j);
-          k_update<CT><<<NBLK, ST_T, 0, st>>>(s, nxt, V, vstride, j);
+          k_dots<CT><<<dim3(nblk, j + 1), ST_T, 0, st>>>(s, nxt, V, vstride, j);
+          k_update<CT><<<nblk, ST_T, 0, st>>>(s, nxt, V, vstride, j);
         }
         AMG_LAUNCH_CHECK();
         h->launches += 2;
@@ -874,7 +885,7 @@ amg_status solve_impl(amg_coarse* h, long long rows, amg_apply_fn op, const CT* 
     amg_status status = op(h, x, cur, nrhs, st, s.done, nullptr, nullptr);
     if (status != AMG_OK) return status;
     ++launched;
-    k_residual<CT><<<NBLK, ST_T, 0, st>>>(s, cur, b, 0, (CT*)nullptr);
+    k_residual<CT><<<nblk, ST_T, 0, st>>>(s, cur, b, 0, (CT*)nullptr);
     AMG_LAUNCH_CHECK();
     h->launches += 1;
     record();
@@ -897,7 +908,7 @@ amg_status solve_impl(amg_coarse* h, long long rows, amg_apply_fn op, const CT* 
 
 size_t amg_internal_solve_bytes(const amg_coarse* h, int nrhs, int m) {
   const size_t N = (size_t)h->g.Vc * h->g.nc * nrhs * coarse_elem_bytes(h);
-  return align256((size_t)(m + 3) * N) + align256((size_t)(m + 1) * NBLK * nrhs * sizeof(double2)) +
+  return align256((size_t)(m + 3) * N) + align256((size_t)(m + 1) * solve_nblk() * nrhs * sizeof(double2)) +
          align256(scal_doubles(nrhs, m) * sizeof(double)) + align256((4 * (size_t)nrhs + 8) * sizeof(int));
 }
 
@@ -954,6 +965,12 @@ amg_status amg_internal_solve(amg_coarse* h, const void* b, void* x, int nrhs, d
   if (nrhs > MAXR || restart < 1 || restart > AMG_MAX_NTV || max_applies < 1) return AMG_ERR_INVALID_ARG;
   AMG_TRY_INTERNAL(ensure_solve_work(h, nrhs, restart, s));
   return amg_internal_solve_ws(h, b, x, nrhs, tol, restart, max_applies, s, info, h->sw.buf, true);
+}
+
+extern "C" amg_status amg_grid_cap_test_hook(amg_handle h, int max_ctas) {
+  if (!h || max_ctas < 0) return AMG_ERR_INVALID_ARG;
+  h->grid_cap = max_ctas;
+  return AMG_OK;
 }
 
 extern "C" amg_status amg_solve_test_hook(amg_handle h, int extra_arrivals) {

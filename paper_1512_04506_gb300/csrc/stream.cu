@@ -970,25 +970,13 @@ __global__ void __launch_bounds__(160) prolong_tma_kernel(const ProlongArgs<ST, 
 }
 
 // ------------------------------------------------------------------ launch helpers
-int sm_count() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 152;
-  }
-  return n;
-}
-
 template <typename K>
-amg_status grid_for(K kernel, int threads, size_t smem, long long items, int* grid) {
+amg_status grid_for(const amg_coarse* h, K kernel, int threads, size_t smem, long long items, int* grid) {
   AMG_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   AMG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem));
   if (per_sm < 1) return AMG_ERR_UNSUPPORTED;
-  const long long g = (long long)per_sm * sm_count();
-  *grid = (int)(items < g ? items : g);
+  *grid = capped_grid(h, items, (long long)per_sm * amg_sm_count());
   return AMG_OK;
 }
 
@@ -1010,7 +998,7 @@ amg_status launch_apply_tma(amg_coarse* h, const LT* D, const float* dscale, con
   const size_t smem = kPipeBytes + ns * chunk + (size_t)2 * 9 * nc * NR * sizeof(AT) + (size_t)G * nc * NR * sizeof(AT);
   if (smem > 227 * 1024) return AMG_ERR_UNSUPPORTED;
   int grid = 0;
-  amg_status s = grid_for(apply_tma_kernel<LT, NR>, threads, smem, h->g.Vc, &grid);
+  amg_status s = grid_for(h, apply_tma_kernel<LT, NR>, threads, smem, h->g.Vc, &grid);
   if (s != AMG_OK) return s;
   ApplyArgs<LT, NR> a{D, dscale, h->nbr, (const AT*)x, (AT*)y, (AT*)vout, xscale, skip, h->err, h->g, ld, r0, ns, G};
   apply_tma_kernel<LT, NR><<<grid, threads, smem, st>>>(a);
@@ -1036,7 +1024,7 @@ amg_status launch_apply_mrhs_rows(amg_coarse* h, const LT* D, const float* dscal
   const size_t smem = kPipeBytes + ns * chunk + (size_t)G * NR * (nc + 1) * sizeof(float2);
   if (smem > 227 * 1024) return AMG_ERR_UNSUPPORTED;
   int grid = 0;
-  amg_status s = grid_for(apply_mrhs_kernel<LT, NR, LPR>, threads, smem, h->g.Vc, &grid);
+  amg_status s = grid_for(h, apply_mrhs_kernel<LT, NR, LPR>, threads, smem, h->g.Vc, &grid);
   if (s != AMG_OK) return s;
   MrhsArgs<LT, NR> a{D, dscale, h->nbr, (const float2*)x, (float2*)y, (float2*)vout, xscale, skip, h->err, h->g, ns, G};
   apply_mrhs_kernel<LT, NR, LPR><<<grid, threads, smem, st>>>(a);
@@ -1081,7 +1069,7 @@ amg_status launch_eo_mrhs(amg_coarse* h, const EoCall& e, cudaStream_t st) {
       kPipeBytes + ns * chunk + (size_t)G * NR * (nc + 1) * sizeof(float2) + (size_t)nc * NR * sizeof(float2);
   if (smem > 227 * 1024) return AMG_ERR_UNSUPPORTED;
   int grid = 0;
-  amg_status s = grid_for(eo_mrhs_kernel<NR>, threads, smem, h->g.Vc / 2, &grid);
+  amg_status s = grid_for(h, eo_mrhs_kernel<NR>, threads, smem, h->g.Vc / 2, &grid);
   if (s != AMG_OK) return s;
   EoArgs<float2, NR> a{(const float2*)h->Dq, (const float2*)h->Dinvq, h->nbr,
                        h->eo_site + (size_t)e.parity * (h->g.Vc / 2), (const float2*)e.s0, (const float2*)e.s1,
@@ -1109,7 +1097,7 @@ amg_status launch_eo(amg_coarse* h, const EoCall& e, int ld, int r0, cudaStream_
   const size_t smem = kPipeBytes + ns * chunk + (size_t)2 * 9 * nc * NR * sizeof(AT) + (size_t)G * nc * NR * sizeof(AT);
   if (smem > 227 * 1024) return AMG_ERR_UNSUPPORTED;
   int grid = 0;
-  amg_status s = grid_for(eo_apply_kernel<LT, NR>, threads, smem, h->g.Vc / 2, &grid);
+  amg_status s = grid_for(h, eo_apply_kernel<LT, NR>, threads, smem, h->g.Vc / 2, &grid);
   if (s != AMG_OK) return s;
   EoArgs<LT, NR> a{(const LT*)h->Dq, (const LT*)h->Dinvq, h->nbr, h->eo_site + (size_t)e.parity * (h->g.Vc / 2),
                    (const AT*)e.s0, (const AT*)e.s1, (const AT*)e.vadd, (AT*)e.y, (AT*)e.vout, e.xscale, e.skip,
@@ -1210,7 +1198,7 @@ amg_status launch_prolong_tma(amg_coarse* h, const ST* R, const ST* xc, ST* x, i
   const size_t chunk = (size_t)h->g.ntv * nch * sizeof(ST);
   const size_t smem = kPipeBytes + ns * chunk + (size_t)2 * h->g.ntv * NR * sizeof(AT);
   int grid = 0;
-  amg_status s = grid_for(prolong_tma_kernel<ST, NR>, threads, smem, h->g.Vc, &grid);
+  amg_status s = grid_for(h, prolong_tma_kernel<ST, NR>, threads, smem, h->g.Vc, &grid);
   if (s != AMG_OK) return s;
   ProlongArgs<ST, NR> a{R, xc, x, h->err, h->g, ld, r0, nch};
   prolong_tma_kernel<ST, NR><<<grid, threads, smem, st>>>(a);

@@ -10,17 +10,6 @@
 namespace {
 using namespace amgtc;
 
-int sm_count_tc() {
-  static int n = 0;
-  if (!n) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 152;
-  }
-  return n;
-}
-
 // Coarse vector (FP32 [Vc][nc][nrhs], optionally times xscale[r]; the (scaled) FP32 vector is also
 // stored to vout when given) -> BF16 rows [Vc][nc][xunits * 8], round to nearest even.
 template <int NRHS>
@@ -95,8 +84,8 @@ amg_status launch_rp_tc(amg_coarse* h, const void* in, void* out, cudaStream_t s
   int per_sm = 0;
   AMG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
   if (per_sm < 1) return AMG_ERR_UNSUPPORTED;
-  const long long gmax = (long long)per_sm * sm_count_tc();
-  const int grid = (int)(g.Vc < gmax ? g.Vc : gmax);
+  const long long gmax = (long long)per_sm * amg_sm_count();
+  const int grid = capped_grid(h, g.Vc, gmax);
   TcRPArgs a{(const bf16*)h->Rtc, in, out, nullptr, true, h->err, g};
   kern<<<grid, threads, smem, st>>>(a, ns);
   AMG_LAUNCH_CHECK();
@@ -205,7 +194,7 @@ amg_status launch_apply_tf32(amg_coarse* h, const void* x, void* y, cudaStream_t
   const int nc = h->g.nc;
   const size_t xsite = (size_t)nc * tf32_xpitch(NRHS) * 4;
   if ((size_t)h->g.Vc * xsite > h->tf_xbytes) return AMG_ERR_INVALID_ARG;  // nrhs > max_nrhs
-  xc_to_f32rows_kernel<NRHS><<<4 * 152, 256, 0, st>>>((const float2*)x, (float*)h->tf_x, h->g.Vc * nc, xscale,
+  xc_to_f32rows_kernel<NRHS><<<4 * amg_sm_count(), 256, 0, st>>>((const float2*)x, (float*)h->tf_x, h->g.Vc * nc, xscale,
                                                       (float2*)vout, skip);
   AMG_LAUNCH_CHECK();
   h->launches++;
@@ -219,8 +208,8 @@ amg_status launch_apply_tf32(amg_coarse* h, const void* x, void* y, cudaStream_t
   int per_sm = 0;
   AMG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, apply_tf32_kernel<NRHS>, threads, smem));
   if (per_sm < 1) return AMG_ERR_UNSUPPORTED;
-  const long long gmax = (long long)per_sm * sm_count_tc();
-  const int grid = (int)(h->g.Vc < gmax ? h->g.Vc : gmax);
+  const long long gmax = (long long)per_sm * amg_sm_count();
+  const int grid = capped_grid(h, h->g.Vc, gmax);
   TfApplyArgs a{(const float*)h->Dtf, (const float*)h->tf_x, h->nbr, (float2*)y, h->err, h->g};
   apply_tf32_kernel<NRHS><<<grid, threads, smem, st>>>(a, skip, ns);
   AMG_LAUNCH_CHECK();
@@ -236,7 +225,7 @@ amg_status launch_apply_tc(amg_coarse* h, const void* x, void* y, cudaStream_t s
   const int nc = h->g.nc;
   const size_t xsite = tc_xbytes_per_site(h->g, NRHS);
   if ((size_t)h->g.Vc * xsite > h->tc_xbytes) return AMG_ERR_INVALID_ARG;  // nrhs > max_nrhs
-  xc_to_bf16_kernel<NRHS><<<4 * 152, 256, 0, st>>>((const float2*)x, (__nv_bfloat162*)h->tc_x, h->g.Vc * nc, xscale,
+  xc_to_bf16_kernel<NRHS><<<4 * amg_sm_count(), 256, 0, st>>>((const float2*)x, (__nv_bfloat162*)h->tc_x, h->g.Vc * nc, xscale,
                                                    (float2*)vout, skip);
   AMG_LAUNCH_CHECK();
   h->launches++;
@@ -251,8 +240,8 @@ amg_status launch_apply_tc(amg_coarse* h, const void* x, void* y, cudaStream_t s
   int per_sm = 0;
   AMG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, apply_tc_kernel<NRHS>, threads, smem));
   if (per_sm < 1) return AMG_ERR_UNSUPPORTED;
-  const long long gmax = (long long)per_sm * sm_count_tc();
-  const int grid = (int)(h->g.Vc < gmax ? h->g.Vc : gmax);
+  const long long gmax = (long long)per_sm * amg_sm_count();
+  const int grid = capped_grid(h, h->g.Vc, gmax);
   TcApplyArgs a{(const bf16*)h->Dtc, (const bf16*)h->tc_x, h->nbr, (float2*)y, h->err, h->g};
   apply_tc_kernel<NRHS><<<grid, threads, smem, st>>>(a, skip, ns);
   AMG_LAUNCH_CHECK();
@@ -267,7 +256,7 @@ amg_status amg_internal_tc_prepare(amg_coarse* h, cudaStream_t st) {
     if (h->g.nc % 8 || h->g.nc > 64) return AMG_ERR_UNSUPPORTED;
     const size_t n = (size_t)h->g.Vc * 9 * 2 * h->g.nc * h->g.nc;
     AMG_CUDA_TRY(cudaMalloc(&h->Dtc, n * sizeof(bf16)));
-    dc_to_bf16_kernel<<<4 * 152, 256, 0, st>>>(h->Dc64, (bf16*)h->Dtc, h->g.nc, h->g.Vc * 9);
+    dc_to_bf16_kernel<<<4 * amg_sm_count(), 256, 0, st>>>(h->Dc64, (bf16*)h->Dtc, h->g.nc, h->g.Vc * 9);
     AMG_LAUNCH_CHECK();
     // BF16 planes of the apply's input, sized for the largest supported column count <= max_nrhs
     const int nmax = h->p.max_nrhs >= 16 ? 16 : (h->p.max_nrhs + 3) / 4 * 4;
@@ -279,7 +268,7 @@ amg_status amg_internal_tc_prepare(amg_coarse* h, cudaStream_t st) {
     // FP32 D_c for the multi-RHS tensor-core apply (3 x TF32)
     const size_t n = (size_t)h->g.Vc * 9 * 2 * h->g.nc * h->g.nc;
     AMG_CUDA_TRY(cudaMalloc(&h->Dtf, n * sizeof(float)));
-    dc_to_tf32_kernel<<<4 * 152, 256, 0, st>>>(h->Dc64, (float*)h->Dtf, h->g.nc, h->g.Vc * 9);
+    dc_to_tf32_kernel<<<4 * amg_sm_count(), 256, 0, st>>>(h->Dc64, (float*)h->Dtf, h->g.nc, h->g.Vc * 9);
     AMG_LAUNCH_CHECK();
     const int nmax = h->p.max_nrhs >= 16 ? 16 : h->p.max_nrhs / 4 * 4;
     h->tf_xbytes = (size_t)h->g.Vc * h->g.nc * tf32_xpitch(nmax) * 4;
@@ -290,7 +279,7 @@ amg_status amg_internal_tc_prepare(amg_coarse* h, cudaStream_t st) {
     if (g.ntv % 4 || g.Vb % 8) return AMG_ERR_UNSUPPORTED;
     const size_t n = (size_t)g.Vc * 2 * 2 * g.ntv * g.nagg;
     AMG_CUDA_TRY(cudaMalloc(&h->Rtc, n * sizeof(bf16)));
-    r_to_tc_kernel<<<4 * 152, 256, 0, st>>>(h->R64, (bf16*)h->Rtc, g);
+    r_to_tc_kernel<<<4 * amg_sm_count(), 256, 0, st>>>(h->R64, (bf16*)h->Rtc, g);
     AMG_LAUNCH_CHECK();
   }
   return AMG_OK;
@@ -310,7 +299,7 @@ amg_status amg_internal_export_stored(amg_coarse* h, double2* out) {
   const size_t n = (size_t)h->g.Vc * 9 * h->g.nc * h->g.nc;
   double2* tmp = nullptr;
   AMG_CUDA_TRY(cudaMalloc(&tmp, n * sizeof(double2)));
-  bf16_to_dc_kernel<<<4 * 152, 256, 0, h->last_stream>>>((const bf16*)h->Dtc, tmp, h->g.nc, h->g.Vc * 9);
+  bf16_to_dc_kernel<<<4 * amg_sm_count(), 256, 0, h->last_stream>>>((const bf16*)h->Dtc, tmp, h->g.nc, h->g.Vc * 9);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->last_stream);
   if (e == cudaSuccess) e = cudaMemcpy(out, tmp, n * sizeof(double2), cudaMemcpyDefault);
