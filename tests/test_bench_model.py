@@ -40,3 +40,22 @@ def test_whole_job_rate_is_per_rank_bytes_times_ranks():
     one = bench.whole_job_gbs(1, 5e9, 10, 0.01)
     assert one == 5e9 * 10 / 0.01 / 1e9
     assert bench.whole_job_gbs(4, 5e9, 10, 0.01) == 4 * one
+
+
+def test_reference_arm_runs_the_gpu_arms_step_on_every_core(monkeypatch):
+    """--impl reference: the oracle on every host core (one single-threaded process each), the
+    same step mix as the GPU arm (R, FGMRES with the workload's 2 applications, P) and the same
+    config; the sample's bytes are the workload's FP32 byte model scaled to the 16^4 volume."""
+    import os
+    for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
+        monkeypatch.delenv(k, raising=False)
+    cfg = bench.workload_config(bench.APPLIES_PER_STEP)
+    assert bench.APPLIES_PER_STEP == 2
+    assert cfg["applies_per_step"] == 2 and cfg["bytes_per_step"] == 5197791232
+    assert bench.sample_step_bytes(2) == 5197791232 / 16
+    res, rank = bench.run_reference(type("A", (), {"warmup": 0, "steps": 1})())
+    assert rank == 0 and res["impl"] == "reference"
+    assert res["config"] == cfg
+    cores = len(os.sched_getaffinity(0))
+    assert res["cpu_baseline"]["cores"] == res["cpu_baseline"]["threads"] == cores
+    assert res["value"] > 0 and res["e2e"]["h2d_bytes_per_step"] == 0
