@@ -201,6 +201,68 @@ amg_status amg_export_Dinv(amg_handle h, void *out);
 amg_status amg_cgc(amg_handle h, const void *d_y, void *d_x, int nrhs, double tol, int restart,
                    int max_applies, void *stream, double *info);
 
+/* ------------------------------------------------------------------ the two-level method around
+ * the coarse-grid correction: fine operator, smoother, V-cycle, outer solve.  They work on fine
+ * vectors [V][4][3][nrhs] in vec_prec (FP64 or FP32), nrhs <= max_nrhs, and need amg_setup_fine
+ * first (AMG_ERR_UNSUPPORTED otherwise).  The smoother needs every coarse extent L_mu / B_mu even
+ * (two block colours) and V_block <= 256 (AMG_ERR_UNSUPPORTED otherwise). */
+
+/*
+ * amg_setup_fine -- keeps the links d_U ([V][4][3][3] complex double, device, the array given to
+ * amg_setup_coarse; not retained) in the handle in vec_prec, with the clover field of the setup,
+ * for the fine operator D.  Asynchronous on the stream; may be called again (replaces the copy).
+ */
+amg_status amg_setup_fine(amg_handle h, const void *d_U, void *stream);
+
+/*
+ * amg_dirac_apply -- out = D psi with the Wilson-clover operator whose block parts Eq. cgo
+ * restricts (D = (4 + m0) + C - 1/2 sum_mu [(1 - g_mu) U_mu(x) T_{+mu} + (1 + g_mu) U_mu(x - mu)^dag
+ * T_{-mu}], periodic; the clover term C^{ll}, C^{rr} of Alg. 7).  psi and out device, distinct.
+ */
+amg_status amg_dirac_apply(amg_handle h, const void *d_psi, void *d_out, int nrhs, void *stream);
+
+/*
+ * amg_sap -- n_cycles cycles of the domain-decomposition smoother of Alg. 3 on D x = y, in place
+ * on x (x is the start and the result): the Schwarz alternating procedure over the aggregation
+ * blocks coloured by the parity of their block coordinates, colour 0 then colour 1 in each
+ * cycle, each block system B_b e = (y - D x)|_b (B = D without the hops across the block face)
+ * solved by n_mr minimal-residual steps from e = 0 and added to x.  y and x device, distinct.
+ */
+amg_status amg_sap(amg_handle h, const void *d_y, void *d_x, int nrhs, int n_cycles, int n_mr, void *stream);
+
+/* Parameters of the V-cycle: the coarse solve of the coarse-grid correction (FGMRES(coarse_restart)
+ * to coarse_tol, at most coarse_max_applies applications of D_c; the paper's tolerance is 0.05) and
+ * the smoother (n_smoother SAP cycles of n_mr MR steps per block). */
+typedef struct {
+  double coarse_tol;
+  int coarse_restart;
+  int coarse_max_applies;
+  int n_smoother;
+  int n_mr;
+} amg_vcycle_params;
+
+/*
+ * amg_vcycle -- one application of the two-level preconditioner of Alg. 1: x = S(y; CGC(y)),
+ * the coarse-grid correction of Alg. 2 (as amg_cgc) followed by n_smoother SAP cycles started from
+ * it.  y and x device, distinct; x is overwritten.
+ */
+amg_status amg_vcycle(amg_handle h, const amg_vcycle_params *vp, const void *d_y, void *d_x, int nrhs,
+                      void *stream);
+
+/*
+ * amg_solve -- D u = f by restarted FGMRES(restart) right-preconditioned with the V-cycle (Sec. 1:
+ * the two-level method as a preconditioner of a flexible Krylov solver), from u = 0, every
+ * right-hand side independently: classical Gram-Schmidt, Givens rotations, stop when the implicit
+ * residual is <= tol ||f|| or after max_applies applications of D (each restart after the first
+ * recomputes the true residual, one more application).  info (may be NULL): per right-hand side
+ * (applications of D, implicit relative residual) as info[2 r], info[2 r + 1].  The scalars are
+ * kept on the host, so the call synchronises the stream after every Arnoldi step and at the end.
+ * Its Krylov basis and preconditioned vectors (2 restart + 2 fine vectors) are allocated in the
+ * handle on first use.  restart <= 64.
+ */
+amg_status amg_solve(amg_handle h, const amg_vcycle_params *vp, const void *d_f, void *d_u, int nrhs,
+                     double tol, int restart, int max_applies, void *stream, double *info);
+
 /*
  * amg_batch_cgc -- x_k = P_k D_ck R_k y_k for n lattices (handles hs[k]) in one
  * persistent launch [Alg. 2's restriction, coarse operator and prolongation; Sec. 3 runs its

@@ -42,6 +42,16 @@ class amg_params(ctypes.Structure):
     ]
 
 
+class amg_vcycle_params(ctypes.Structure):
+    _fields_ = [
+        ("coarse_tol", ctypes.c_double),
+        ("coarse_restart", ctypes.c_int),
+        ("coarse_max_applies", ctypes.c_int),
+        ("n_smoother", ctypes.c_int),
+        ("n_mr", ctypes.c_int),
+    ]
+
+
 class AmgError(RuntimeError):
     def __init__(self, status, where):
         self.status = status
@@ -70,6 +80,11 @@ _proto = {
     "amg_coarse_solve_eo": [_vp, _vp, _vp, _i, _d, _i, _i, _vp, ctypes.POINTER(_d)],
     "amg_cgc_eo": [_vp, _vp, _vp, _i, _d, _i, _i, _vp, ctypes.POINTER(_d)],
     "amg_export_Dinv": [_vp, _vp],
+    "amg_setup_fine": [_vp, _vp, _vp],
+    "amg_dirac_apply": [_vp, _vp, _vp, _i, _vp],
+    "amg_sap": [_vp, _vp, _vp, _i, _i, _i, _vp],
+    "amg_vcycle": [_vp, ctypes.POINTER(amg_vcycle_params), _vp, _vp, _i, _vp],
+    "amg_solve": [_vp, ctypes.POINTER(amg_vcycle_params), _vp, _vp, _i, _d, _i, _i, _vp, ctypes.POINTER(_d)],
     "amg_batch_cgc": [ctypes.POINTER(_vp), _i, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                       ctypes.POINTER(_i), _vp],
     "amg_batch_autotune": [ctypes.POINTER(_vp), _i, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
@@ -216,6 +231,33 @@ def amg_coarse_solve_mixed(h_outer, h_inner, b, x, nrhs=1, tol=1e-4, inner_tol=0
 def amg_cgc(h, y, x, nrhs=1, tol=0.05, restart=30, max_applies=200, stream=None, info=True):
     buf = _info(nrhs, info)
     _check(lib.amg_cgc(h, ptr(y), ptr(x), nrhs, tol, restart, max_applies, stream_ptr(stream), buf), "amg_cgc")
+    return _info_out(buf, nrhs)
+
+
+def make_vcycle_params(coarse_tol=0.05, coarse_restart=30, coarse_max_applies=200, n_smoother=4, n_mr=4):
+    return amg_vcycle_params(coarse_tol, coarse_restart, coarse_max_applies, n_smoother, n_mr)
+
+
+def amg_setup_fine(h, U, stream=None):
+    return _check(lib.amg_setup_fine(h, ptr(U), stream_ptr(stream)), "amg_setup_fine")
+
+
+def amg_dirac_apply(h, psi, out, nrhs=1, stream=None):
+    return _check(lib.amg_dirac_apply(h, ptr(psi), ptr(out), nrhs, stream_ptr(stream)), "amg_dirac_apply")
+
+
+def amg_sap(h, y, x, nrhs=1, n_cycles=1, n_mr=4, stream=None):
+    return _check(lib.amg_sap(h, ptr(y), ptr(x), nrhs, n_cycles, n_mr, stream_ptr(stream)), "amg_sap")
+
+
+def amg_vcycle(h, vp, y, x, nrhs=1, stream=None):
+    return _check(lib.amg_vcycle(h, ctypes.byref(vp), ptr(y), ptr(x), nrhs, stream_ptr(stream)), "amg_vcycle")
+
+
+def amg_solve(h, vp, f, u, nrhs=1, tol=1e-10, restart=30, max_applies=500, stream=None, info=True):
+    buf = _info(nrhs, info)
+    _check(lib.amg_solve(h, ctypes.byref(vp), ptr(f), ptr(u), nrhs, tol, restart, max_applies, stream_ptr(stream),
+                         buf), "amg_solve")
     return _info_out(buf, nrhs)
 
 

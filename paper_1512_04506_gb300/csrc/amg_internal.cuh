@@ -154,6 +154,10 @@ struct amg_coarse {
   size_t tmp_bytes = 0;
   unsigned long long launches = 0;  // kernels launched through this handle (host-side count)
   int grid_cap = 0;           // test hook: most CTAs of a grid-stride launch (0: occupancy x SMs)
+  void* fU = nullptr;         // fine operator (amg_setup_fine): links [V][4][3][3] in vec_prec
+  void* fC = nullptr;         // clover [V][2][6][6] in vec_prec (aliases clover for FP64)
+  void* fwork = nullptr;      // outer FGMRES workspace (fine Krylov basis, Z vectors, sums)
+  size_t fwork_bytes = 0;
 };
 
 // Grid of a grid-stride launch over `items` work items with `resident` CTAs resident at once: the
@@ -222,6 +226,7 @@ amg_status amg_internal_batch(amg_coarse* const* hs, int n, const void* const* y
 amg_status amg_internal_export_stored(amg_coarse* h, double2* out);
 amg_status amg_internal_tc_prepare(amg_coarse* h, cudaStream_t s);
 void amg_internal_free_tc(amg_coarse* h);
+void amg_internal_free_fine(amg_coarse* h);
 // Coarse application for the solver: CTAs return at once while *skip != 0; with xscale the input
 // is xc * xscale[r] and that scaled input is also stored to vout (both may be null).
 // Even/odd stencil piece (see eo_apply_kernel in stream.cu); parity of the output half.

@@ -104,6 +104,7 @@ void free_handle(amg_coarse* h) {
   cudaFree(h->xc_tmp);
   cudaFree(h->yc_tmp);
   amg_internal_free_tc(h);
+  amg_internal_free_fine(h);
   delete h;
 }
 

@@ -1,0 +1,801 @@
+// Fine-grid part of the two-level method around the coarse-grid correction:
+//   D        the Wilson-clover operator (the fine operator whose blocks Eq. cgo restricts),
+//   SAP      the domain-decomposition smoother of Alg. 3 (multiplicative Schwarz over two block
+//            colours, each block system solved by minimal-residual steps),
+//   V-cycle  Alg. 1: the smoother started from the coarse-grid correction of Alg. 2,
+//   solve    the outer FGMRES of Sec. 1, right-preconditioned with the V-cycle.
+//
+// D psi(x) = (4 + m0) psi(x) + C(x) psi(x)
+//            - 1/2 sum_mu [(1 - g_mu) U_mu(x) psi(x + mu) + (1 + g_mu) U_mu(x - mu)^dag psi(x - mu)],
+// periodic, chiral basis g_mu = [[0, A_mu], [A_mu^dag, 0]] with A = -i sigma_1, -i sigma_2, -i sigma_3, 1.
+// Each hop is spin-projected: with psi = (u, d) (spins 0,1 and 2,3),
+//   (1 - g) psi = (h, -A^dag h), h = u - A d;   (1 + g) psi = (h', A^dag h'), h' = u + A d,
+// so a hop costs two colour mat-vecs (on h) instead of four.  The clover term acts on the two
+// chirality halves with the handle's 6x6 blocks C^{ll}, C^{rr}.
+//
+// The smoother's blocks are the aggregation blocks.  One half sweep (colour c) is one launch: one
+// CTA per (block of colour c, right-hand side), one thread per site.  The CTA forms the residual
+// r = y - D x on its sites (the neighbours outside the block have the other colour and are not
+// written in this launch), runs n_mr MR steps on B e = r with B = D without the hops that cross
+// the block face (rho in shared memory, block-wide sums), and adds e to x.
+#include "amg_internal.cuh"
+
+#include <math.h>
+
+#include <algorithm>
+#include <complex>
+#include <vector>
+
+namespace {
+
+template <typename T> struct Cx;
+template <> struct Cx<double> { using type = double2; };
+template <> struct Cx<float> { using type = float2; };
+
+template <typename C> __device__ __forceinline__ C zadd(C a, C b) { a.x += b.x; a.y += b.y; return a; }
+template <typename C> __device__ __forceinline__ C zsub(C a, C b) { a.x -= b.x; a.y -= b.y; return a; }
+template <typename C> __device__ __forceinline__ C zneg(C a) { a.x = -a.x; a.y = -a.y; return a; }
+template <typename C> __device__ __forceinline__ C zi(C a) { C r; r.x = -a.y; r.y = a.x; return r; }    // i a
+template <typename C> __device__ __forceinline__ C zmi(C a) { C r; r.x = a.y; r.y = -a.x; return r; }   // -i a
+template <typename C> __device__ __forceinline__ C zzero() { C r; r.x = 0; r.y = 0; return r; }
+template <typename C, typename T> __device__ __forceinline__ C zscale(C a, T s) { a.x *= s; a.y *= s; return a; }
+template <typename C> __device__ __forceinline__ void zfma(C& acc, C a, C b) {  // acc += a b
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+}
+template <typename C> __device__ __forceinline__ void zfmac(C& acc, C a, C b) {  // acc += conj(a) b
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(-a.y, b.x, acc.y);
+}
+
+// (A_mu d)_s, s = 0, 1
+template <typename C>
+__device__ __forceinline__ void amul(int mu, C d0, C d1, C& o0, C& o1) {
+  if (mu == 0) { o0 = zmi(d1); o1 = zmi(d0); }          // -i sigma_1
+  else if (mu == 1) { o0 = zneg(d1); o1 = d0; }         // -i sigma_2 = [[0, -1], [1, 0]]
+  else if (mu == 2) { o0 = zmi(d0); o1 = zi(d1); }      // -i sigma_3
+  else { o0 = d0; o1 = d1; }                            // 1
+}
+// (A_mu^dag v)_s
+template <typename C>
+__device__ __forceinline__ void adagmul(int mu, C v0, C v1, C& o0, C& o1) {
+  if (mu == 0) { o0 = zi(v1); o1 = zi(v0); }            // i sigma_1
+  else if (mu == 1) { o0 = v1; o1 = zneg(v0); }         // i sigma_2 = [[0, 1], [-1, 0]]
+  else if (mu == 2) { o0 = zi(v0); o1 = zmi(v1); }      // i sigma_3
+  else { o0 = v0; o1 = v1; }
+}
+
+// out += -1/2 (1 - g_mu) U p   (FWD) or   out += -1/2 (1 + g_mu) U^dag p   (!FWD); p, out: [spin][colour]
+template <bool FWD, typename C>
+__device__ __forceinline__ void hop(int mu, const C* __restrict__ U, const C p[12], C out[12]) {
+  C h[2][3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    C a0, a1;
+    amul(mu, p[6 + c], p[9 + c], a0, a1);
+    h[0][c] = FWD ? zsub(p[c], a0) : zadd(p[c], a0);
+    h[1][c] = FWD ? zsub(p[3 + c], a1) : zadd(p[3 + c], a1);
+  }
+  C u[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) u[k] = U[k];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    C w0 = zzero<C>(), w1 = zzero<C>();
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      if (FWD) {
+        zfma(w0, u[a * 3 + b], h[0][b]);
+        zfma(w1, u[a * 3 + b], h[1][b]);
+      } else {
+        zfmac(w0, u[b * 3 + a], h[0][b]);
+        zfmac(w1, u[b * 3 + a], h[1][b]);
+      }
+    }
+    C d0, d1;
+    adagmul(mu, w0, w1, d0, d1);
+    // upper half -1/2 W; lower half +1/2 A^dag W (forward) or -1/2 A^dag W (backward)
+    out[a] = zsub(out[a], zscale(w0, 0.5));
+    out[3 + a] = zsub(out[3 + a], zscale(w1, 0.5));
+    if (FWD) {
+      out[6 + a] = zadd(out[6 + a], zscale(d0, 0.5));
+      out[9 + a] = zadd(out[9 + a], zscale(d1, 0.5));
+    } else {
+      out[6 + a] = zsub(out[6 + a], zscale(d0, 0.5));
+      out[9 + a] = zsub(out[9 + a], zscale(d1, 0.5));
+    }
+  }
+}
+
+// out = (4 + m0) p + C(x) p for the site whose clover blocks start at Cl ([2][6][6])
+template <typename C, typename T>
+__device__ __forceinline__ void site_term(const C* __restrict__ Cl, T mass, const C p[12], C out[12]) {
+#pragma unroll
+  for (int hh = 0; hh < 2; ++hh) {
+#pragma unroll
+    for (int a = 0; a < 6; ++a) {
+      C acc = zscale(p[hh * 6 + a], mass);
+#pragma unroll
+      for (int b = 0; b < 6; ++b) zfma(acc, Cl[(hh * 6 + a) * 6 + b], p[hh * 6 + b]);
+      out[hh * 6 + a] = acc;
+    }
+  }
+}
+
+struct FineGeom {
+  int L[4];
+  long long V;
+  int B[4];
+  int Lc[4];
+  int Vb;
+};
+
+__device__ __forceinline__ void site_coords(const FineGeom& g, long long s, int x[4]) {
+  x[0] = (int)(s % g.L[0]);
+  s /= g.L[0];
+  x[1] = (int)(s % g.L[1]);
+  s /= g.L[1];
+  x[2] = (int)(s % g.L[2]);
+  x[3] = (int)(s / g.L[2]);
+}
+
+__device__ __forceinline__ long long site_of(const FineGeom& g, const int x[4]) {
+  return (((long long)x[3] * g.L[2] + x[2]) * g.L[1] + x[1]) * g.L[0] + x[0];
+}
+
+__device__ __forceinline__ long long shifted(const FineGeom& g, const int x[4], int mu, int dir) {
+  int y[4] = {x[0], x[1], x[2], x[3]};
+  y[mu] = (y[mu] + dir + g.L[mu]) % g.L[mu];
+  return site_of(g, y);
+}
+
+template <typename C>
+__device__ __forceinline__ void load12(const C* __restrict__ v, long long site, int nrhs, int r, C p[12]) {
+#pragma unroll
+  for (int k = 0; k < 12; ++k) p[k] = v[(site * 12 + k) * nrhs + r];
+}
+
+// out = D psi (SUB: out = y - D psi), one thread per (site, right-hand side)
+template <typename T, bool SUB>
+__global__ void __launch_bounds__(128) dirac_kernel(const typename Cx<T>::type* __restrict__ U,
+                                                    const typename Cx<T>::type* __restrict__ Cl,
+                                                    const typename Cx<T>::type* __restrict__ psi,
+                                                    const typename Cx<T>::type* __restrict__ y,
+                                                    typename Cx<T>::type* __restrict__ out, FineGeom g, T mass,
+                                                    int nrhs) {
+  using C = typename Cx<T>::type;
+  const long long total = g.V * nrhs;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long s = e / nrhs;
+    const int r = (int)(e % nrhs);
+    int x[4];
+    site_coords(g, s, x);
+    C p[12], o[12];
+    load12(psi, s, nrhs, r, p);
+    site_term(Cl + s * 72, mass, p, o);
+#pragma unroll 1
+    for (int mu = 0; mu < 4; ++mu) {
+      const long long sf = shifted(g, x, mu, 1), sb = shifted(g, x, mu, -1);
+      load12(psi, sf, nrhs, r, p);
+      hop<true>(mu, U + (s * 4 + mu) * 9, p, o);
+      load12(psi, sb, nrhs, r, p);
+      hop<false>(mu, U + (sb * 4 + mu) * 9, p, o);
+    }
+    if (SUB) {
+      load12(y, s, nrhs, r, p);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) o[k] = zsub(p[k], o[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < 12; ++k) out[(s * 12 + k) * nrhs + r] = o[k];
+  }
+}
+
+// Block sum of three doubles over the CTA (all threads call it; every thread gets the sums).
+__device__ __forceinline__ void cta_sum3(double v[3], double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+  __syncthreads();  // red may still be read by the previous call
+  if (lane == 0)
+    for (int k = 0; k < 3; ++k) red[warp * 3 + k] = v[k];
+  __syncthreads();
+  for (int k = 0; k < 3; ++k) {
+    double s = 0;
+    for (int w = 0; w < nw; ++w) s += red[w * 3 + k];
+    v[k] = s;
+  }
+}
+
+// One SAP half sweep on the blocks of one colour: x += MR_{n_mr}(B_b, (y - D x)|_b) per block.
+// grid (Vc / 2, nrhs); blockDim >= Vb (threads past Vb only join the sums); dynamic smem: rho
+// [Vb][12] + 3 doubles per warp.
+template <typename T>
+__global__ void __launch_bounds__(256) sap_kernel(const typename Cx<T>::type* __restrict__ U,
+                                                  const typename Cx<T>::type* __restrict__ Cl,
+                                                  const typename Cx<T>::type* __restrict__ y,
+                                                  typename Cx<T>::type* __restrict__ x, FineGeom g, T mass,
+                                                  int nrhs, int colour, int n_mr) {
+  using C = typename Cx<T>::type;
+  extern __shared__ __align__(16) unsigned char smem[];
+  C* rho = reinterpret_cast<C*>(smem);
+  double* red = reinterpret_cast<double*>(smem + (size_t)g.Vb * 12 * sizeof(C));
+  const int r = blockIdx.y;
+  // the k-th block of this colour: rows of Lc[0] / 2 blocks, X of the colour's parity in each row
+  const long long k = blockIdx.x;
+  const int half = g.Lc[0] / 2;
+  long long row = k / half;
+  const int Y = (int)(row % g.Lc[1]);
+  row /= g.Lc[1];
+  const int Z = (int)(row % g.Lc[2]);
+  const int Tt = (int)(row / g.Lc[2]);
+  const int X = 2 * (int)(k % half) + ((colour + Y + Z + Tt) & 1);
+  const int t = threadIdx.x;
+  const bool act = t < g.Vb;
+  int lc[4] = {0, 0, 0, 0}, xs[4] = {0, 0, 0, 0};
+  long long s = 0;
+  if (act) {
+    lc[0] = t % g.B[0];
+    lc[1] = (t / g.B[0]) % g.B[1];
+    lc[2] = (t / (g.B[0] * g.B[1])) % g.B[2];
+    lc[3] = t / (g.B[0] * g.B[1] * g.B[2]);
+    xs[0] = X * g.B[0] + lc[0];
+    xs[1] = Y * g.B[1] + lc[1];
+    xs[2] = Z * g.B[2] + lc[2];
+    xs[3] = Tt * g.B[3] + lc[3];
+    s = site_of(g, xs);
+  }
+  const int stride[4] = {1, g.B[0], g.B[0] * g.B[1], g.B[0] * g.B[1] * g.B[2]};
+  // residual r = y - D x on this site (full D: neighbours outside the block have the other colour)
+  C p[12], o[12], e[12];
+  if (act) {
+    load12(x, s, nrhs, r, p);
+    site_term(Cl + s * 72, mass, p, o);
+#pragma unroll 1
+    for (int mu = 0; mu < 4; ++mu) {
+      const long long sf = shifted(g, xs, mu, 1), sb = shifted(g, xs, mu, -1);
+      load12(x, sf, nrhs, r, p);
+      hop<true>(mu, U + (s * 4 + mu) * 9, p, o);
+      load12(x, sb, nrhs, r, p);
+      hop<false>(mu, U + (sb * 4 + mu) * 9, p, o);
+    }
+    load12(y, s, nrhs, r, p);
+#pragma unroll
+    for (int q = 0; q < 12; ++q) {
+      const C rq = zsub(p[q], o[q]);
+      rho[t * 12 + q] = rq;
+      e[q] = zzero<C>();
+    }
+  }
+  __syncthreads();
+#pragma unroll 1
+  for (int it = 0; it < n_mr; ++it) {
+    // p = B rho at this site: site term plus the hops that stay inside the block
+    double v[3] = {0, 0, 0};
+    if (act) {
+      C rr[12];
+#pragma unroll
+      for (int q = 0; q < 12; ++q) rr[q] = rho[t * 12 + q];
+      site_term(Cl + s * 72, mass, rr, o);
+#pragma unroll 1
+      for (int mu = 0; mu < 4; ++mu) {
+        if (lc[mu] + 1 < g.B[mu]) {
+#pragma unroll
+          for (int q = 0; q < 12; ++q) p[q] = rho[(t + stride[mu]) * 12 + q];
+          hop<true>(mu, U + (s * 4 + mu) * 9, p, o);
+        }
+        if (lc[mu] > 0) {
+#pragma unroll
+          for (int q = 0; q < 12; ++q) p[q] = rho[(t - stride[mu]) * 12 + q];
+          const long long sb = shifted(g, xs, mu, -1);
+          hop<false>(mu, U + (sb * 4 + mu) * 9, p, o);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 12; ++q) {
+        v[0] += (double)o[q].x * o[q].x + (double)o[q].y * o[q].y;            // <p, p>
+        v[1] += (double)o[q].x * rr[q].x + (double)o[q].y * rr[q].y;          // Re <p, rho>
+        v[2] += (double)o[q].x * rr[q].y - (double)o[q].y * rr[q].x;          // Im <p, rho>
+      }
+    }
+    cta_sum3(v, red);  // also orders every read of rho before the writes below
+    if (act && v[0] > 0) {
+      const double ar = v[1] / v[0], ai = v[2] / v[0];
+      C al;
+      al.x = (T)ar;
+      al.y = (T)ai;
+#pragma unroll
+      for (int q = 0; q < 12; ++q) {
+        const C rq = rho[t * 12 + q];
+        zfma(e[q], al, rq);
+        C ap = zzero<C>();
+        zfma(ap, al, o[q]);
+        rho[t * 12 + q] = zsub(rq, ap);
+      }
+    }
+    __syncthreads();
+  }
+  if (act) {
+#pragma unroll
+    for (int q = 0; q < 12; ++q) {
+      const long long idx = (s * 12 + q) * nrhs + r;
+      x[idx] = zadd(x[idx], e[q]);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ outer FGMRES vector kernels
+constexpr int FT = 256;
+
+// part[i][r] += sum_n conj(V_i[n, r]) w[n, r] for i < nv (FP64 sums; one atomic per CTA and pair)
+template <typename C>
+__global__ void __launch_bounds__(FT) fdots_kernel(const C* __restrict__ Vb, long long vstride, int nv,
+                                                   const C* __restrict__ w, long long n, int nrhs, double2* out) {
+  __shared__ double2 red[FT];
+  const int i = blockIdx.y;
+  const C* v = Vb + vstride * i;
+  const int per = FT / nrhs * nrhs;  // threads per CTA that take part (a multiple of nrhs)
+  double2 acc = make_double2(0, 0);
+  if (threadIdx.x < per) {
+    for (long long e = blockIdx.x * (long long)per + threadIdx.x; e < n * nrhs; e += (long long)gridDim.x * per) {
+      const C a = v[e], b = w[e];
+      acc.x += (double)a.x * b.x + (double)a.y * b.y;
+      acc.y += (double)a.x * b.y - (double)a.y * b.x;
+    }
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x < nrhs) {
+    double2 s = make_double2(0, 0);
+    for (int q = threadIdx.x; q < per; q += nrhs) {
+      s.x += red[q].x;
+      s.y += red[q].y;
+    }
+    atomicAdd(&out[i * nrhs + threadIdx.x].x, s.x);
+    atomicAdd(&out[i * nrhs + threadIdx.x].y, s.y);
+  }
+}
+
+// w -= sum_{i < nv} h[i][r] V_i ; nrm2[r] += |w|^2 (after the update)
+template <typename C>
+__global__ void __launch_bounds__(FT) fupdate_kernel(const C* __restrict__ Vb, long long vstride, int nv,
+                                                     const double2* __restrict__ h, C* __restrict__ w, long long n,
+                                                     int nrhs, double* nrm2) {
+  __shared__ double red[FT];
+  const int per = FT / nrhs * nrhs;
+  double acc = 0;
+  if (threadIdx.x < per) {
+    for (long long e = blockIdx.x * (long long)per + threadIdx.x; e < n * nrhs; e += (long long)gridDim.x * per) {
+      const int r = (int)(e % nrhs);
+      double2 a = make_double2((double)w[e].x, (double)w[e].y);
+      for (int i = 0; i < nv; ++i) {
+        const C v = Vb[vstride * i + e];
+        const double2 c = h[i * nrhs + r];
+        a.x -= c.x * v.x - c.y * v.y;
+        a.y -= c.x * v.y + c.y * v.x;
+      }
+      C o;
+      o.x = a.x;
+      o.y = a.y;
+      w[e] = o;
+      acc += (double)o.x * o.x + (double)o.y * o.y;
+    }
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x < nrhs) {
+    double s = 0;
+    for (int q = threadIdx.x; q < per; q += nrhs) s += red[q];
+    atomicAdd(&nrm2[threadIdx.x], s);
+  }
+}
+
+// y = a[r] * x (a per column, complex); y may be x
+template <typename C>
+__global__ void fscale_kernel(const C* x, C* y, const double2* __restrict__ a, long long n, int nrhs) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n * nrhs;
+       e += (long long)gridDim.x * blockDim.x) {
+    const double2 c = a[e % nrhs];
+    const C v = x[e];
+    C o;
+    o.x = c.x * v.x - c.y * v.y;
+    o.y = c.x * v.y + c.y * v.x;
+    y[e] = o;
+  }
+}
+
+// y += sum_{i < nv} c[i][r] X_i
+template <typename C>
+__global__ void fcombine_kernel(const C* __restrict__ Xb, long long vstride, int nv, const double2* __restrict__ c,
+                                C* __restrict__ y, long long n, int nrhs) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n * nrhs;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(e % nrhs);
+    double2 a = make_double2((double)y[e].x, (double)y[e].y);
+    for (int i = 0; i < nv; ++i) {
+      const C v = Xb[vstride * i + e];
+      const double2 k = c[i * nrhs + r];
+      a.x += k.x * v.x - k.y * v.y;
+      a.y += k.x * v.y + k.y * v.x;
+    }
+    C o;
+    o.x = a.x;
+    o.y = a.y;
+    y[e] = o;
+  }
+}
+
+// nrm2[r] += |v|^2
+template <typename C>
+__global__ void __launch_bounds__(FT) fnorm_kernel(const C* __restrict__ v, long long n, int nrhs, double* nrm2) {
+  __shared__ double red[FT];
+  const int per = FT / nrhs * nrhs;
+  double acc = 0;
+  if (threadIdx.x < per)
+    for (long long e = blockIdx.x * (long long)per + threadIdx.x; e < n * nrhs; e += (long long)gridDim.x * per)
+      acc += (double)v[e].x * v[e].x + (double)v[e].y * v[e].y;
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x < nrhs) {
+    double s = 0;
+    for (int q = threadIdx.x; q < per; q += nrhs) s += red[q];
+    atomicAdd(&nrm2[threadIdx.x], s);
+  }
+}
+
+FineGeom fine_geom(const amg_coarse* h) {
+  FineGeom g;
+  for (int mu = 0; mu < 4; ++mu) {
+    g.L[mu] = h->g.L[mu];
+    g.B[mu] = h->g.B[mu];
+    g.Lc[mu] = h->g.Lc[mu];
+  }
+  g.V = h->g.V;
+  g.Vb = (int)h->g.Vb;
+  return g;
+}
+
+template <typename T>
+__global__ void to_prec_kernel(const double2* __restrict__ in, typename Cx<T>::type* __restrict__ out, long long n) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    typename Cx<T>::type v;
+    v.x = (T)in[e].x;
+    v.y = (T)in[e].y;
+    out[e] = v;
+  }
+}
+
+bool fine_fp64(const amg_coarse* h) { return h->p.vec_prec == AMG_FP64; }
+size_t fine_elem(const amg_coarse* h) { return fine_fp64(h) ? sizeof(double2) : sizeof(float2); }
+
+template <typename T>
+amg_status launch_dirac(amg_coarse* h, const void* psi, const void* y, void* out, int nrhs, cudaStream_t st) {
+  using C = typename Cx<T>::type;
+  const long long total = h->g.V * nrhs;
+  const long long want = (total + 127) / 128;
+  const int grid = (int)(want < 16LL * amg_sm_count() ? want : 16LL * amg_sm_count());
+  const T mass = (T)(4.0 + h->p.m0);
+  if (y)
+    dirac_kernel<T, true><<<grid, 128, 0, st>>>((const C*)h->fU, (const C*)h->fC, (const C*)psi, (const C*)y, (C*)out,
+                                                 fine_geom(h), mass, nrhs);
+  else
+    dirac_kernel<T, false><<<grid, 128, 0, st>>>((const C*)h->fU, (const C*)h->fC, (const C*)psi, nullptr, (C*)out,
+                                                  fine_geom(h), mass, nrhs);
+  AMG_LAUNCH_CHECK();
+  h->launches++;
+  return AMG_OK;
+}
+
+amg_status dirac_any(amg_coarse* h, const void* psi, const void* y, void* out, int nrhs, cudaStream_t st) {
+  return fine_fp64(h) ? launch_dirac<double>(h, psi, y, out, nrhs, st) : launch_dirac<float>(h, psi, y, out, nrhs, st);
+}
+
+template <typename T>
+amg_status launch_sap(amg_coarse* h, const void* y, void* x, int nrhs, int n_cycles, int n_mr, cudaStream_t st) {
+  using C = typename Cx<T>::type;
+  const int threads = (h->g.Vb + 31) / 32 * 32;
+  const size_t smem = (size_t)h->g.Vb * 12 * sizeof(C) + (size_t)(threads / 32) * 3 * sizeof(double);
+  if (threads > 256 || smem > 227 * 1024) return AMG_ERR_UNSUPPORTED;
+  AMG_CUDA_TRY(cudaFuncSetAttribute(sap_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const dim3 grid((unsigned)(h->g.Vc / 2), (unsigned)nrhs);
+  const T mass = (T)(4.0 + h->p.m0);
+  for (int c = 0; c < n_cycles; ++c)
+    for (int colour = 0; colour < 2; ++colour) {
+      sap_kernel<T><<<grid, threads, smem, st>>>((const C*)h->fU, (const C*)h->fC, (const C*)y, (C*)x, fine_geom(h),
+                                                 mass, nrhs, colour, n_mr);
+      AMG_LAUNCH_CHECK();
+      h->launches++;
+    }
+  return AMG_OK;
+}
+
+amg_status sap_any(amg_coarse* h, const void* y, void* x, int nrhs, int n_cycles, int n_mr, cudaStream_t st) {
+  return fine_fp64(h) ? launch_sap<double>(h, y, x, nrhs, n_cycles, n_mr, st)
+                      : launch_sap<float>(h, y, x, nrhs, n_cycles, n_mr, st);
+}
+
+amg_status check_fine(amg_coarse* h, const void* a, const void* b, int nrhs) {
+  if (!h || !a || !b || !aligned16(a) || !aligned16(b)) return AMG_ERR_INVALID_ARG;
+  if (nrhs < 1 || nrhs > h->p.max_nrhs) return AMG_ERR_INVALID_ARG;
+  if (!h->fU) return AMG_ERR_UNSUPPORTED;  // amg_setup_fine not called
+  return AMG_OK;
+}
+
+bool sap_supported(const amg_coarse* h) {
+  for (int mu = 0; mu < 4; ++mu)
+    if (h->g.Lc[mu] % 2) return false;
+  return h->g.Vb <= 256;
+}
+
+amg_status check_vp(const amg_vcycle_params* vp) {
+  if (!vp || !(vp->coarse_tol >= 0) || vp->coarse_restart < 1 || vp->coarse_max_applies < 1 || vp->n_smoother < 0 ||
+      vp->n_mr < 1)
+    return AMG_ERR_INVALID_ARG;
+  return AMG_OK;
+}
+
+amg_status vcycle_impl(amg_coarse* h, const amg_vcycle_params* vp, const void* y, void* x, int nrhs,
+                       cudaStream_t st) {
+  AMG_TRY_INTERNAL(amg_cgc(h, y, x, nrhs, vp->coarse_tol, vp->coarse_restart, vp->coarse_max_applies, st, nullptr));
+  if (vp->n_smoother > 0) AMG_TRY_INTERNAL(sap_any(h, y, x, nrhs, vp->n_smoother, vp->n_mr, st));
+  return AMG_OK;
+}
+
+// ------------------------------------------------------------------ outer FGMRES (host-driven)
+// Right-preconditioned flexible GMRES(m) of Saad Alg. 9.6 from u = 0, every right-hand side
+// independently: classical Gram-Schmidt Arnoldi, Givens rotations, convergence on the implicit
+// residual |g_{j+1}| <= tol ||f||; every restart after the first recomputes the true residual
+// (one more application of D), as the coarse solve counts them.  Scalars live on the host: each
+// Arnoldi step synchronises once, which is small against the V-cycle it waits for.
+template <typename T>
+amg_status solve_impl(amg_coarse* h, const amg_vcycle_params* vp, const void* f, void* u, int nrhs, double tol,
+                      int m, int max_applies, cudaStream_t st, double* info) {
+  using C = typename Cx<T>::type;
+  const long long n = h->g.V * 12;
+  const long long vs = n * nrhs;  // elements of one multi-column vector
+  const size_t vbytes = (size_t)vs * sizeof(C);
+  // workspace: V_0..V_m, Z_0..Z_{m-1}, r, and (m + 1) x nrhs double2 + nrhs doubles of sums
+  const size_t need = (size_t)(2 * m + 2) * vbytes + ((size_t)(m + 1) * nrhs * 2 + nrhs) * sizeof(double) + 256;
+  if (need > h->fwork_bytes) {
+    AMG_CUDA_TRY(cudaStreamSynchronize(st));
+    cudaFree(h->fwork);
+    h->fwork = nullptr;
+    h->fwork_bytes = 0;
+    AMG_CUDA_TRY(cudaMalloc(&h->fwork, need));
+    h->fwork_bytes = need;
+  }
+  C* Vb = (C*)h->fwork;
+  C* Zb = Vb + (size_t)(m + 1) * vs;
+  C* R = Zb + (size_t)m * vs;
+  double2* dh = (double2*)(R + vs);
+  double* dn = (double*)(dh + (size_t)(m + 1) * nrhs);
+  C* U = (C*)u;
+  const int vgrid = 4 * amg_sm_count();
+  const dim3 fblk(FT);
+
+  auto colnorm = [&](const C* v, std::vector<double>& out) -> amg_status {
+    AMG_CUDA_TRY(cudaMemsetAsync(dn, 0, nrhs * sizeof(double), st));
+    fnorm_kernel<C><<<vgrid, fblk, 0, st>>>(v, n, nrhs, dn);
+    AMG_LAUNCH_CHECK();
+    h->launches++;
+    AMG_CUDA_TRY(cudaMemcpyAsync(out.data(), dn, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
+    AMG_CUDA_TRY(cudaStreamSynchronize(st));
+    for (auto& x : out) x = sqrt(x);
+    return AMG_OK;
+  };
+
+  std::vector<double> fnorm(nrhs), beta(nrhs), tmp(nrhs);
+  std::vector<int> applies(nrhs, 0), done(nrhs, 0);
+  std::vector<double> relres(nrhs, 1.0);
+  AMG_CUDA_TRY(cudaMemsetAsync(U, 0, vbytes, st));
+  AMG_CUDA_TRY(cudaMemcpyAsync(R, f, vbytes, cudaMemcpyDeviceToDevice, st));
+  AMG_TRY_INTERNAL(colnorm((const C*)f, fnorm));
+  for (int r = 0; r < nrhs; ++r)
+    if (fnorm[r] == 0) {
+      done[r] = 1;
+      relres[r] = 0;
+    }
+  int total_applies = 0;
+  const size_t hs = (size_t)(m + 1) * m;
+  std::vector<std::complex<double>> H(hs * nrhs), cs(m * nrhs), sn(m * nrhs), g((m + 1) * nrhs);
+  std::vector<double2> coef((m + 1) * nrhs);
+  while (true) {
+    AMG_TRY_INTERNAL(colnorm(R, beta));
+    bool any = false;
+    for (int r = 0; r < nrhs; ++r) {
+      if (!done[r] && beta[r] <= tol * fnorm[r]) done[r] = 1;
+      any = any || !done[r];
+    }
+    const int mm = std::min(m, max_applies - total_applies);
+    if (!any || mm <= 0) break;
+    // V_0 = r / beta (columns already converged get 0 and stay 0)
+    for (int r = 0; r < nrhs; ++r) coef[r] = make_double2(done[r] ? 0.0 : 1.0 / beta[r], 0.0);
+    AMG_CUDA_TRY(cudaMemcpyAsync(dh, coef.data(), nrhs * sizeof(double2), cudaMemcpyHostToDevice, st));
+    fscale_kernel<C><<<vgrid, fblk, 0, st>>>(R, Vb, dh, n, nrhs);
+    AMG_LAUNCH_CHECK();
+    h->launches++;
+    std::fill(H.begin(), H.end(), 0.0);
+    std::fill(g.begin(), g.end(), 0.0);
+    for (int r = 0; r < nrhs; ++r) g[r * (m + 1)] = beta[r];
+    std::vector<int> k(nrhs, 0), active(nrhs);
+    for (int r = 0; r < nrhs; ++r) active[r] = !done[r];
+    for (int j = 0; j < mm; ++j) {
+      C* Vj = Vb + (size_t)j * vs;
+      C* Zj = Zb + (size_t)j * vs;
+      C* W = Vb + (size_t)(j + 1) * vs;
+      AMG_TRY_INTERNAL(vcycle_impl(h, vp, Vj, Zj, nrhs, st));        // Z_j = M V_j
+      AMG_TRY_INTERNAL(dirac_any(h, Zj, nullptr, W, nrhs, st));      // w = D Z_j
+      total_applies++;
+      AMG_CUDA_TRY(cudaMemsetAsync(dh, 0, (size_t)(j + 1) * nrhs * sizeof(double2), st));
+      fdots_kernel<C><<<dim3(vgrid, j + 1), fblk, 0, st>>>(Vb, vs, j + 1, W, n, nrhs, dh);
+      AMG_LAUNCH_CHECK();
+      AMG_CUDA_TRY(cudaMemsetAsync(dn, 0, nrhs * sizeof(double), st));
+      fupdate_kernel<C><<<vgrid, fblk, 0, st>>>(Vb, vs, j + 1, dh, W, n, nrhs, dn);
+      AMG_LAUNCH_CHECK();
+      h->launches += 2;
+      std::vector<double2> hc((size_t)(j + 1) * nrhs);
+      AMG_CUDA_TRY(cudaMemcpyAsync(hc.data(), dh, hc.size() * sizeof(double2), cudaMemcpyDeviceToHost, st));
+      AMG_CUDA_TRY(cudaMemcpyAsync(tmp.data(), dn, nrhs * sizeof(double), cudaMemcpyDeviceToHost, st));
+      AMG_CUDA_TRY(cudaStreamSynchronize(st));
+      bool more = false;
+      for (int r = 0; r < nrhs; ++r) {
+        coef[r] = make_double2(0, 0);
+        if (!active[r]) continue;
+        applies[r]++;
+        std::complex<double>* Hr = H.data() + hs * r;  // Hr[i * m + j]
+        for (int i = 0; i <= j; ++i) Hr[i * m + j] = std::complex<double>(hc[i * nrhs + r].x, hc[i * nrhs + r].y);
+        const double hnext = sqrt(tmp[r]);
+        Hr[(j + 1) * m + j] = hnext;
+        std::complex<double>* c = cs.data() + (size_t)m * r;
+        std::complex<double>* s = sn.data() + (size_t)m * r;
+        std::complex<double>* gr = g.data() + (size_t)(m + 1) * r;
+        for (int i = 0; i < j; ++i) {
+          const std::complex<double> a = c[i] * Hr[i * m + j] + s[i] * Hr[(i + 1) * m + j];
+          Hr[(i + 1) * m + j] = -std::conj(s[i]) * Hr[i * m + j] + std::conj(c[i]) * Hr[(i + 1) * m + j];
+          Hr[i * m + j] = a;
+        }
+        const std::complex<double> a = Hr[j * m + j], b = Hr[(j + 1) * m + j];
+        const double den = sqrt(std::norm(a) + std::norm(b));
+        c[j] = std::conj(a) / den;
+        s[j] = std::conj(b) / den;
+        Hr[j * m + j] = den;
+        Hr[(j + 1) * m + j] = 0.0;
+        gr[j + 1] = -std::conj(s[j]) * gr[j];
+        gr[j] = c[j] * gr[j];
+        k[r] = j + 1;
+        relres[r] = std::abs(gr[j + 1]) / fnorm[r];
+        if (std::abs(gr[j + 1]) <= tol * fnorm[r] || hnext == 0) {
+          active[r] = 0;
+          done[r] = 1;
+        } else {
+          coef[r] = make_double2(1.0 / hnext, 0.0);
+          more = true;
+        }
+      }
+      if (!more) break;
+      // V_{j+1} = w / h_{j+1,j} (columns that stopped get 0 and drop out of later sums)
+      AMG_CUDA_TRY(cudaMemcpyAsync(dh, coef.data(), nrhs * sizeof(double2), cudaMemcpyHostToDevice, st));
+      AMG_CUDA_TRY(cudaStreamSynchronize(st));
+      fscale_kernel<C><<<vgrid, fblk, 0, st>>>(W, W, dh, n, nrhs);
+      AMG_LAUNCH_CHECK();
+      h->launches++;
+    }
+    // u += Z y, y from the k x k triangular systems
+    std::vector<double2> yv((size_t)m * nrhs, make_double2(0, 0));
+    int kmax = 0;
+    for (int r = 0; r < nrhs; ++r) {
+      const std::complex<double>* Hr = H.data() + hs * r;
+      const std::complex<double>* gr = g.data() + (size_t)(m + 1) * r;
+      std::vector<std::complex<double>> yy(k[r]);
+      for (int i = k[r] - 1; i >= 0; --i) {
+        std::complex<double> acc = gr[i];
+        for (int q = i + 1; q < k[r]; ++q) acc -= Hr[i * m + q] * yy[q];
+        yy[i] = acc / Hr[i * m + i];
+      }
+      for (int i = 0; i < k[r]; ++i) yv[i * nrhs + r] = make_double2(yy[i].real(), yy[i].imag());
+      kmax = std::max(kmax, k[r]);
+    }
+    if (kmax > 0) {
+      AMG_CUDA_TRY(cudaMemcpyAsync(dh, yv.data(), (size_t)kmax * nrhs * sizeof(double2), cudaMemcpyHostToDevice, st));
+      fcombine_kernel<C><<<vgrid, fblk, 0, st>>>(Zb, vs, kmax, dh, U, n, nrhs);
+      AMG_LAUNCH_CHECK();
+      h->launches++;
+    }
+    bool all = true;
+    for (int r = 0; r < nrhs; ++r) all = all && done[r];
+    if (all || total_applies >= max_applies) break;
+    // true residual r = f - D u
+    AMG_TRY_INTERNAL(dirac_any(h, u, f, R, nrhs, st));
+    total_applies++;
+    for (int r = 0; r < nrhs; ++r)
+      if (!done[r]) applies[r]++;
+  }
+  AMG_CUDA_TRY(cudaStreamSynchronize(st));
+  if (info)
+    for (int r = 0; r < nrhs; ++r) {
+      info[2 * r] = applies[r];
+      info[2 * r + 1] = relres[r];
+    }
+  return AMG_OK;
+}
+
+}  // namespace
+
+void amg_internal_free_fine(amg_coarse* h) {
+  cudaFree(h->fU);
+  if (h->fC != (void*)h->clover) cudaFree(h->fC);
+  cudaFree(h->fwork);
+  h->fU = h->fC = h->fwork = nullptr;
+  h->fwork_bytes = 0;
+}
+
+extern "C" {
+
+amg_status amg_setup_fine(amg_handle h, const void* d_U, void* stream) {
+  if (!h || !d_U || !aligned16(d_U)) return AMG_ERR_INVALID_ARG;
+  if (h->p.vec_prec != AMG_FP64 && h->p.vec_prec != AMG_FP32) return AMG_ERR_UNSUPPORTED;
+  cudaStream_t st = (cudaStream_t)stream;
+  h->last_stream = st;
+  amg_internal_free_fine(h);
+  const long long nU = h->g.V * 36, nC = h->g.V * 72;
+  if (fine_fp64(h)) {
+    AMG_CUDA_TRY(cudaMalloc(&h->fU, nU * sizeof(double2)));
+    AMG_CUDA_TRY(cudaMemcpyAsync(h->fU, d_U, nU * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    h->fC = h->clover;
+  } else {
+    AMG_CUDA_TRY(cudaMalloc(&h->fU, nU * sizeof(float2)));
+    AMG_CUDA_TRY(cudaMalloc(&h->fC, nC * sizeof(float2)));
+    to_prec_kernel<float><<<4 * amg_sm_count(), 256, 0, st>>>((const double2*)d_U, (float2*)h->fU, nU);
+    AMG_LAUNCH_CHECK();
+    to_prec_kernel<float><<<4 * amg_sm_count(), 256, 0, st>>>(h->clover, (float2*)h->fC, nC);
+    AMG_LAUNCH_CHECK();
+    h->launches += 2;
+  }
+  return AMG_OK;
+}
+
+amg_status amg_dirac_apply(amg_handle h, const void* d_psi, void* d_out, int nrhs, void* stream) {
+  AMG_TRY_INTERNAL(check_fine(h, d_psi, d_out, nrhs));
+  if (d_psi == d_out) return AMG_ERR_INVALID_ARG;
+  h->last_stream = (cudaStream_t)stream;
+  return dirac_any(h, d_psi, nullptr, d_out, nrhs, (cudaStream_t)stream);
+}
+
+amg_status amg_sap(amg_handle h, const void* d_y, void* d_x, int nrhs, int n_cycles, int n_mr, void* stream) {
+  AMG_TRY_INTERNAL(check_fine(h, d_y, d_x, nrhs));
+  if (d_y == d_x || n_cycles < 0 || n_mr < 1) return AMG_ERR_INVALID_ARG;
+  if (!sap_supported(h)) return AMG_ERR_UNSUPPORTED;
+  h->last_stream = (cudaStream_t)stream;
+  return sap_any(h, d_y, d_x, nrhs, n_cycles, n_mr, (cudaStream_t)stream);
+}
+
+amg_status amg_vcycle(amg_handle h, const amg_vcycle_params* vp, const void* d_y, void* d_x, int nrhs,
+                      void* stream) {
+  AMG_TRY_INTERNAL(check_fine(h, d_y, d_x, nrhs));
+  AMG_TRY_INTERNAL(check_vp(vp));
+  if (d_y == d_x) return AMG_ERR_INVALID_ARG;
+  if (!sap_supported(h)) return AMG_ERR_UNSUPPORTED;
+  h->last_stream = (cudaStream_t)stream;
+  return vcycle_impl(h, vp, d_y, d_x, nrhs, (cudaStream_t)stream);
+}
+
+amg_status amg_solve(amg_handle h, const amg_vcycle_params* vp, const void* d_f, void* d_u, int nrhs, double tol,
+                     int restart, int max_applies, void* stream, double* info) {
+  AMG_TRY_INTERNAL(check_fine(h, d_f, d_u, nrhs));
+  AMG_TRY_INTERNAL(check_vp(vp));
+  if (d_f == d_u || !(tol >= 0) || restart < 1 || restart > 64 || max_applies < 1) return AMG_ERR_INVALID_ARG;
+  if (!sap_supported(h)) return AMG_ERR_UNSUPPORTED;
+  cudaStream_t st = (cudaStream_t)stream;
+  h->last_stream = st;
+  return fine_fp64(h) ? solve_impl<double>(h, vp, d_f, d_u, nrhs, tol, restart, max_applies, st, info)
+                      : solve_impl<float>(h, vp, d_f, d_u, nrhs, tol, restart, max_applies, st, info);
+}
+
+}  // extern "C"

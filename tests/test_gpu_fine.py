@@ -1,0 +1,237 @@
+"""GPU parity of the two-level method around the coarse-grid correction.
+
+* amg_dirac_apply against oracle.dirac.apply_dirac (the Wilson-clover D): FP64 1e-12, FP32 1e-5;
+* amg_sap against oracle.smoother.sap (Alg. 3: SAP over two block colours, n_mr MR steps per block):
+  FP64 1e-10 after several cycles (the MR step lengths are ratios of sums, rounding is amplified
+  mildly), FP32 1e-5;
+* amg_vcycle against oracle.mg.Hierarchy.vcycle (Alg. 1: SAP started from the coarse-grid
+  correction of Alg. 2) with a fixed number of coarse FGMRES steps (coarse tolerance 0): FP64 1e-10;
+* amg_solve (Sec. 1: FGMRES right-preconditioned with the V-cycle) against oracle.mg.solve at a
+  fixed number of outer steps across a restart (FP64 1e-9), and to convergence by the oracle's true
+  residual ||f - D u|| / ||f||.
+Every right-hand side is independent: the oracle runs column by column.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import coarse, dirac, lattice as lat, mg, smoother  # noqa: E402
+from synth import inputs as si  # noqa: E402
+
+import helpers as H  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def amg():
+    import paper_1512_04506_gb300 as m
+    return m
+
+
+class Fine:
+    def __init__(self, amg, L, B, ntv, seed, prec, eps=0.3, max_nrhs=4):
+        self.amg, self.L, self.B, self.ntv, self.seed = amg, L, B, ntv, seed
+        self.V = int(np.prod(L))
+        self.Lc = lat.coarse_dims(L, B)
+        sites = si.all_sites(L)
+        self.Uh = si.links(seed, eps, sites)
+        self.tvh = si.test_vectors(seed, ntv, sites)
+        self.U = np.moveaxis(self.Uh.reshape(H.field_shape(L) + (4, 3, 3)), 4, 0)
+        self.C = dirac.clover_field(self.U, H.CSW)
+        pr = amg.AMG_FP64 if prec == "fp64" else amg.AMG_FP32
+        self.ctype = torch.complex128 if prec == "fp64" else torch.complex64
+        self.np_ctype = np.complex128 if prec == "fp64" else np.complex64
+        p = amg.make_params(L, B, ntv, max_nrhs, H.M0, H.CSW, pr, pr, pr)
+        self.stream = torch.cuda.current_stream()
+        Ud = torch.from_numpy(self.Uh).cuda()
+        self.h, _ = amg.amg_setup_coarse(p, Ud, torch.from_numpy(self.tvh).cuda(), self.stream)
+        amg.amg_setup_fine(self.h, Ud, self.stream)
+
+    def field(self, v):
+        """library vector (V, 4, 3) -> oracle field (t, z, y, x, 4, 3)"""
+        return v.reshape(H.field_shape(self.L) + (4, 3))
+
+    def vec(self, nrhs, off):
+        return si.fine_rhs(self.seed + off, nrhs, si.all_sites(self.L)).astype(self.np_ctype)
+
+    def dev(self, a):
+        return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+    def hierarchy(self, **kw):
+        hh = mg.Hierarchy(self.U, self.C, H.M0, self.L, self.B, **kw)
+        hh.build_coarse(self.tvh.reshape(H.field_shape(self.L) + (4, 3, self.ntv)))
+        return hh
+
+    def close(self):
+        self.amg.amg_destroy(self.h)
+
+
+@pytest.fixture(scope="module", params=[((8, 8, 8, 8), (4, 4, 4, 4), 8), ((8, 4, 4, 8), (2, 2, 2, 2), 6)],
+                ids=["8^4_b4", "8x4x4x8_b2"])
+def f64(amg, request):
+    L, B, ntv = request.param
+    c = Fine(amg, L, B, ntv, 707, "fp64")
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def f32(amg):
+    c = Fine(amg, (8, 8, 8, 8), (4, 4, 4, 4), 8, 708, "fp32")
+    yield c
+    c.close()
+
+
+def _dirac_cols(c, psi):
+    """oracle D applied to every column of a library vector (V, 4, 3, k)"""
+    out = np.empty(psi.shape, dtype=np.complex128)
+    for r in range(psi.shape[-1]):
+        out[..., r] = dirac.apply_dirac(c.U, c.C, H.M0, c.field(psi[..., r].astype(np.complex128))).reshape(
+            c.V, 4, 3)
+    return out
+
+
+@pytest.mark.parametrize("nrhs", [1, 3])
+def test_dirac_fp64(amg, f64, nrhs):
+    c = f64
+    psi = c.vec(nrhs, 1)
+    out = torch.empty_like(c.dev(psi))
+    amg.amg_dirac_apply(c.h, c.dev(psi), out, nrhs, c.stream)
+    assert H.rel(out.cpu().numpy(), _dirac_cols(c, psi)) < 1e-12
+    assert amg.amg_sync_status(c.h) == amg.AMG_OK
+
+
+def test_dirac_ragged_fp64(amg):
+    c = Fine(amg, (8, 4, 6, 4), (2, 2, 2, 2), 6, 709, "fp64")
+    try:
+        psi = c.vec(2, 1)
+        out = torch.empty_like(c.dev(psi))
+        amg.amg_dirac_apply(c.h, c.dev(psi), out, 2, c.stream)
+        assert H.rel(out.cpu().numpy(), _dirac_cols(c, psi)) < 1e-12
+        # coarse extents 4, 2, 3, 2: no two-colouring, so the smoother refuses
+        x = torch.zeros_like(out)
+        with pytest.raises(amg.AmgError) as e:
+            amg.amg_sap(c.h, c.dev(psi), x, 2, 1, 2, c.stream)
+        assert e.value.status == amg.AMG_ERR_UNSUPPORTED
+    finally:
+        c.close()
+
+
+@pytest.mark.parametrize("nrhs", [1, 4])
+def test_dirac_fp32(amg, f32, nrhs):
+    c = f32
+    psi = c.vec(nrhs, 2)
+    out = torch.empty_like(c.dev(psi))
+    amg.amg_dirac_apply(c.h, c.dev(psi), out, nrhs, c.stream)
+    ref = _dirac_cols(c, psi)
+    got = out.cpu().numpy().astype(np.complex128)
+    assert H.rel(got, ref) < 1e-5
+    assert np.abs(got - ref).max() < 1e-5 * np.abs(ref).max()
+
+
+def _sap_cols(c, y, x0, n_cycles, n_mr):
+    out = np.empty(y.shape, dtype=np.complex128)
+    for r in range(y.shape[-1]):
+        out[..., r] = smoother.sap(c.U, c.C, H.M0, c.field(y[..., r].astype(np.complex128)),
+                                   c.field(x0[..., r].astype(np.complex128)), c.B, n_cycles,
+                                   n_mr=n_mr).reshape(c.V, 4, 3)
+    return out
+
+
+@pytest.mark.parametrize("nrhs", [1, 2])
+def test_sap_fp64(amg, f64, nrhs):
+    c = f64
+    y, x0 = c.vec(nrhs, 3), c.vec(nrhs, 4)
+    x = c.dev(x0)
+    amg.amg_sap(c.h, c.dev(y), x, nrhs, 3, 4, c.stream)
+    ref = _sap_cols(c, y, x0, 3, 4)
+    assert H.rel(x.cpu().numpy(), ref) < 1e-10
+    # the smoother reduces the residual (it is a convergent iteration on this operator)
+    r0 = np.linalg.norm(y - _dirac_cols(c, x0).reshape(y.shape))
+    r3 = np.linalg.norm(y - _dirac_cols(c, ref).reshape(y.shape))
+    assert r3 < 0.5 * r0
+    assert amg.amg_sync_status(c.h) == amg.AMG_OK
+
+
+def test_sap_fp32(amg, f32):
+    c = f32
+    y, x0 = c.vec(2, 5), c.vec(2, 6)
+    x = c.dev(x0)
+    amg.amg_sap(c.h, c.dev(y), x, 2, 2, 3, c.stream)
+    ref = _sap_cols(c, y, x0, 2, 3)
+    assert H.rel(x.cpu().numpy().astype(np.complex128), ref) < 1e-5
+
+
+def test_vcycle_fp64(amg, f64):
+    """Fixed coarse work (tolerance 0, 5 applications of D_c) so that both sides take the same steps."""
+    c = f64
+    vp = amg.make_vcycle_params(coarse_tol=0.0, coarse_restart=30, coarse_max_applies=5, n_smoother=2, n_mr=3)
+    hh = c.hierarchy(n_smoother=2, n_mr=3, coarse_tol=0.0, coarse_restart=30, coarse_max_applies=5)
+    y = c.vec(1, 7)
+    x = torch.empty_like(c.dev(y))
+    amg.amg_vcycle(c.h, vp, c.dev(y), x, 1, c.stream)
+    ref = hh.vcycle(c.field(y[..., 0])).reshape(c.V, 4, 3)
+    assert H.rel(x.cpu().numpy()[..., 0], ref) < 1e-10
+    assert amg.amg_sync_status(c.h) == amg.AMG_OK
+
+
+def test_outer_solve_fixed_steps_fp64(amg, f64):
+    """Outer FGMRES(4) with 6 applications of D: one restart (true residual) inside; coarse solves
+    and smoothers at fixed work, so every step matches the oracle's."""
+    c = f64
+    vp = amg.make_vcycle_params(coarse_tol=0.0, coarse_restart=30, coarse_max_applies=4, n_smoother=2, n_mr=3)
+    hh = c.hierarchy(n_smoother=2, n_mr=3, coarse_tol=0.0, coarse_restart=30, coarse_max_applies=4)
+    f = c.vec(2, 8)
+    u = torch.empty_like(c.dev(f))
+    info = amg.amg_solve(c.h, vp, c.dev(f), u, 2, tol=0.0, restart=4, max_applies=6, stream=c.stream)
+    got = u.cpu().numpy()
+    for r in range(2):
+        ref, hist, n = mg.solve(hh, c.field(f[..., r]), tol=0.0, restart=4, max_applies=6)
+        assert info[r][0] == n == 6
+        assert H.rel(got[..., r], ref.reshape(c.V, 4, 3)) < 1e-9
+        assert info[r][1] == pytest.approx(hist[-1], rel=1e-6)
+
+
+def test_outer_solve_converges_fp64(amg, f64):
+    """To 1e-10 with the paper's coarse tolerance: the true residual from the oracle's D, and far
+    fewer applications of D than plain GMRES needs."""
+    c = f64
+    vp = amg.make_vcycle_params(coarse_tol=0.05, coarse_restart=30, coarse_max_applies=200, n_smoother=4, n_mr=4)
+    f = c.vec(1, 9)
+    u = torch.empty_like(c.dev(f))
+    info = amg.amg_solve(c.h, vp, c.dev(f), u, 1, tol=1e-10, restart=30, max_applies=200, stream=c.stream)
+    true = np.linalg.norm(f - _dirac_cols(c, u.cpu().numpy())) / np.linalg.norm(f)
+    assert info[0][1] <= 1e-10
+    assert true < 1e-9
+    assert info[0][0] < 60
+
+
+def test_outer_solve_fp32_reaches_single_precision(amg, f32):
+    c = f32
+    vp = amg.make_vcycle_params(coarse_tol=0.05, n_smoother=4, n_mr=4)
+    f = c.vec(2, 10)
+    u = torch.empty_like(c.dev(f))
+    info = amg.amg_solve(c.h, vp, c.dev(f), u, 2, tol=1e-5, restart=20, max_applies=100, stream=c.stream)
+    got = u.cpu().numpy().astype(np.complex128)
+    for r in range(2):
+        assert info[r][1] <= 1e-5
+        true = np.linalg.norm(f[..., r] - _dirac_cols(c, got[..., r:r + 1])[..., 0]) / np.linalg.norm(f[..., r])
+        assert true < 5e-5
+
+
+def test_fine_calls_need_setup_fine(amg):
+    L, B, ntv = (8, 8, 8, 8), (4, 4, 4, 4), 8
+    sites = si.all_sites(L)
+    p = amg.make_params(L, B, ntv, 1, H.M0, H.CSW, amg.AMG_FP64, amg.AMG_FP64, amg.AMG_FP64)
+    h, _ = amg.amg_setup_coarse(p, torch.from_numpy(si.links(1, 0.3, sites)).cuda(),
+                                torch.from_numpy(si.test_vectors(1, ntv, sites)).cuda())
+    try:
+        a = torch.zeros((int(np.prod(L)), 4, 3, 1), dtype=torch.complex128, device="cuda")
+        b = torch.empty_like(a)
+        with pytest.raises(amg.AmgError) as e:
+            amg.amg_dirac_apply(h, a, b, 1)
+        assert e.value.status == amg.AMG_ERR_UNSUPPORTED
+    finally:
+        amg.amg_destroy(h)
