@@ -338,14 +338,15 @@ def run_gpu(args):
     if rank == 0 and world == 1 and not args.no_workloads and not args.lattice:
         # the other workloads, each with its own step time, algorithmic bytes, roofline and clocks
         result["workloads"] = {name: sub_line(fn(args)) for name, fn in
-                               (("tc16", run_tc16), ("fp16", run_fp16), ("batch", run_batch))}
+                               (("tc16", run_tc16), ("fp16", run_fp16), ("batch", run_batch),
+                                ("vcycle", run_vcycle))}
     if dist:
         dist.destroy_process_group()
     return result, rank
 
 
 SUB_KEYS = ("value", "unit", "ms_per_step", "steps", "warmup", "dtype", "config", "roofline", "kernels",
-            "setup_ms", "clocks")
+            "setup_ms", "outer_solve", "clocks")
 
 
 def sub_line(res):
@@ -658,6 +659,77 @@ def _timed_steps(step, steps, warmup, stream, flush=None):
     return sum(a.elapsed_time(b) for a, b in ev) / 1000.0, clk.summary()
 
 
+def run_vcycle(args):
+    """The two-level method on the default workload's lattice (32^4, 4^4 blocks, Ntv = 20, FP32
+    vectors, FP32 R and D_c): one V-cycle (Alg. 1) = the coarse-grid correction (FGMRES(30) to 0.05)
+    followed by 4 SAP cycles (Alg. 3) of 4 MR steps per block; the fine Wilson-clover D on its own;
+    and the outer FGMRES(30) preconditioned with the V-cycle to relative residual 1e-5 (Sec. 1).
+
+    Algorithmic bytes (FP32 complex = 8 B) per fine site: D reads 4 links (288 B), the clover
+    (576 B), psi (96 B) and writes out (96 B) = 1056 B; one SAP half sweep reads, per site of its
+    colour, the links, the clover, y and x and writes x (1152 B), and reads x on the other colour's
+    sites once (96 B): 624 B per fine site of the lattice."""
+    import torch
+    import paper_1512_04506_gb300 as amg
+    from synth import device as sd
+    n_smoother, n_mr = 4, 4
+    V, Vb, Vc, nc = geometry()
+    st = torch.cuda.current_stream()
+    U = sd.links(SEED, EPS, L)
+    tv = sd.test_vectors(SEED, NTV, L)
+    p = amg.make_params(L, B, NTV, 1, M0, CSW, amg.AMG_FP32, amg.AMG_FP32, amg.AMG_FP32)
+    h, _ = amg.amg_setup_coarse(p, U, tv, st)
+    amg.amg_setup_fine(h, U, st)
+    del U, tv
+    torch.cuda.empty_cache()
+    vp = amg.make_vcycle_params(coarse_tol=TOL, coarse_restart=RESTART, coarse_max_applies=MAX_APPLIES,
+                                n_smoother=n_smoother, n_mr=n_mr)
+    y = sd.fine_rhs(SEED, 1, L, torch.complex64)
+    x = torch.empty_like(y)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    info = amg.amg_cgc(h, y, x, 1, TOL, RESTART, MAX_APPLIES, st, info=True)
+    applies = info[0][0]
+    t, clk = _timed_steps(lambda: amg.amg_vcycle(h, vp, y, x, 1, st), args.steps, args.warmup, st, flush)
+    t_d = _kernel_time(lambda: amg.amg_dirac_apply(h, y, x, 1, st), 20, st)
+    t_sap = _kernel_time(lambda: amg.amg_sap(h, y, x, 1, 1, n_mr, st), 10, st) / 2  # one half sweep
+    u = torch.empty_like(y)
+    t0 = time.perf_counter()
+    sinfo = amg.amg_solve(h, vp, y, u, 1, tol=1e-5, restart=30, max_applies=200, stream=st)
+    t_solve = time.perf_counter() - t0
+    status = amg.amg_sync_status(h)
+    amg.amg_destroy(h)
+    if status != amg.AMG_OK:
+        raise RuntimeError(amg.amg_status_string(status))
+    d_bytes = V * 1056
+    half_bytes = V * 624
+    cgc_bytes, _ = bytes_model(applies, arnoldi_iterations(applies))
+    step_bytes = cgc_bytes + 2 * n_smoother * half_bytes
+    peaks, src = measured_peaks()
+    d_gbs = d_bytes / t_d / 1e9
+    sap_gbs = half_bytes / t_sap / 1e9
+    ms = 1000 * t / args.steps
+    return {
+        "value": round(step_bytes * args.steps / t / 1e9, 2), "unit": "GB/s", "ms_per_step": round(ms, 4),
+        "steps": args.steps, "warmup": args.warmup, "dtype": "f32",
+        "config": {"workload": "vcycle_32^4_b4_ntv20: one V-cycle (Alg. 1) on the default workload: CGC "
+                               "(FGMRES(30) to 0.05) + %d SAP cycles of %d MR steps per 4^4 block; FP32" % (n_smoother, n_mr),
+                   "bytes_per_step": step_bytes, "coarse_applies": applies, "n_smoother": n_smoother, "n_mr": n_mr,
+                   "l2": "256 MB flush before each step"},
+        "roofline": {"bound": "hbm", "kernel": "sap_kernel<float> (one half sweep: residual + %d MR steps per block)"
+                     % n_mr, "achieved": round(sap_gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": round(sap_gbs / peaks["hbm_gbs"], 4), "peak_source": src, "traffic": None,
+                     "bytes_per_launch": half_bytes, "avg_launch_us": round(t_sap * 1e6, 2),
+                     "step_share": round(2 * n_smoother * t_sap / (t / args.steps), 3)},
+        "kernels": {"dirac": {"us": round(t_d * 1e6, 1), "GB/s": round(d_gbs, 1),
+                              "frac": round(d_gbs / peaks["hbm_gbs"], 4), "bytes_per_launch": d_bytes},
+                    "sap_half_sweep": {"us": round(t_sap * 1e6, 1), "GB/s": round(sap_gbs, 1),
+                                       "frac": round(sap_gbs / peaks["hbm_gbs"], 4)}},
+        "outer_solve": {"tol": 1e-5, "applies_of_D": sinfo[0][0], "relres": sinfo[0][1],
+                        "seconds": round(t_solve, 4), "restart": 30},
+        "clocks": clk,
+    }
+
+
 def run_tc16(args):
     """48^3 x 96, 4^4 blocks (12^3 x 24 coarse), Ntv = 24, 16 right-hand sides, BF16 tensor cores.
 
@@ -875,7 +947,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-speedup", action="store_true",
                     help="skip the batched-mixed vs plain FP32 coarse-solve comparison")
-    ap.add_argument("--workload", default="fp32", choices=["fp32", "tc16", "fp16", "batch"],
+    ap.add_argument("--workload", default="fp32", choices=["fp32", "tc16", "fp16", "batch", "vcycle"],
                     help="fp32: the default 32^4 workload; tc16: 48^3x96 with 16 RHS on the tensor cores; "
                          "fp16: 200 FP16 coarse applications at 32^3x64; batch: the uneven batch")
     ap.add_argument("--no-autotune", action="store_true",
@@ -904,6 +976,8 @@ def main():
         res, rank = run_fp16(args), 0
     elif args.workload == "batch":
         res, rank = run_batch(args), 0
+    elif args.workload == "vcycle":
+        res, rank = run_vcycle(args), 0
     else:
         res, rank = run_gpu(args)
     if rank == 0 and res is not None:

@@ -250,6 +250,22 @@ amg_status amg_vcycle(amg_handle h, const amg_vcycle_params *vp, const void *d_y
                       void *stream);
 
 /*
+ * amg_adaptive_setup -- the adaptive setup of Alg. 4 on this handle.  d_tv ([V][4][3][ntv] complex
+ * double, device) holds the random starting test vectors and receives the final ones; d_U is the
+ * link field of amg_setup_coarse (complex double, device).  Initial phase: every v_j becomes
+ * S_k(v_j; 0) for k = 1, 2, 3 in turn (k SAP cycles on right-hand side v_j from zero, vp->n_mr MR
+ * steps per block), R and D_c are rebuilt from them (Alg. 5), and every v_j is divided by its norm.
+ * Each of the n_setup passes then replaces every v_j by the V-cycle S(v_j; CGC(v_j)) with the
+ * current R and D_c and the parameters vp, and rebuilds R and D_c once all are replaced.  The
+ * vectors run through the smoother and the V-cycle in chunks of min(max_nrhs, 16) columns, in the
+ * handle's vector precision.  Every copy derived from R and D_c (tensor-core layouts) is rebuilt;
+ * even/odd data are dropped (call amg_setup_evenodd again).  Needs amg_setup_fine.  Synchronises
+ * the stream.  AMG_ERR_RANK_DEFICIENT if the smoothed vectors lose rank on an aggregate.
+ */
+amg_status amg_adaptive_setup(amg_handle h, const amg_vcycle_params *vp, const void *d_U, void *d_tv, int n_setup,
+                              void *stream);
+
+/*
  * amg_solve -- D u = f by restarted FGMRES(restart) right-preconditioned with the V-cycle (Sec. 1:
  * the two-level method as a preconditioner of a flexible Krylov solver), from u = 0, every
  * right-hand side independently: classical Gram-Schmidt, Givens rotations, stop when the implicit

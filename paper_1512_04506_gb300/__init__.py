@@ -84,6 +84,7 @@ _proto = {
     "amg_dirac_apply": [_vp, _vp, _vp, _i, _vp],
     "amg_sap": [_vp, _vp, _vp, _i, _i, _i, _vp],
     "amg_vcycle": [_vp, ctypes.POINTER(amg_vcycle_params), _vp, _vp, _i, _vp],
+    "amg_adaptive_setup": [_vp, ctypes.POINTER(amg_vcycle_params), _vp, _vp, _i, _vp],
     "amg_solve": [_vp, ctypes.POINTER(amg_vcycle_params), _vp, _vp, _i, _d, _i, _i, _vp, ctypes.POINTER(_d)],
     "amg_batch_cgc": [ctypes.POINTER(_vp), _i, ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                       ctypes.POINTER(_i), _vp],
@@ -252,6 +253,12 @@ def amg_sap(h, y, x, nrhs=1, n_cycles=1, n_mr=4, stream=None):
 
 def amg_vcycle(h, vp, y, x, nrhs=1, stream=None):
     return _check(lib.amg_vcycle(h, ctypes.byref(vp), ptr(y), ptr(x), nrhs, stream_ptr(stream)), "amg_vcycle")
+
+
+def amg_adaptive_setup(h, vp, U, tv, n_setup=1, stream=None, allow_rank_deficient=False):
+    allow = (AMG_ERR_RANK_DEFICIENT,) if allow_rank_deficient else ()
+    return _check(lib.amg_adaptive_setup(h, ctypes.byref(vp), ptr(U), ptr(tv), n_setup, stream_ptr(stream)),
+                  "amg_adaptive_setup", allow)
 
 
 def amg_solve(h, vp, f, u, nrhs=1, tol=1e-10, restart=30, max_applies=500, stream=None, info=True):

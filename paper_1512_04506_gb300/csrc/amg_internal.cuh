@@ -227,6 +227,9 @@ amg_status amg_internal_export_stored(amg_coarse* h, double2* out);
 amg_status amg_internal_tc_prepare(amg_coarse* h, cudaStream_t s);
 void amg_internal_free_tc(amg_coarse* h);
 void amg_internal_free_fine(amg_coarse* h);
+// Rebuilds R and D_c (and every copy derived from them) from new test vectors on an existing
+// handle: the setup of Alg. 5 again (api.cu); even/odd data are dropped (amg_setup_evenodd again).
+amg_status amg_internal_rebuild(amg_coarse* h, const double2* U, const double2* tv, cudaStream_t s);
 // Coarse application for the solver: CTAs return at once while *skip != 0; with xscale the input
 // is xc * xscale[r] and that scaled input is also stored to vout (both may be null).
 // Even/odd stencil piece (see eo_apply_kernel in stream.cu); parity of the output half.

@@ -250,6 +250,27 @@ amg_status amg_setup_coarse(const amg_params* p, const void* d_U, const void* d_
 #undef AMG_TRY_H
 }
 
+}  // extern "C"
+
+amg_status amg_internal_rebuild(amg_coarse* h, const double2* U, const double2* tv, cudaStream_t st) {
+  AMG_CUDA_TRY(cudaStreamSynchronize(st));
+  amg_internal_free_tc(h);
+  cudaFree(h->eo_site);
+  cudaFree(h->Dinv64);
+  cudaFree(h->Dinvq);
+  cudaFree(h->eo_tmp);
+  h->eo_site = nullptr;
+  h->Dinv64 = nullptr;
+  h->Dinvq = nullptr;
+  h->eo_tmp = nullptr;
+  h->eo_tmp_bytes = 0;
+  h->bw.sig = 0;  // a cached batch job list may hold the old tensor-core copies
+  AMG_CUDA_TRY(cudaMemsetAsync(h->err, 0, sizeof(unsigned), st));
+  return amg_internal_setup(h, U, tv, st);
+}
+
+extern "C" {
+
 amg_status amg_restrict(amg_handle h, const void* d_y, void* d_yc, int nrhs, void* stream) {
   AMG_TRY(check_apply_args(h, d_y, d_yc, nrhs));
   h->last_stream = (cudaStream_t)stream;

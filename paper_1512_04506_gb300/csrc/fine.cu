@@ -70,8 +70,8 @@ __device__ __forceinline__ void adagmul(int mu, C v0, C v1, C& o0, C& o1) {
 }
 
 // out += -1/2 (1 - g_mu) U p   (FWD) or   out += -1/2 (1 + g_mu) U^dag p   (!FWD); p, out: [spin][colour]
-template <bool FWD, typename C>
-__device__ __forceinline__ void hop(int mu, const C* __restrict__ U, const C p[12], C out[12]) {
+template <bool FWD, int mu, typename C>
+__device__ __forceinline__ void hop(const C* __restrict__ U, const C p[12], C out[12]) {
   C h[2][3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -147,16 +147,53 @@ __device__ __forceinline__ long long site_of(const FineGeom& g, const int x[4]) 
   return (((long long)x[3] * g.L[2] + x[2]) * g.L[1] + x[1]) * g.L[0] + x[0];
 }
 
-__device__ __forceinline__ long long shifted(const FineGeom& g, const int x[4], int mu, int dir) {
-  int y[4] = {x[0], x[1], x[2], x[3]};
-  y[mu] = (y[mu] + dir + g.L[mu]) % g.L[mu];
-  return site_of(g, y);
-}
-
 template <typename C>
 __device__ __forceinline__ void load12(const C* __restrict__ v, long long site, int nrhs, int r, C p[12]) {
+  if (nrhs == 1 && sizeof(C) == 8) {  // one column of FP32: six 16-byte loads
+    const float4* q = reinterpret_cast<const float4*>(v + site * 12);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const float4 f = __ldg(q + k);
+      p[2 * k].x = f.x;
+      p[2 * k].y = f.y;
+      p[2 * k + 1].x = f.z;
+      p[2 * k + 1].y = f.w;
+    }
+    return;
+  }
 #pragma unroll
   for (int k = 0; k < 12; ++k) p[k] = v[(site * 12 + k) * nrhs + r];
+}
+
+// site +- mu (periodic) from the coordinates of site s
+template <int mu, int dir>
+__device__ __forceinline__ long long nbr_site(const FineGeom& g, long long s, const int x[4]) {
+  long long st = 1;
+#pragma unroll
+  for (int k = 0; k < mu; ++k) st *= g.L[k];
+  if (dir > 0) return x[mu] + 1 < g.L[mu] ? s + st : s - st * (g.L[mu] - 1);
+  return x[mu] > 0 ? s - st : s + st * (g.L[mu] - 1);
+}
+
+// out += all 8 hops of D at site s (neighbour spinors from v)
+template <typename C>
+__device__ __forceinline__ void all_hops(const FineGeom& g, const C* __restrict__ U, const C* __restrict__ v,
+                                         long long s, const int x[4], int nrhs, int r, C o[12]) {
+  C p[12];
+#define AMG_HOPS(MU)                                      \
+  {                                                       \
+    const long long sf = nbr_site<MU, 1>(g, s, x);        \
+    load12(v, sf, nrhs, r, p);                            \
+    hop<true, MU>(U + (s * 4 + MU) * 9, p, o);            \
+    const long long sb = nbr_site<MU, -1>(g, s, x);       \
+    load12(v, sb, nrhs, r, p);                            \
+    hop<false, MU>(U + (sb * 4 + MU) * 9, p, o);          \
+  }
+  AMG_HOPS(0)
+  AMG_HOPS(1)
+  AMG_HOPS(2)
+  AMG_HOPS(3)
+#undef AMG_HOPS
 }
 
 // out = D psi (SUB: out = y - D psi), one thread per (site, right-hand side)
@@ -178,14 +215,7 @@ __global__ void __launch_bounds__(128) dirac_kernel(const typename Cx<T>::type* 
     C p[12], o[12];
     load12(psi, s, nrhs, r, p);
     site_term(Cl + s * 72, mass, p, o);
-#pragma unroll 1
-    for (int mu = 0; mu < 4; ++mu) {
-      const long long sf = shifted(g, x, mu, 1), sb = shifted(g, x, mu, -1);
-      load12(psi, sf, nrhs, r, p);
-      hop<true>(mu, U + (s * 4 + mu) * 9, p, o);
-      load12(psi, sb, nrhs, r, p);
-      hop<false>(mu, U + (sb * 4 + mu) * 9, p, o);
-    }
+    all_hops(g, U, psi, s, x, nrhs, r, o);
     if (SUB) {
       load12(y, s, nrhs, r, p);
 #pragma unroll
@@ -196,8 +226,10 @@ __global__ void __launch_bounds__(128) dirac_kernel(const typename Cx<T>::type* 
   }
 }
 
-// Block sum of three doubles over the CTA (all threads call it; every thread gets the sums).
-__device__ __forceinline__ void cta_sum3(double v[3], double* red) {
+// Block sum of three values over the CTA (all threads call it; every thread gets the sums).  The
+// warp sums run in the values' own precision, the CTA sum in FP64.
+template <typename T>
+__device__ __forceinline__ void cta_sum3(T v[3], double out[3], double* red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
 #pragma unroll
   for (int k = 0; k < 3; ++k)
@@ -205,18 +237,37 @@ __device__ __forceinline__ void cta_sum3(double v[3], double* red) {
     for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
   __syncthreads();  // red may still be read by the previous call
   if (lane == 0)
-    for (int k = 0; k < 3; ++k) red[warp * 3 + k] = v[k];
+    for (int k = 0; k < 3; ++k) red[warp * 3 + k] = (double)v[k];
   __syncthreads();
   for (int k = 0; k < 3; ++k) {
     double s = 0;
     for (int w = 0; w < nw; ++w) s += red[w * 3 + k];
-    v[k] = s;
+    out[k] = s;
+  }
+}
+
+// Intra-block hops of the block operator B at local site t: neighbours' rho from shared memory
+// (component-major: rho[q * Vb + t]), links from global memory.
+template <int mu, typename C>
+__device__ __forceinline__ void block_hops_mu(const FineGeom& g, const C* __restrict__ U, const C* rho, int t,
+                                              long long s, const int x[4], const int lc[4], int stride, C o[12]) {
+  C p[12];
+  if (lc[mu] + 1 < g.B[mu]) {
+#pragma unroll
+    for (int q = 0; q < 12; ++q) p[q] = rho[q * g.Vb + t + stride];
+    hop<true, mu>(U + (s * 4 + mu) * 9, p, o);
+  }
+  if (lc[mu] > 0) {
+#pragma unroll
+    for (int q = 0; q < 12; ++q) p[q] = rho[q * g.Vb + t - stride];
+    const long long sb = nbr_site<mu, -1>(g, s, x);
+    hop<false, mu>(U + (sb * 4 + mu) * 9, p, o);
   }
 }
 
 // One SAP half sweep on the blocks of one colour: x += MR_{n_mr}(B_b, (y - D x)|_b) per block.
 // grid (Vc / 2, nrhs); blockDim >= Vb (threads past Vb only join the sums); dynamic smem: rho
-// [Vb][12] + 3 doubles per warp.
+// [12][Vb] + 3 doubles per warp.
 template <typename T>
 __global__ void __launch_bounds__(256) sap_kernel(const typename Cx<T>::type* __restrict__ U,
                                                   const typename Cx<T>::type* __restrict__ Cl,
@@ -252,25 +303,18 @@ __global__ void __launch_bounds__(256) sap_kernel(const typename Cx<T>::type* __
     xs[3] = Tt * g.B[3] + lc[3];
     s = site_of(g, xs);
   }
-  const int stride[4] = {1, g.B[0], g.B[0] * g.B[1], g.B[0] * g.B[1] * g.B[2]};
+  const int st1 = g.B[0], st2 = g.B[0] * g.B[1], st3 = g.B[0] * g.B[1] * g.B[2];
   // residual r = y - D x on this site (full D: neighbours outside the block have the other colour)
-  C p[12], o[12], e[12];
+  C o[12], e[12];
   if (act) {
+    C p[12];
     load12(x, s, nrhs, r, p);
     site_term(Cl + s * 72, mass, p, o);
-#pragma unroll 1
-    for (int mu = 0; mu < 4; ++mu) {
-      const long long sf = shifted(g, xs, mu, 1), sb = shifted(g, xs, mu, -1);
-      load12(x, sf, nrhs, r, p);
-      hop<true>(mu, U + (s * 4 + mu) * 9, p, o);
-      load12(x, sb, nrhs, r, p);
-      hop<false>(mu, U + (sb * 4 + mu) * 9, p, o);
-    }
+    all_hops(g, U, x, s, xs, nrhs, r, o);
     load12(y, s, nrhs, r, p);
 #pragma unroll
     for (int q = 0; q < 12; ++q) {
-      const C rq = zsub(p[q], o[q]);
-      rho[t * 12 + q] = rq;
+      rho[q * g.Vb + t] = zsub(p[q], o[q]);
       e[q] = zzero<C>();
     }
   }
@@ -278,46 +322,35 @@ __global__ void __launch_bounds__(256) sap_kernel(const typename Cx<T>::type* __
 #pragma unroll 1
   for (int it = 0; it < n_mr; ++it) {
     // p = B rho at this site: site term plus the hops that stay inside the block
-    double v[3] = {0, 0, 0};
+    T v[3] = {0, 0, 0};
+    C rr[12];
     if (act) {
-      C rr[12];
 #pragma unroll
-      for (int q = 0; q < 12; ++q) rr[q] = rho[t * 12 + q];
+      for (int q = 0; q < 12; ++q) rr[q] = rho[q * g.Vb + t];
       site_term(Cl + s * 72, mass, rr, o);
-#pragma unroll 1
-      for (int mu = 0; mu < 4; ++mu) {
-        if (lc[mu] + 1 < g.B[mu]) {
-#pragma unroll
-          for (int q = 0; q < 12; ++q) p[q] = rho[(t + stride[mu]) * 12 + q];
-          hop<true>(mu, U + (s * 4 + mu) * 9, p, o);
-        }
-        if (lc[mu] > 0) {
-#pragma unroll
-          for (int q = 0; q < 12; ++q) p[q] = rho[(t - stride[mu]) * 12 + q];
-          const long long sb = shifted(g, xs, mu, -1);
-          hop<false>(mu, U + (sb * 4 + mu) * 9, p, o);
-        }
-      }
+      block_hops_mu<0>(g, U, rho, t, s, xs, lc, 1, o);
+      block_hops_mu<1>(g, U, rho, t, s, xs, lc, st1, o);
+      block_hops_mu<2>(g, U, rho, t, s, xs, lc, st2, o);
+      block_hops_mu<3>(g, U, rho, t, s, xs, lc, st3, o);
 #pragma unroll
       for (int q = 0; q < 12; ++q) {
-        v[0] += (double)o[q].x * o[q].x + (double)o[q].y * o[q].y;            // <p, p>
-        v[1] += (double)o[q].x * rr[q].x + (double)o[q].y * rr[q].y;          // Re <p, rho>
-        v[2] += (double)o[q].x * rr[q].y - (double)o[q].y * rr[q].x;          // Im <p, rho>
+        v[0] += o[q].x * o[q].x + o[q].y * o[q].y;        // <p, p>
+        v[1] += o[q].x * rr[q].x + o[q].y * rr[q].y;      // Re <p, rho>
+        v[2] += o[q].x * rr[q].y - o[q].y * rr[q].x;      // Im <p, rho>
       }
     }
-    cta_sum3(v, red);  // also orders every read of rho before the writes below
-    if (act && v[0] > 0) {
-      const double ar = v[1] / v[0], ai = v[2] / v[0];
+    double sums[3];
+    cta_sum3(v, sums, red);  // also orders every read of rho before the writes below
+    if (act && sums[0] > 0) {
       C al;
-      al.x = (T)ar;
-      al.y = (T)ai;
+      al.x = (T)(sums[1] / sums[0]);
+      al.y = (T)(sums[2] / sums[0]);
 #pragma unroll
       for (int q = 0; q < 12; ++q) {
-        const C rq = rho[t * 12 + q];
-        zfma(e[q], al, rq);
+        zfma(e[q], al, rr[q]);
         C ap = zzero<C>();
         zfma(ap, al, o[q]);
-        rho[t * 12 + q] = zsub(rq, ap);
+        rho[q * g.Vb + t] = zsub(rr[q], ap);
       }
     }
     __syncthreads();
@@ -726,6 +759,95 @@ amg_status solve_impl(amg_coarse* h, const amg_vcycle_params* vp, const void* f,
   return AMG_OK;
 }
 
+// Columns j0 .. j0 + nc - 1 of the FP64 test vectors tv ([V][12][ntv]) <-> a fine vector of nc
+// columns in the vector precision ([V][12][nc]).
+template <typename C>
+__global__ void tv_gather_kernel(const double2* __restrict__ tv, C* __restrict__ out, long long n12, int ntv, int j0,
+                                 int nc) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n12 * nc;
+       e += (long long)gridDim.x * blockDim.x) {
+    const double2 v = tv[(e / nc) * ntv + j0 + (int)(e % nc)];
+    C o;
+    o.x = v.x;
+    o.y = v.y;
+    out[e] = o;
+  }
+}
+
+template <typename C>
+__global__ void tv_scatter_kernel(const C* __restrict__ in, double2* __restrict__ tv, long long n12, int ntv, int j0,
+                                  int nc) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n12 * nc;
+       e += (long long)gridDim.x * blockDim.x)
+    tv[(e / nc) * ntv + j0 + (int)(e % nc)] = make_double2((double)in[e].x, (double)in[e].y);
+}
+
+// Alg. 4 on the handle: see amg_adaptive_setup in amg.h.  The test vectors go through the smoother
+// and the V-cycle in column chunks of at most min(max_nrhs, 16); R and D_c are rebuilt in place.
+template <typename T>
+amg_status adaptive_impl(amg_coarse* h, const amg_vcycle_params* vp, const double2* U, double2* tv, int n_setup,
+                         cudaStream_t st) {
+  using C = typename Cx<T>::type;
+  const int ntv = h->g.ntv;
+  const int chunk = std::min(h->p.max_nrhs, 16);
+  const long long n12 = h->g.V * 12;
+  const size_t vbytes = (size_t)n12 * chunk * sizeof(C);
+  void* buf = nullptr;
+  AMG_CUDA_TRY(cudaMallocAsync(&buf, 2 * vbytes + 256 + (size_t)ntv * (sizeof(double) + sizeof(double2)), st));
+  C* y = (C*)buf;
+  C* x = y + (size_t)n12 * chunk;
+  double* dn = (double*)(x + (size_t)n12 * chunk);
+  double2* dc = (double2*)(dn + ntv);
+  const int vgrid = 4 * amg_sm_count();
+  amg_status s = AMG_OK;
+  auto each_chunk = [&](auto&& body) -> amg_status {
+    for (int j0 = 0; j0 < ntv; j0 += chunk) {
+      const int nc = std::min(chunk, ntv - j0);
+      tv_gather_kernel<C><<<vgrid, 256, 0, st>>>(tv, y, n12, ntv, j0, nc);
+      AMG_LAUNCH_CHECK();
+      AMG_TRY_INTERNAL(body(nc));
+      tv_scatter_kernel<C><<<vgrid, 256, 0, st>>>(x, tv, n12, ntv, j0, nc);
+      AMG_LAUNCH_CHECK();
+      h->launches += 2;
+    }
+    return AMG_OK;
+  };
+  // initial phase: v <- S_k(v; 0), k = 1, 2, 3
+  s = each_chunk([&](int nc) -> amg_status {
+    for (int k = 1; k <= 3; ++k) {
+      AMG_CUDA_TRY(cudaMemsetAsync(x, 0, (size_t)n12 * nc * sizeof(C), st));
+      AMG_TRY_INTERNAL(sap_any(h, y, x, nc, k, vp->n_mr, st));
+      if (k < 3) AMG_CUDA_TRY(cudaMemcpyAsync(y, x, (size_t)n12 * nc * sizeof(C), cudaMemcpyDeviceToDevice, st));
+    }
+    return AMG_OK;
+  });
+  if (s == AMG_OK) s = amg_internal_rebuild(h, U, tv, st);
+  if (s == AMG_OK) {  // v_j <- v_j / ||v_j||
+    cudaMemsetAsync(dn, 0, ntv * sizeof(double), st);
+    fnorm_kernel<double2><<<vgrid, FT, 0, st>>>(tv, n12, ntv, dn);
+    std::vector<double> nrm(ntv);
+    cudaMemcpyAsync(nrm.data(), dn, ntv * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) s = AMG_ERR_CUDA;
+    std::vector<double2> inv(ntv);
+    for (int j = 0; j < ntv; ++j) inv[j] = make_double2(nrm[j] > 0 ? 1.0 / sqrt(nrm[j]) : 0.0, 0.0);
+    if (s == AMG_OK && cudaMemcpyAsync(dc, inv.data(), ntv * sizeof(double2), cudaMemcpyHostToDevice, st) != cudaSuccess)
+      s = AMG_ERR_CUDA;
+    if (s == AMG_OK) {
+      fscale_kernel<double2><<<vgrid, 256, 0, st>>>(tv, tv, dc, n12, ntv);
+      if (cudaGetLastError() != cudaSuccess) s = AMG_ERR_CUDA;
+      h->launches += 2;
+    }
+  }
+  // iterative passes: v_j <- S(v_j; CGC(v_j)) with the current R and D_c, then rebuild
+  for (int pass = 0; pass < n_setup && s == AMG_OK; ++pass) {
+    s = each_chunk([&](int nc) -> amg_status { return vcycle_impl(h, vp, y, x, nc, st); });
+    if (s == AMG_OK) s = amg_internal_rebuild(h, U, tv, st);
+  }
+  cudaFreeAsync(buf, st);
+  cudaStreamSynchronize(st);
+  return s;
+}
+
 }  // namespace
 
 void amg_internal_free_fine(amg_coarse* h) {
@@ -784,6 +906,18 @@ amg_status amg_vcycle(amg_handle h, const amg_vcycle_params* vp, const void* d_y
   if (!sap_supported(h)) return AMG_ERR_UNSUPPORTED;
   h->last_stream = (cudaStream_t)stream;
   return vcycle_impl(h, vp, d_y, d_x, nrhs, (cudaStream_t)stream);
+}
+
+amg_status amg_adaptive_setup(amg_handle h, const amg_vcycle_params* vp, const void* d_U, void* d_tv, int n_setup,
+                              void* stream) {
+  if (!h || !d_U || !d_tv || !aligned16(d_U) || !aligned16(d_tv) || n_setup < 0) return AMG_ERR_INVALID_ARG;
+  AMG_TRY_INTERNAL(check_vp(vp));
+  if (!h->fU) return AMG_ERR_UNSUPPORTED;
+  if (!sap_supported(h)) return AMG_ERR_UNSUPPORTED;
+  cudaStream_t st = (cudaStream_t)stream;
+  h->last_stream = st;
+  return fine_fp64(h) ? adaptive_impl<double>(h, vp, (const double2*)d_U, (double2*)d_tv, n_setup, st)
+                      : adaptive_impl<float>(h, vp, (const double2*)d_U, (double2*)d_tv, n_setup, st);
 }
 
 amg_status amg_solve(amg_handle h, const amg_vcycle_params* vp, const void* d_f, void* d_u, int nrhs, double tol,

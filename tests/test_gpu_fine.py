@@ -31,8 +31,8 @@ def amg():
 
 
 class Fine:
-    def __init__(self, amg, L, B, ntv, seed, prec, eps=0.3, max_nrhs=4):
-        self.amg, self.L, self.B, self.ntv, self.seed = amg, L, B, ntv, seed
+    def __init__(self, amg, L, B, ntv, seed, prec, eps=0.3, max_nrhs=4, m0=H.M0):
+        self.amg, self.L, self.B, self.ntv, self.seed, self.m0 = amg, L, B, ntv, seed, m0
         self.V = int(np.prod(L))
         self.Lc = lat.coarse_dims(L, B)
         sites = si.all_sites(L)
@@ -43,7 +43,7 @@ class Fine:
         pr = amg.AMG_FP64 if prec == "fp64" else amg.AMG_FP32
         self.ctype = torch.complex128 if prec == "fp64" else torch.complex64
         self.np_ctype = np.complex128 if prec == "fp64" else np.complex64
-        p = amg.make_params(L, B, ntv, max_nrhs, H.M0, H.CSW, pr, pr, pr)
+        p = amg.make_params(L, B, ntv, max_nrhs, m0, H.CSW, pr, pr, pr)
         self.stream = torch.cuda.current_stream()
         Ud = torch.from_numpy(self.Uh).cuda()
         self.h, _ = amg.amg_setup_coarse(p, Ud, torch.from_numpy(self.tvh).cuda(), self.stream)
@@ -88,7 +88,7 @@ def _dirac_cols(c, psi):
     """oracle D applied to every column of a library vector (V, 4, 3, k)"""
     out = np.empty(psi.shape, dtype=np.complex128)
     for r in range(psi.shape[-1]):
-        out[..., r] = dirac.apply_dirac(c.U, c.C, H.M0, c.field(psi[..., r].astype(np.complex128))).reshape(
+        out[..., r] = dirac.apply_dirac(c.U, c.C, c.m0, c.field(psi[..., r].astype(np.complex128))).reshape(
             c.V, 4, 3)
     return out
 
@@ -235,3 +235,51 @@ def test_fine_calls_need_setup_fine(amg):
         assert e.value.status == amg.AMG_ERR_UNSUPPORTED
     finally:
         amg.amg_destroy(h)
+
+
+def test_adaptive_setup_fp64_matches_oracle(amg):
+    """Alg. 4 with one iterative pass, fixed coarse work and smoother: the final test vectors, R and
+    D_c equal the oracle's (oracle.mg.setup, pinned step by step against dense propagators)."""
+    c = Fine(amg, (8, 8, 8, 8), (4, 4, 4, 4), 8, 711, "fp64")
+    try:
+        vp = amg.make_vcycle_params(coarse_tol=0.0, coarse_restart=30, coarse_max_applies=4, n_smoother=2, n_mr=3)
+        hh = mg.Hierarchy(c.U, c.C, H.M0, c.L, c.B, n_smoother=2, n_mr=3, coarse_tol=0.0, coarse_restart=30,
+                          coarse_max_applies=4)
+        tv0 = c.tvh.reshape(H.field_shape(c.L) + (4, 3, c.ntv))
+        want = mg.setup(hh, tv0, 1)
+        tv = torch.from_numpy(c.tvh).cuda()
+        amg.amg_adaptive_setup(c.h, vp, torch.from_numpy(c.Uh).cuda(), tv, 1, c.stream)
+        assert H.rel(tv.cpu().numpy(), want.reshape(c.tvh.shape)) < 1e-9
+        Vc = int(np.prod(c.Lc))
+        Dc = torch.empty((Vc, 9, 2 * c.ntv, 2 * c.ntv), dtype=torch.complex128, device="cuda")
+        amg.amg_export_Dc(c.h, Dc)
+        assert H.rel(Dc.cpu().numpy(), hh.Dc) < 1e-9
+        R = torch.empty((Vc, 2, c.ntv, 6 * 256), dtype=torch.complex128, device="cuda")
+        amg.amg_export_R(c.h, R)
+        assert H.rel(R.cpu().numpy(), H.q_to_lib_R(hh.Q)) < 1e-9
+        assert amg.amg_sync_status(c.h) == amg.AMG_OK
+    finally:
+        c.close()
+
+
+def test_adaptive_setup_speeds_up_the_solve(amg):
+    """The point of Alg. 4: the test vectors it leaves make the V-cycle-preconditioned solve need
+    fewer applications of D than the random ones.  On a rough field with a light mass (eps = 0.6,
+    m0 = -0.6) the oracle (oracle.mg.setup with two passes, then oracle.mg.solve to 1e-5) goes
+    from 12 to 10 applications; on the smooth eps = 0.3, m0 = -0.3 field it gains nothing (24 -> 26
+    in the oracle), so this input is the rough one.  FP64 handle, the paper's coarse tolerance."""
+    c = Fine(amg, (8, 8, 8, 8), (4, 4, 4, 4), 8, 712, "fp64", eps=0.6, m0=-0.6)
+    try:
+        vp = amg.make_vcycle_params(coarse_tol=0.05, n_smoother=3, n_mr=3)
+        f = si.fine_rhs(723, 1, si.all_sites(c.L))
+        u = torch.empty_like(c.dev(f))
+        before = amg.amg_solve(c.h, vp, c.dev(f), u, 1, tol=1e-5, restart=30, max_applies=300, stream=c.stream)
+        tv = torch.from_numpy(c.tvh).cuda()
+        amg.amg_adaptive_setup(c.h, vp, torch.from_numpy(c.Uh).cuda(), tv, 2, c.stream)
+        after = amg.amg_solve(c.h, vp, c.dev(f), u, 1, tol=1e-5, restart=30, max_applies=300, stream=c.stream)
+        assert after[0][1] <= 1e-5
+        true = np.linalg.norm(f - _dirac_cols(c, u.cpu().numpy())) / np.linalg.norm(f)
+        assert true < 2e-5
+        assert after[0][0] < before[0][0], (before, after)
+    finally:
+        c.close()
