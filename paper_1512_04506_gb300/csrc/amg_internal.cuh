@@ -154,6 +154,11 @@ struct amg_coarse {
   size_t tmp_bytes = 0;
   unsigned long long launches = 0;  // kernels launched through this handle (host-side count)
   int grid_cap = 0;           // test hook: most CTAs of a grid-stride launch (0: occupancy x SMs)
+  void* tc5_x = nullptr;      // tcgen05 apply (FP32 / FP16 storage, 4-16 columns): coarse rows,
+  size_t tc5_xbytes = 0;
+  float* tc5_xs = nullptr;    // their power-of-two scale per site,
+  float* tc5_ds = nullptr;    // the power-of-two scale of every FP32 stencil block,
+  void* tc5_d16 = nullptr;    // and the FP16 storage as planes with rotated pieces
   void* fU = nullptr;         // fine operator (amg_setup_fine): links [V][4][3][3] in vec_prec
   void* fC = nullptr;         // clover [V][2][6][6] in vec_prec (aliases clover for FP64)
   void* fwork = nullptr;      // outer FGMRES workspace (fine Krylov basis, Z vectors, sums)
@@ -249,6 +254,13 @@ amg_status amg_internal_solve_op(amg_coarse* h, long long rows, amg_apply_fn op,
 // FP32 D_c, nrhs = 4, 8, 12 or 16: tensor cores with split TF32 operands (tc.cu)
 amg_status amg_internal_apply_tf32(amg_coarse* h, const void* xc, void* yc, int nrhs, cudaStream_t s,
                                    const int* skip, const double* xscale, void* vout);
+// FP32 or FP16-scaled storage, 1 <= nrhs <= 16, nc % 8 == 0, nc <= 56: tcgen05 with FP16 split
+// operands (tc5.cu); prepare allocates its storage at setup, free releases it.
+bool amg_internal_tc5_supported(const amg_coarse* h);
+amg_status amg_internal_tc5_prepare(amg_coarse* h, cudaStream_t s);
+void amg_internal_free_tc5(amg_coarse* h);
+amg_status amg_internal_apply_tc5(amg_coarse* h, const void* xc, void* yc, int nrhs, cudaStream_t s,
+                                  const int* skip, const double* xscale, void* vout);
 amg_status amg_internal_apply_ex(amg_coarse* h, const void* xc, void* yc, int nrhs, cudaStream_t s,
                                  const int* skip, const double* xscale, void* vout);
 // Tensor-core (BF16) forms for nrhs = 4, 8, 12, 16.

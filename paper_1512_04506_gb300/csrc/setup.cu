@@ -656,7 +656,8 @@ amg_status amg_internal_setup(amg_coarse* h, const double2* U, const double2* tv
       r_to_fp32_kernel<<<1216, 256, 0, st>>>(h->R64, (float2*)h->Rq, n);
       AMG_LAUNCH_CHECK();
     }
-    if (h->p.link_prec == AMG_BF16 || h->p.r_prec == AMG_BF16 || (h->p.link_prec == AMG_FP32 && h->p.max_nrhs >= 4)) {
+    if (h->p.link_prec == AMG_BF16 || h->p.r_prec == AMG_BF16 ||
+        ((h->p.link_prec == AMG_FP32 || h->p.link_prec == AMG_FP16_SCALED) && h->p.max_nrhs >= 4)) {
       amg_status s = amg_internal_tc_prepare(h, st);
       if (s != AMG_OK) return s;
     }

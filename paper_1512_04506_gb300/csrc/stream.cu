@@ -1295,13 +1295,15 @@ amg_status amg_internal_apply_ex(amg_coarse* h, const void* xc, void* yc, int nr
       return apply_prec<double2>(h, (const double2*)h->Dq, nullptr, xc, yc, nrhs, s, skip, xscale, vout);
     case AMG_FP32:
       if (h->p.vec_prec == AMG_FP64) return AMG_ERR_UNSUPPORTED;
-      // 4..16 columns: one pass on the tensor cores with split-TF32 operands (measured faster than
-      // the one-pass SIMT kernel for FP32 storage)
+      // 4..16 columns: one pass on the tensor cores, tcgen05 with FP16 split operands up to nc = 56,
+      // mma.sync with split-TF32 operands beyond (both measured faster than the one-pass SIMT kernel)
+      if (h->tc5_x && nrhs >= 4 && nrhs <= 16) return amg_internal_apply_tc5(h, xc, yc, nrhs, s, skip, xscale, vout);
       if (h->Dtf && (nrhs == 4 || nrhs == 8 || nrhs == 12 || nrhs == 16))
         return amg_internal_apply_tf32(h, xc, yc, nrhs, s, skip, xscale, vout);
       return apply_prec<float2>(h, (const float2*)h->Dq, nullptr, xc, yc, nrhs, s, skip, xscale, vout);
     case AMG_FP16_SCALED:
       if (h->p.vec_prec == AMG_FP64) return AMG_ERR_UNSUPPORTED;
+      if (h->tc5_x && nrhs >= 4 && nrhs <= 16) return amg_internal_apply_tc5(h, xc, yc, nrhs, s, skip, xscale, vout);
       return apply_prec<__half2>(h, (const __half2*)h->Dq, h->Dscale, xc, yc, nrhs, s, skip, xscale, vout);
     case AMG_BF16:
       return amg_internal_apply_tc(h, xc, yc, nrhs, s, skip, xscale, vout);

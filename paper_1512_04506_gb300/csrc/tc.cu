@@ -264,8 +264,8 @@ amg_status amg_internal_tc_prepare(amg_coarse* h, cudaStream_t st) {
     AMG_CUDA_TRY(cudaMalloc(&h->tc_x, h->tc_xbytes));
   }
   if (h->p.link_prec == AMG_FP32 && h->p.vec_prec == AMG_FP32 && h->g.nc % 8 == 0 && h->g.nc <= 64 &&
-      h->p.max_nrhs >= 4) {
-    // FP32 D_c for the multi-RHS tensor-core apply (3 x TF32)
+      h->p.max_nrhs >= 4 && !amg_internal_tc5_supported(h)) {
+    // FP32 D_c for the multi-RHS tensor-core apply (3 x TF32) where the tcgen05 form does not fit
     const size_t n = (size_t)h->g.Vc * 9 * 2 * h->g.nc * h->g.nc;
     AMG_CUDA_TRY(cudaMalloc(&h->Dtf, n * sizeof(float)));
     dc_to_tf32_kernel<<<4 * amg_sm_count(), 256, 0, st>>>(h->Dc64, (float*)h->Dtf, h->g.nc, h->g.Vc * 9);
@@ -274,6 +274,7 @@ amg_status amg_internal_tc_prepare(amg_coarse* h, cudaStream_t st) {
     h->tf_xbytes = (size_t)h->g.Vc * h->g.nc * tf32_xpitch(nmax) * 4;
     AMG_CUDA_TRY(cudaMalloc(&h->tf_x, h->tf_xbytes));
   }
+  if (h->p.max_nrhs >= 4 && amg_internal_tc5_supported(h)) AMG_TRY_INTERNAL(amg_internal_tc5_prepare(h, st));
   if (h->p.r_prec == AMG_BF16) {
     const Geom& g = h->g;
     if (g.ntv % 4 || g.Vb % 8) return AMG_ERR_UNSUPPORTED;
@@ -286,6 +287,7 @@ amg_status amg_internal_tc_prepare(amg_coarse* h, cudaStream_t st) {
 }
 
 void amg_internal_free_tc(amg_coarse* h) {
+  amg_internal_free_tc5(h);
   cudaFree(h->Dtc);
   cudaFree(h->Rtc);
   cudaFree(h->tc_x);
