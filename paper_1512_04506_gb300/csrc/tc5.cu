@@ -80,6 +80,17 @@ __device__ inline void tc5_mma(uint32_t d, uint32_t a, uint64_t bdesc, uint32_t 
       "r"(a), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
+__device__ inline void tc5_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+      "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
+        "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+        "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr)
+      : "memory");
+}
 __device__ inline void tc5_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 __device__ inline void tc5_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ inline void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -94,9 +105,9 @@ __device__ inline uint64_t tc5_desc(const void* p, uint32_t lbo, uint32_t sbo) {
   d |= (uint64_t)1 << 46;
   return d;
 }
-// Instruction descriptor of kind::f16: FP32 accumulator, FP16 A and B, both K-major, N = 32, M = 128.
-__host__ __device__ constexpr uint32_t tc5_idesc() {
-  return (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(32 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+// Instruction descriptor of kind::f16: FP32 accumulator, FP16 A and B, both K-major, N, M = 128.
+__host__ __device__ constexpr uint32_t tc5_idesc(int n) {
+  return (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 }
 
 __device__ inline bool t5_wait(uint64_t* bar, unsigned parity, Pipe* pp, unsigned* err) {
@@ -152,9 +163,9 @@ struct T5Args {
 // (accumulators first, from column 0; A stages from column 32 NACC).  More accumulators let the
 // MMAs run further ahead of the epilogue, whose reads wait for a commit each.
 __host__ __device__ constexpr int t5_aw(int nc, bool f32) { return f32 ? 2 * nc : nc; }
-__host__ __device__ constexpr int t5_nst(int nc, bool f32) { return 4 * t5_aw(nc, f32) + 4 * 32 <= 512 ? 4 : 3; }
+__host__ __device__ constexpr int t5_nst(int nc, bool f32) { return 4 * t5_aw(nc, f32) + 2 * 64 <= 512 ? 4 : 3; }
 __host__ __device__ constexpr int t5_nacc(int nc, bool f32) {
-  return (512 - t5_nst(nc, f32) * t5_aw(nc, f32)) / 32 >= 8 ? 8 : (512 - t5_nst(nc, f32) * t5_aw(nc, f32)) / 32 >= 4 ? 4 : 2;
+  return (512 - t5_nst(nc, f32) * t5_aw(nc, f32)) / 64 >= 4 ? 4 : (512 - t5_nst(nc, f32) * t5_aw(nc, f32)) / 64 >= 3 ? 3 : 2;
 }
 
 // Bytes of one B buffer (hi or lo): 32 / 8 column groups x (2 nc / 8) core matrices x 128 bytes.
@@ -185,7 +196,7 @@ __global__ void __launch_bounds__(kT5Threads, 1) apply_tc5_kernel(const T5Args a
   constexpr int NST = t5_nst(NC, F32), NACC = t5_nacc(NC, F32);
   static_assert(NST <= kT5MaxStages && NACC <= kT5MaxAcc, "tensor-memory plan");
   constexpr uint32_t AW = (uint32_t)t5_aw(NC, F32);  // tensor-memory columns per A stage
-  constexpr uint32_t kAcc = 0, kA = 32u * NACC;
+  constexpr uint32_t kAcc = 0, kA = 64u * NACC;
   static_assert(kA + NST * AW <= 512, "tensor-memory columns");
   const int XP = 2 * nrhs + (nrhs % 8 == 0 ? 8 : 0);      // tf32_xpitch(nrhs)
   const unsigned xbytes = (unsigned)(NC * XP * 4);
@@ -248,7 +259,7 @@ __global__ void __launch_bounds__(kT5Threads, 1) apply_tc5_kernel(const T5Args a
   } else if (warp == 19) {
     // ---------------------------------------------------------------- MMA issue
     if (lane == 0) {
-      constexpr uint32_t idesc = tc5_idesc();
+      constexpr uint32_t idesc64 = tc5_idesc(64), idesc32 = tc5_idesc(32);
       long long blk = 0;
       bool ok = true;
       for (long long i = i0; i < Vc && ok && !pp->abort; i += step) {
@@ -264,17 +275,15 @@ __global__ void __launch_bounds__(kT5Threads, 1) apply_tc5_kernel(const T5Args a
             break;
           }
           tc5_fence_after();
-          const uint32_t acc = tmem + kAcc + (uint32_t)(buf * 32);
+          const uint32_t acc = tmem + kAcc + (uint32_t)(buf * 64);
           const uint32_t ahi = tmem + kA + (uint32_t)st * AW, alo = ahi + (uint32_t)NC;
-          const unsigned char* bhi = bbuf + (size_t)(2 * st) * bbytes;
-          const unsigned char* blo = bhi + bbytes;
+          const unsigned char* bhi = bbuf + (size_t)(2 * st) * bbytes;  // B_lo follows at 4 SBO: N = 64 covers both
 #pragma unroll
           for (int ks = 0; ks < K / 16; ++ks) {
-            const uint64_t dh = tc5_desc(bhi + ks * 256, 128u, SBO);
-            const uint64_t dl = tc5_desc(blo + ks * 256, 128u, SBO);
-            tc5_mma(acc, ahi + 8 * ks, dh, idesc, ks > 0 ? 1u : 0u);
-            tc5_mma(acc, ahi + 8 * ks, dl, idesc, 1u);
-            if (F32) tc5_mma(acc, alo + 8 * ks, dh, idesc, 1u);
+            const uint64_t db = tc5_desc(bhi + ks * 256, 128u, SBO);
+            // columns 0-31: A_hi B_hi (+ A_lo B_hi), columns 32-63: A_hi B_lo
+            tc5_mma(acc, ahi + 8 * ks, db, idesc64, ks > 0 ? 1u : 0u);
+            if (F32) tc5_mma(acc, alo + 8 * ks, db, idesc32, 1u);
           }
           tc5_commit(&tb->afree[st]);
           tc5_commit(&tb->accfull[buf]);
@@ -311,22 +320,16 @@ __global__ void __launch_bounds__(kT5Threads, 1) apply_tc5_kernel(const T5Args a
         }
         tc5_fence_after();
         uint32_t v[32];
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
-            "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-              "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]),
-              "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
-              "=r"(v[30]), "=r"(v[31])
-            : "r"(tmem + lane_off + kAcc + (uint32_t)(buf * 32))
-            : "memory");
-        tc5_wait_ld();
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {  // columns 0-31, then 32-63 (the A_hi B_lo part)
+          tc5_ld32(tmem + lane_off + kAcc + (uint32_t)(buf * 64 + 32 * half), v);
+          tc5_wait_ld();
+#pragma unroll
+          for (int c = 0; c < 32; ++c) sum[c] = fmaf(__uint_as_float(v[c]), sc, sum[c]);
+        }
         tc5_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&tb->accempty[buf]);
-#pragma unroll
-        for (int c = 0; c < 32; ++c) sum[c] = fmaf(__uint_as_float(v[c]), sc, sum[c]);
       }
       if (ok && q < NC) {
         float2* dst = a.y + (i * NC + q) * nrhs;
