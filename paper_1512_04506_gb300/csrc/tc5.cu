@@ -11,9 +11,10 @@
 // coarse site, so that every scaled entry lies below 2^15 and FP16 holds it.  The FP16 operands are
 // split: x' = x_hi + x_lo (both FP16, 22 significant bits together); for FP32 storage also
 // D' = D_hi + D_lo with s_D a power of two (exact scaling), split once at setup and kept in HBM as
-// FP16 hi and lo planes (the bytes of FP32), and the product is accumulated as
-// A_hi B_hi + A_hi B_lo + A_lo B_hi; FP16 storage already is the FP16 A and takes A B_hi + A B_lo.
-// Instructions: tcgen05.mma kind::f16, M = 128 (nc rows used), N = 32, K = 16.
+// FP16 hi and lo planes (the bytes of FP32).  One instruction per K step, tcgen05.mma kind::f16,
+// M = 128, N = 64 over [B_hi | B_lo]: FP16 storage gives [A B_hi | A B_lo] in rows 0 .. nc - 1;
+// FP32 storage stacks A_hi (rows 0 ..) and A_lo (rows 64 ..) and gives all four products, of which
+// A_lo B_lo (below FP32 rounding) is kept as well.
 //
 // Operands.  The streamed D_c is A and lives in tensor memory (two FP16 per column): with N = 32 an
 // A operand in shared memory would be fetched again for every instruction.  A warps (lane
@@ -26,14 +27,16 @@
 // instructions that cost about 1e-5 relative.  The A stages let the builders, the accumulator ring
 // the MMAs run ahead.
 //
-// Tensor-memory columns (512 allocated, one CTA per SM): 2, 4 or 8 accumulators of 32 columns, then
-// 3 or 4 A stages (FP32 storage: A_hi and A_lo, nc columns each; FP16: A, nc columns), nc <= 56.
+// Tensor-memory columns (512 allocated, one CTA per SM): 3 or 4 accumulators of 64 columns, then 4 A
+// stages of nc columns (FP32 storage: A_hi in lanes 0 .. nc - 1, A_lo in lanes 64 .., so that one
+// M = 128 instruction multiplies both), nc <= 56.
 //
-// Roles (640 threads): warps 0-15 write the operands in two groups of eight (w / 8) that take
+// Roles (704 threads): warps 0-15 write the operands in two groups of eight (w / 8) that take
 // alternate blocks, so that two blocks are prepared at once; in a group, warps with w % 4 < 2 copy
-// the A rows of their lane quadrant and plane, the others write B; warps 16, 17 (quadrants 0, 1)
-// read, scale and sum the block products and store y; warp 18 lane 0 issues the bulk copies;
-// warp 19 allocates tensor memory and lane 0 issues the MMAs.  Every wait is bounded; a wait that runs out raises the CTA's abort flag and sets the
+// the A_hi rows of their lane quadrant and plane, the others write B and (FP32 storage) copy the
+// A_lo rows; warps 16-19 (quadrants 0-3) read, scale and sum the block products, the A_lo rows'
+// sums handed to the A_hi rows' warps through shared memory once per site, and store y; warp 20
+// lane 0 issues the bulk copies; warp 21 allocates tensor memory and lane 0 issues the MMAs.  Every wait is bounded; a wait that runs out raises the CTA's abort flag and sets the
 // timeout bit of the error word, after which every role leaves its loop, the MMA thread waits
 // (bounded) for its last commit, and tensor memory is freed.
 #include "tc_body.cuh"
@@ -41,7 +44,7 @@
 namespace {
 using namespace amgtc;
 
-constexpr int kT5Threads = 640;  // 16 builder warps, 2 epilogue warps, the copy warp, the MMA warp
+constexpr int kT5Threads = 704;  // 16 builder warps, 4 epilogue warps, the copy warp, the MMA warp
 constexpr int kT5Cols = 512;       // tensor-memory columns allocated
 
 constexpr int kT5MaxStages = 4;  // A stages / B buffers
@@ -50,7 +53,8 @@ struct T5Bars {
   uint64_t aready[kT5MaxStages];  // A stage and B buffer written (the 8 builder warps)
   uint64_t afree[kT5MaxStages];   // the MMAs that read them completed (tcgen05.commit)
   uint64_t accfull[kT5MaxAcc];    // a block's product complete (tcgen05.commit)
-  uint64_t accempty[kT5MaxAcc];   // the epilogue has read it (2 epilogue warps)
+  uint64_t accempty[kT5MaxAcc];   // the epilogue has read it (the epilogue warps)
+  uint64_t xfull, xempty;         // FP32 storage: the lo rows' site sums handed to the hi rows' warps
   uint64_t done;                  // final commit of the MMA thread
   uint32_t tmem_base;
 };
@@ -159,14 +163,11 @@ struct T5Args {
   Geom g;
 };
 
-// Tensor-memory plan: columns per A stage, A stages and 32-column accumulators within 512 columns
-// (accumulators first, from column 0; A stages from column 32 NACC).  More accumulators let the
-// MMAs run further ahead of the epilogue, whose reads wait for a commit each.
-__host__ __device__ constexpr int t5_aw(int nc, bool f32) { return f32 ? 2 * nc : nc; }
-__host__ __device__ constexpr int t5_nst(int nc, bool f32) { return 4 * t5_aw(nc, f32) + 2 * 64 <= 512 ? 4 : 3; }
-__host__ __device__ constexpr int t5_nacc(int nc, bool f32) {
-  return (512 - t5_nst(nc, f32) * t5_aw(nc, f32)) / 64 >= 4 ? 4 : (512 - t5_nst(nc, f32) * t5_aw(nc, f32)) / 64 >= 3 ? 3 : 2;
-}
+// Tensor-memory plan: A stages of nc columns (FP32 storage: A_hi in lanes 0 .. nc - 1 and A_lo in
+// lanes 64 .. 64 + nc - 1 of the same columns, so that one M = 128 instruction covers both) and
+// 64-column accumulators within 512 columns (accumulators first, A stages from column 64 NACC).
+__host__ __device__ constexpr int t5_nst(int nc) { return 4; }
+__host__ __device__ constexpr int t5_nacc(int nc) { return (512 - 4 * nc) / 64 >= 4 ? 4 : 3; }
 
 // Bytes of one B buffer (hi or lo): 32 / 8 column groups x (2 nc / 8) core matrices x 128 bytes.
 __host__ __device__ inline unsigned t5_bbytes(int nc) { return 4u * (unsigned)(2 * nc / 8) * 128u; }
@@ -193,10 +194,11 @@ __global__ void __launch_bounds__(kT5Threads, 1) apply_tc5_kernel(const T5Args a
   constexpr unsigned bbytes = 4u * (unsigned)(K / 8) * 128u;
   constexpr unsigned SBO = (unsigned)(K / 8) * 128u;  // N-adjacent core matrices
   constexpr unsigned dbytes = (unsigned)((F32 ? 8 : 4) * NC * NC);
-  constexpr int NST = t5_nst(NC, F32), NACC = t5_nacc(NC, F32);
+  constexpr int NST = t5_nst(NC), NACC = t5_nacc(NC);
   static_assert(NST <= kT5MaxStages && NACC <= kT5MaxAcc, "tensor-memory plan");
-  constexpr uint32_t AW = (uint32_t)t5_aw(NC, F32);  // tensor-memory columns per A stage
+  constexpr uint32_t AW = (uint32_t)NC;  // tensor-memory columns per A stage
   constexpr uint32_t kAcc = 0, kA = 64u * NACC;
+  constexpr int EPI = F32 ? 4 : 2;       // epilogue warps (lane quadrants 0 .. EPI - 1)
   static_assert(kA + NST * AW <= 512, "tensor-memory columns");
   const int XP = 2 * nrhs + (nrhs % 8 == 0 ? 8 : 0);      // tf32_xpitch(nrhs)
   const unsigned xbytes = (unsigned)(NC * XP * 4);
@@ -204,7 +206,8 @@ __global__ void __launch_bounds__(kT5Threads, 1) apply_tc5_kernel(const T5Args a
   Pipe* pp = reinterpret_cast<Pipe*>(sm);
   T5Bars* tb = reinterpret_cast<T5Bars*>(sm + kPipeBytes);
   unsigned char* bbuf = sm + kPipeBytes + kT5BarBytes;  // B buffers [stage][hi, lo]
-  unsigned char* stages = bbuf + 2 * kT5MaxStages * (size_t)bbytes;
+  float* xb = reinterpret_cast<float*>(bbuf + 2 * kT5MaxStages * (size_t)bbytes);  // [nc][32] lo-row sums
+  unsigned char* stages = bbuf + 2 * kT5MaxStages * (size_t)bbytes + (size_t)NC * 32 * sizeof(float);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   ring_init(pp, ns, 8);
   if (threadIdx.x == 0) {
@@ -214,12 +217,14 @@ __global__ void __launch_bounds__(kT5Threads, 1) apply_tc5_kernel(const T5Args a
     }
     for (int k = 0; k < NACC; ++k) {
       mbar_init(&tb->accfull[k], 1);
-      mbar_init(&tb->accempty[k], 2);
+      mbar_init(&tb->accempty[k], EPI);
     }
+    mbar_init(&tb->xfull, 2);
+    mbar_init(&tb->xempty, 2);
     mbar_init(&tb->done, 1);
     fence_mbar_init();
   }
-  if (warp == 19) tc5_alloc(&tb->tmem_base);
+  if (warp == 21) tc5_alloc(&tb->tmem_base);
   tc5_fence_before();
   __syncthreads();
   tc5_fence_after();
@@ -227,7 +232,7 @@ __global__ void __launch_bounds__(kT5Threads, 1) apply_tc5_kernel(const T5Args a
   const Ring rg{pp, stages, ns, dbytes + xbytes};
   const long long i0 = blockIdx.x, step = gridDim.x, Vc = a.g.Vc;
 
-  if (warp == 18) {
+  if (warp == 20) {
     // ---------------------------------------------------------------- bulk copies
     if (lane == 0) {
       RingPos rp;
@@ -256,10 +261,10 @@ __global__ void __launch_bounds__(kT5Threads, 1) apply_tc5_kernel(const T5Args a
       }
       drain(pp, rp.c, ns);
     }
-  } else if (warp == 19) {
+  } else if (warp == 21) {
     // ---------------------------------------------------------------- MMA issue
     if (lane == 0) {
-      constexpr uint32_t idesc64 = tc5_idesc(64), idesc32 = tc5_idesc(32);
+      constexpr uint32_t idesc64 = tc5_idesc(64);
       long long blk = 0;
       bool ok = true;
       for (long long i = i0; i < Vc && ok && !pp->abort; i += step) {
@@ -276,14 +281,12 @@ __global__ void __launch_bounds__(kT5Threads, 1) apply_tc5_kernel(const T5Args a
           }
           tc5_fence_after();
           const uint32_t acc = tmem + kAcc + (uint32_t)(buf * 64);
-          const uint32_t ahi = tmem + kA + (uint32_t)st * AW, alo = ahi + (uint32_t)NC;
+          const uint32_t aa = tmem + kA + (uint32_t)st * AW;
           const unsigned char* bhi = bbuf + (size_t)(2 * st) * bbytes;  // B_lo follows at 4 SBO: N = 64 covers both
 #pragma unroll
           for (int ks = 0; ks < K / 16; ++ks) {
-            const uint64_t db = tc5_desc(bhi + ks * 256, 128u, SBO);
-            // columns 0-31: A_hi B_hi (+ A_lo B_hi), columns 32-63: A_hi B_lo
-            tc5_mma(acc, ahi + 8 * ks, db, idesc64, ks > 0 ? 1u : 0u);
-            if (F32) tc5_mma(acc, alo + 8 * ks, db, idesc32, 1u);
+            // rows 0 .. nc - 1: [A_hi B_hi | A_hi B_lo]; FP32 rows 64 ..: [A_lo B_hi | A_lo B_lo]
+            tc5_mma(acc, aa + 8 * ks, tc5_desc(bhi + ks * 256, 128u, SBO), idesc64, ks > 0 ? 1u : 0u);
           }
           tc5_commit(&tb->afree[st]);
           tc5_commit(&tb->accfull[buf]);
@@ -297,45 +300,75 @@ __global__ void __launch_bounds__(kT5Threads, 1) apply_tc5_kernel(const T5Args a
     }
   } else if (warp >= 16) {
     // ---------------------------------------------------------------- epilogue
-    // lane q = output row q: each block's product (real parts in accumulator columns 0-15,
-    // imaginary parts in 16-31) times s_D s_x, summed in FP32 registers, stored as (re, im) pairs
-    const int q = 32 * (warp - 16) + lane;
-    const uint32_t lane_off = (uint32_t)(32 * (warp - 16)) << 16;
-    long long blk = 0;
-    bool ok = true;
-    float nd, nx;
-    site_scales(a, i0, lane, nd, nx);
-    for (long long i = i0; i < Vc && ok; i += step) {
-      const float sc_site = nd * nx;
-      site_scales(a, i + step, lane, nd, nx);
-      float sum[32];
+    // warp 16 + u reads lane quadrant u: row 32 u + lane for u < 2 (the A_hi rows), row 32 (u - 2) +
+    // lane of the A_lo rows for u >= 2 (FP32 storage).  Each block's two 32-column halves times
+    // s_D s_x are summed over the site in FP32 registers; at the end of a site the A_lo warps hand
+    // their sums to the A_hi warps through shared memory, which add them and store (re, im) pairs.
+    const int u = warp - 16;
+    if (u < EPI) {
+      const bool lo_rows = u >= 2;
+      const int q = 32 * (u & 1) + lane;
+      const uint32_t lane_off = (uint32_t)(32 * u) << 16;
+      long long blk = 0, site = 0;
+      bool ok = true;
+      float nd, nx;
+      site_scales(a, i0, lane, nd, nx);
+      for (long long i = i0; i < Vc && ok; i += step, ++site) {
+        const float sc_site = nd * nx;
+        site_scales(a, i + step, lane, nd, nx);
+        float sum[32];
 #pragma unroll
-      for (int c = 0; c < 32; ++c) sum[c] = 0.f;
-      for (int d = 0; d < 9; ++d, ++blk) {
-        const int buf = (int)(blk % NACC);
-        const float sc = __shfl_sync(0xffffffffu, sc_site, d);
-        if (!__all_sync(0xffffffffu, t5_wait(&tb->accfull[buf], (unsigned)((blk / NACC) & 1), pp, a.err))) {
-          ok = false;
-          break;
+        for (int c = 0; c < 32; ++c) sum[c] = 0.f;
+        for (int d = 0; d < 9; ++d, ++blk) {
+          const int buf = (int)(blk % NACC);
+          const float sc = __shfl_sync(0xffffffffu, sc_site, d);
+          if (!__all_sync(0xffffffffu, t5_wait(&tb->accfull[buf], (unsigned)((blk / NACC) & 1), pp, a.err))) {
+            ok = false;
+            break;
+          }
+          tc5_fence_after();
+          uint32_t v[32];
+#pragma unroll
+          for (int half = 0; half < 2; ++half) {  // columns 0-31 (x B_hi), then 32-63 (x B_lo)
+            tc5_ld32(tmem + lane_off + kAcc + (uint32_t)(buf * 64 + 32 * half), v);
+            tc5_wait_ld();
+#pragma unroll
+            for (int c = 0; c < 32; ++c) sum[c] = fmaf(__uint_as_float(v[c]), sc, sum[c]);
+          }
+          tc5_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&tb->accempty[buf]);
         }
-        tc5_fence_after();
-        uint32_t v[32];
+        if (!ok) break;
+        if (F32) {
+          if (lo_rows) {
+            if (site > 0 && !__all_sync(0xffffffffu, t5_wait(&tb->xempty, (unsigned)((site - 1) & 1), pp, a.err))) {
+              ok = false;
+              break;
+            }
+            if (q < NC)
 #pragma unroll
-        for (int half = 0; half < 2; ++half) {  // columns 0-31, then 32-63 (the A_hi B_lo part)
-          tc5_ld32(tmem + lane_off + kAcc + (uint32_t)(buf * 64 + 32 * half), v);
-          tc5_wait_ld();
+              for (int c = 0; c < 32; ++c) xb[q * 32 + c] = sum[c];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tb->xfull);
+            continue;
+          }
+          if (!__all_sync(0xffffffffu, t5_wait(&tb->xfull, (unsigned)(site & 1), pp, a.err))) {
+            ok = false;
+            break;
+          }
+          if (q < NC)
 #pragma unroll
-          for (int c = 0; c < 32; ++c) sum[c] = fmaf(__uint_as_float(v[c]), sc, sum[c]);
+            for (int c = 0; c < 32; ++c) sum[c] += xb[q * 32 + c];
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&tb->xempty);
         }
-        tc5_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&tb->accempty[buf]);
-      }
-      if (ok && q < NC) {
-        float2* dst = a.y + (i * NC + q) * nrhs;
+        if (q < NC) {
+          float2* dst = a.y + (i * NC + q) * nrhs;
 #pragma unroll
-        for (int c = 0; c < 16; ++c)
-          if (c < nrhs) dst[c] = make_float2(sum[c], sum[16 + c]);
+          for (int c = 0; c < 16; ++c)
+            if (c < nrhs) dst[c] = make_float2(sum[c], sum[16 + c]);
+        }
       }
     }
   } else {
@@ -343,12 +376,15 @@ __global__ void __launch_bounds__(kT5Threads, 1) apply_tc5_kernel(const T5Args a
     // Two groups (w / 8) take alternate blocks.  In a group, A warps (w % 4 < 2): row q = lane of
     // quadrant w % 4, plane (w / 4) % 2; B warps (w % 4 >= 2): threads 0 .. 127 of the B operand.
     const int grp = warp >> 3;
-    const bool awarp = (warp & 3) < 2;
+    const bool awarp = (warp & 3) < 2;    // A_hi rows (quadrants 0, 1); the others write B and, for FP32
+                                          // storage, the A_lo rows (quadrants 2, 3: lanes 64 + q)
+    const bool arow = awarp || F32;
     const int plane = (warp >> 2) & 1;  // 0 = Re, 1 = Im
-    const int q = 32 * (warp & 3) + lane;
-    const bool row_ok = awarp && q < NC;
+    const int q = 32 * (warp & 1) + lane;
+    const bool row_ok = arow && q < NC;
     const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
     const int rot = row_ok ? tc_rot(q, P) : 0;
+    const size_t lo_off = awarp ? 0 : (size_t)2 * NC * NC * 2;  // the lo planes follow the hi planes
     const int bt = (((warp >> 2) & 1) * 2 + (warp & 3) - 2) * 32 + lane;  // B warps: 0 .. 127
     bool ok = true;
     long long blk = 0;
@@ -376,31 +412,24 @@ __global__ void __launch_bounds__(kT5Threads, 1) apply_tc5_kernel(const T5Args a
         }
         tc5_fence_after();
         const unsigned char* Ds = ring_stage(rg, rp);
-        if (awarp) {
-          // row q of plane `plane`: K columns NC plane .., two FP16 per column; one 16-byte piece =
-          // 8 elements = 4 columns, hi (and lo) copied as stored
-          const unsigned char* rowp = Ds + ((size_t)plane * NC * NC + (size_t)(row_ok ? q : 0) * NC) * 2;
+        if (arow) {
+          // row q of plane `plane` (hi, or lo for the quadrant 2, 3 warps): K columns NC plane ..,
+          // two FP16 per column; one 16-byte piece = 8 elements = 4 columns, copied as stored
+          const unsigned char* rowp = Ds + lo_off + ((size_t)plane * NC * NC + (size_t)(row_ok ? q : 0) * NC) * 2;
           const uint32_t acol = tmem + lane_off + kA + (uint32_t)st * AW + (uint32_t)(plane * NC / 2);
 #pragma unroll
           for (int pc = 0; pc < P; ++pc) {
             int pos = pc + rot;
             pos = pos >= P ? pos - P : pos;
-            uint4 f = make_uint4(0u, 0u, 0u, 0u), g2 = make_uint4(0u, 0u, 0u, 0u);
-            if (row_ok) {
-              f = *reinterpret_cast<const uint4*>(rowp + pos * 16);
-              if (F32) g2 = *reinterpret_cast<const uint4*>(rowp + (size_t)2 * NC * NC * 2 + pos * 16);
-            }
+            uint4 f = make_uint4(0u, 0u, 0u, 0u);
+            if (row_ok) f = *reinterpret_cast<const uint4*>(rowp + pos * 16);
             asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(acol + (uint32_t)(4 * pc)),
                          "r"(f.x), "r"(f.y), "r"(f.z), "r"(f.w)
                          : "memory");
-            if (F32)
-              asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(
-                               acol + (uint32_t)(NC + 4 * pc)),
-                           "r"(g2.x), "r"(g2.y), "r"(g2.z), "r"(g2.w)
-                           : "memory");
           }
           tc5_wait_st();
-        } else {
+        }
+        if (!awarp) {
           // B (K x 32): column n < 16 = real part of right-hand side n, 16 + n its imaginary part;
           // B = [[x_re, x_im], [-x_im, x_re]]' of the neighbour, split into FP16 hi + lo.  A thread
           // takes rows kk, kk + 1 (kk even) of one right-hand side m: two (re, im) loads, packed
@@ -444,7 +473,7 @@ __global__ void __launch_bounds__(kT5Threads, 1) apply_tc5_kernel(const T5Args a
   tc5_fence_before();
   __syncthreads();
   tc5_fence_after();
-  if (warp == 19) tc5_dealloc(tmem);
+  if (warp == 21) tc5_dealloc(tmem);
 }
 
 // FP32 coarse vector x (times xscale[r]; the scaled vector also to vout) -> FP32 rows of
@@ -540,7 +569,7 @@ __global__ void dq16_to_planes_kernel(const __half2* __restrict__ Dq, __half* __
 
 // Shared memory of the tcgen05 apply with ns ring stages.
 static size_t tc5_smem(int nc, bool f32, int nrhs, int ns) {
-  return kPipeBytes + kT5BarBytes + 2 * kT5MaxStages * (size_t)t5_bbytes(nc) +
+  return kPipeBytes + kT5BarBytes + 2 * kT5MaxStages * (size_t)t5_bbytes(nc) + (size_t)nc * 32 * sizeof(float) +
          (size_t)ns * (t5_dbytes(nc, f32) + t5_xbytes(nc, nrhs));
 }
 
@@ -594,8 +623,8 @@ static amg_status launch_tc5(amg_coarse* h, const void* x, void* y, int nrhs, cu
   AMG_LAUNCH_CHECK();
   h->launches++;
   const size_t stage = t5_dbytes(NC, F32) + t5_xbytes(NC, nrhs);
-  // the ring takes what is left of 200 KB: one CTA per SM (it holds all 512 tensor-memory columns)
-  int ns = (int)((200 * 1024 - tc5_smem(NC, F32, nrhs, 0)) / stage);
+  // the ring takes what is left of 224 KB: one CTA per SM (it holds all 512 tensor-memory columns)
+  int ns = (int)((224 * 1024 - tc5_smem(NC, F32, nrhs, 0)) / stage);
   ns = ns < 2 ? 2 : (ns > kMaxStages ? kMaxStages : ns);
   // an even depth: block b uses stage b % ns, so every stage then belongs to one of the two builder
   // groups (b % 2) and is consumed in order.  With an odd depth a stage alternates between the
