@@ -49,6 +49,9 @@ TC16_KERNELS = {"restrict": "restrict_tc_kernel<16> (Y_c = R Y, BF16 R, 16 RHS)"
 # DRAM bytes of one FP16 coarse application at 32^3 x 64, Ntv = 24 (ncu capture of the full size,
 # profiles/apply_mrhs_fp16_32x3x64_ntv24.md)
 TRAFFIC_FP16_APPLY = 692893440
+# DRAM bytes of one FP32 16-column tcgen05 apply at 32^3 x 64, Ntv = 24: the 16^3 x 32 capture
+# (profiles/apply_tc5_fp32_16x3x32_ntv24_nrhs16.md, 91,356.4 KB for 512 sites) x 16 sites
+TRAFFIC_MRHS_FP32 = 1461702400
 # DRAM traffic / algorithmic bytes of the fused batch launch, from the reduced-volume capture
 # (profiles/batch_kernel_small_mixed.md); the full launch's traffic is taken in that proportion
 BATCH_TRAFFIC_RATIO = 0.990
@@ -338,8 +341,8 @@ def run_gpu(args):
     if rank == 0 and world == 1 and not args.no_workloads and not args.lattice:
         # the other workloads, each with its own step time, algorithmic bytes, roofline and clocks
         result["workloads"] = {name: sub_line(fn(args)) for name, fn in
-                               (("tc16", run_tc16), ("fp16", run_fp16), ("batch", run_batch),
-                                ("vcycle", run_vcycle))}
+                               (("tc16", run_tc16), ("fp16", run_fp16), ("mrhs", run_mrhs),
+                                ("batch", run_batch), ("vcycle", run_vcycle))}
     if dist:
         dist.destroy_process_group()
     return result, rank
@@ -730,6 +733,60 @@ def run_vcycle(args):
     }
 
 
+def run_mrhs(args):
+    """Coarse applications with many right-hand sides at 32^3 x 64, 4^4 blocks (8^3 x 16 coarse
+    sites), Ntv = 24: FP32 D_c and FP16 D_c with block scales, 16 and 4 columns, one pass on the
+    tensor cores (tcgen05).  Algorithmic bytes: D_c once (FP32: 8 B per complex entry; FP16: 4 B
+    plus one FP32 scale per block) and the input and output coarse vectors (FP32)."""
+    import torch
+    import paper_1512_04506_gb300 as amg
+    from synth import device as sd
+    Lt, ntv, seed = (32, 32, 32, 64), 24, 20151204 + 3
+    if args.lattice:
+        Lt = tuple(int(v) for v in args.lattice.split(","))
+    Vc = int(np.prod(Lt)) // int(np.prod(B))
+    nc = 2 * ntv
+    st = torch.cuda.current_stream()
+    peaks, src = measured_peaks()
+    kern, t_total, bytes_total, steps = {}, 0.0, 0, 0
+    clk = None
+    for name, link, eb, extra in (("fp32", amg.AMG_FP32, 8, 0), ("fp16", amg.AMG_FP16_SCALED, 4, Vc * 9 * 4)):
+        U = sd.links(seed, EPS, Lt)
+        tv = sd.test_vectors(seed, ntv, Lt)
+        h, _ = amg.amg_setup_coarse(amg.make_params(Lt, B, ntv, 16, M0, CSW, link, amg.AMG_FP32, amg.AMG_FP32),
+                                    U, tv, st)
+        del U, tv
+        torch.cuda.empty_cache()
+        for nrhs in (16, 4):
+            x = sd.coarse_vector(seed + nrhs, ntv, nrhs, Vc, torch.complex64)
+            y = torch.empty_like(x)
+            t, clk = _timed_steps(lambda: amg.amg_coarse_apply(h, x, y, nrhs, st), args.steps, args.warmup, st)
+            b = Vc * 9 * nc * nc * eb + extra + 2 * Vc * nc * nrhs * 8
+            us = 1e6 * t / args.steps
+            kern["%s_%d" % (name, nrhs)] = {"us": round(us, 1), "GB/s": round(b / us / 1e3, 1),
+                                            "frac": round(b / us / 1e3 / peaks["hbm_gbs"], 4), "bytes_per_launch": b}
+            t_total += t
+            bytes_total += b * args.steps
+            steps += args.steps
+        status = amg.amg_sync_status(h)
+        amg.amg_destroy(h)
+        if status != amg.AMG_OK:
+            raise RuntimeError(amg.amg_status_string(status))
+    dom = kern["fp32_16"]
+    return {
+        "value": round(bytes_total / t_total / 1e9, 2), "unit": "GB/s",
+        "ms_per_step": round(1000 * t_total / steps, 4), "steps": args.steps, "warmup": args.warmup, "dtype": "f32",
+        "config": {"workload": ("mrhs_32^3x64_b4_ntv24: D_c x_c with 16 and 4 columns, FP32 and FP16-scaled "
+                                "D_c, tcgen05 one-pass apply; inputs larger than L2 (FP32 D_c 1.36 GB)")
+                               if Lt == (32, 32, 32, 64) else "%dx%dx%dx%d variant of mrhs" % Lt},
+        "roofline": {"bound": "hbm", "kernel": "apply_tc5_kernel<48, true> (FP32 D_c, 16 columns)",
+                     "achieved": dom["GB/s"], "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": dom["frac"],
+                     "peak_source": src, "traffic": TRAFFIC_MRHS_FP32 if Lt == (32, 32, 32, 64) else None,
+                     "bytes_per_launch": dom["bytes_per_launch"], "avg_launch_us": dom["us"]},
+        "kernels": kern, "clocks": clk,
+    }
+
+
 def run_tc16(args):
     """48^3 x 96, 4^4 blocks (12^3 x 24 coarse), Ntv = 24, 16 right-hand sides, BF16 tensor cores.
 
@@ -947,7 +1004,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-speedup", action="store_true",
                     help="skip the batched-mixed vs plain FP32 coarse-solve comparison")
-    ap.add_argument("--workload", default="fp32", choices=["fp32", "tc16", "fp16", "batch", "vcycle"],
+    ap.add_argument("--workload", default="fp32", choices=["fp32", "tc16", "fp16", "mrhs", "batch", "vcycle"],
                     help="fp32: the default 32^4 workload; tc16: 48^3x96 with 16 RHS on the tensor cores; "
                          "fp16: 200 FP16 coarse applications at 32^3x64; batch: the uneven batch")
     ap.add_argument("--no-autotune", action="store_true",
@@ -978,6 +1035,8 @@ def main():
         res, rank = run_batch(args), 0
     elif args.workload == "vcycle":
         res, rank = run_vcycle(args), 0
+    elif args.workload == "mrhs":
+        res, rank = run_mrhs(args), 0
     else:
         res, rank = run_gpu(args)
     if rank == 0 and res is not None:
