@@ -204,6 +204,22 @@ def whole_job_gbs(world, step_bytes, steps, seconds):
     return world * step_bytes * steps / seconds / 1e9
 
 
+FP64_TFLOPS = 1.25  # GB300 FP64 peak (nominal; an FMA-chain probe on this pool measured 1.258)
+
+
+def setup_report(setup_ms, V, ntv):
+    """Setup phase times; the assembly's rank-6 contractions (4 hops over all 2Ntv x 2Ntv entries,
+    the self term over the two chirality-diagonal quadrants) as FP64-equivalent flops (8 per
+    complex multiply-add) against the FP64 peak."""
+    nc = 2 * ntv
+    flop = 8.0 * V * 6 * (4 * nc * nc + 2 * ntv * ntv)
+    rate = flop / (setup_ms[2] * 1e-3) / 1e12
+    return {"clover": round(setup_ms[0], 2), "gram_schmidt": round(setup_ms[1], 2),
+            "assembly": round(setup_ms[2], 2), "quantise": round(setup_ms[3], 2),
+            "assembly_arith": "f32pair", "assembly_tflop": round(flop / 1e12, 3),
+            "assembly_fp64_equiv_tflops": round(rate, 3), "fp64_peak_tflops": FP64_TFLOPS}
+
+
 def run_gpu(args):
     import torch
     import paper_1512_04506_gb300 as amg
@@ -220,7 +236,8 @@ def run_gpu(args):
     seed = SEED + 1000 * rank  # independent replica per rank
     U = sd.links(seed, EPS, L)
     tv = sd.test_vectors(seed, NTV, L)
-    p = amg.make_params(L, B, NTV, 1, M0, CSW, amg.AMG_FP32, amg.AMG_FP32, amg.AMG_FP32)
+    p = amg.make_params(L, B, NTV, 1, M0, CSW, amg.AMG_FP32, amg.AMG_FP32, amg.AMG_FP32,
+                        setup_arith=amg.AMG_SETUP_F32PAIR)
     h, _ = amg.amg_setup_coarse(p, U, tv, stream)
     setup_ms = amg.amg_setup_timings(h)
     del U, tv
@@ -325,8 +342,7 @@ def run_gpu(args):
             "prolong": {"GB/s": round(parts["prolong"] / t_prolong / 1e9, 1), "us": round(t_prolong * 1e6, 1),
                         "frac": round(parts["prolong"] / t_prolong / 1e9 / peaks["hbm_gbs"], 4)},
         },
-        "setup_ms": {"clover": round(setup_ms[0], 2), "gram_schmidt": round(setup_ms[1], 2),
-                     "assembly": round(setup_ms[2], 2), "quantise": round(setup_ms[3], 2)},
+        "setup_ms": setup_report(setup_ms, V, NTV),
         "e2e": {"value": round(e2e_value, 2), "unit": "GB/s", "h2d_bytes_per_step": V * 12 * 8,
                 "d2h_bytes_per_step": V * 12 * 8},
         "gpu_launches": int(launches),
@@ -806,7 +822,8 @@ def run_tc16(args):
     st = torch.cuda.current_stream()
     U = sd.links(seed, EPS, Lt)
     tv = sd.test_vectors(seed, ntv, Lt)
-    p = amg.make_params(Lt, B, ntv, nrhs, M0, CSW, amg.AMG_BF16, amg.AMG_BF16, amg.AMG_BF16)
+    p = amg.make_params(Lt, B, ntv, nrhs, M0, CSW, amg.AMG_BF16, amg.AMG_BF16, amg.AMG_BF16,
+                        setup_arith=amg.AMG_SETUP_F32PAIR)
     h, _ = amg.amg_setup_coarse(p, U, tv, st)
     setup_ms = amg.amg_setup_timings(h)
     del U, tv
@@ -860,7 +877,7 @@ def run_tc16(args):
                      "traffic": TRAFFIC_TC16.get(dom) if Lt == (48, 48, 48, 96) else None,
                      "bytes_per_launch": parts[dom], "avg_launch_us": kern[dom]["us"],
                      "step_share": round(tk[dom] * counts[dom] / (t / args.steps), 3)},
-        "kernels": kern, "setup_ms": [round(v, 1) for v in setup_ms], "clocks": clk,
+        "kernels": kern, "setup_ms": setup_report(setup_ms, V, ntv), "clocks": clk,
     }
 
 

@@ -66,6 +66,14 @@ typedef enum {
     AMG_BF16 = 3
 } amg_prec;
 
+/* Arithmetic of the D_c = R D P assembly in amg_setup_coarse (clover and Gram-Schmidt stay FP64). */
+typedef enum {
+    AMG_SETUP_FP64 = 0,     /* doubles on the FP64 pipe                                      */
+    AMG_SETUP_F32PAIR = 1   /* each number an unevaluated sum of two floats (~47 bits), sums by
+                               TwoSum and products by the FMA residual, on the FP32 pipes;
+                               results agree with FP64 to about 1e-14 relative              */
+} amg_setup_arith;
+
 typedef struct {
     int L[4];            /* fine lattice extents, mu = 0..3 = x, y, z, t               */
     int B[4];            /* block extents                                              */
@@ -76,6 +84,7 @@ typedef struct {
     amg_prec link_prec;  /* storage of D_c for apply/solve: FP64, FP32, FP16_SCALED, BF16 */
     amg_prec r_prec;     /* storage of R for restrict/prolong: FP64, FP32, BF16         */
     amg_prec vec_prec;   /* element type of fine vectors: FP64, FP32 or BF16            */
+    amg_setup_arith setup_arith;  /* assembly arithmetic; 0 (zero-initialised) = FP64       */
 } amg_params;
 /* BF16 storage runs on the tensor cores and needs ntv a multiple of 4 and V_block a
  * multiple of 8 (else amg_setup_coarse returns AMG_ERR_UNSUPPORTED); its applies take

@@ -27,6 +27,9 @@ AMG_FP32 = 1
 AMG_FP16_SCALED = 2
 AMG_BF16 = 3
 
+AMG_SETUP_FP64 = 0
+AMG_SETUP_F32PAIR = 1
+
 
 class amg_params(ctypes.Structure):
     _fields_ = [
@@ -39,6 +42,7 @@ class amg_params(ctypes.Structure):
         ("link_prec", ctypes.c_int),
         ("r_prec", ctypes.c_int),
         ("vec_prec", ctypes.c_int),
+        ("setup_arith", ctypes.c_int),
     ]
 
 
@@ -157,7 +161,7 @@ def _check(status, where, allow=()):
 
 
 def make_params(L, B, ntv, max_nrhs=1, m0=-0.3, csw=1.0, link_prec=AMG_FP32, r_prec=AMG_FP32,
-                vec_prec=AMG_FP32):
+                vec_prec=AMG_FP32, setup_arith=AMG_SETUP_FP64):
     p = amg_params()
     p.L[:] = list(L)
     p.B[:] = list(B)
@@ -168,6 +172,7 @@ def make_params(L, B, ntv, max_nrhs=1, m0=-0.3, csw=1.0, link_prec=AMG_FP32, r_p
     p.link_prec = link_prec
     p.r_prec = r_prec
     p.vec_prec = vec_prec
+    p.setup_arith = setup_arith
     return p
 
 

@@ -50,6 +50,7 @@ amg_status validate_params(const amg_params* p) {
   if (p->max_nrhs < 1 || p->max_nrhs > 64) return AMG_ERR_INVALID_ARG;
   if (!valid_prec(p->link_prec) || !valid_prec(p->r_prec) || !valid_prec(p->vec_prec)) return AMG_ERR_INVALID_ARG;
   if (p->r_prec == AMG_FP16_SCALED || p->vec_prec == AMG_FP16_SCALED) return AMG_ERR_INVALID_ARG;
+  if (p->setup_arith != AMG_SETUP_FP64 && p->setup_arith != AMG_SETUP_F32PAIR) return AMG_ERR_INVALID_ARG;
   // supported storage / vector combinations
   if (p->vec_prec == AMG_FP64) {
     if (p->link_prec != AMG_FP64 || p->r_prec != AMG_FP64) return AMG_ERR_UNSUPPORTED;

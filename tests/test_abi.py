@@ -52,9 +52,10 @@ def test_synth_library_exports(built):
 
 def test_params_struct_layout(built):
     import paper_1512_04506_gb300 as amg
-    # int L[4], B[4], ntv, max_nrhs, (pad to 8), double m0, csw, 3 enums (+pad)
-    assert ctypes.sizeof(amg.amg_params) == 4 * 10 + 2 * 8 + 3 * 4 + 4
+    # int L[4], B[4], ntv, max_nrhs, double m0, csw, 4 enums
+    assert ctypes.sizeof(amg.amg_params) == 4 * 10 + 2 * 8 + 4 * 4
     assert amg.amg_params.m0.offset == 40
+    assert amg.amg_params.setup_arith.offset == 68
 
 
 def test_argument_validation_without_gpu(built):
@@ -68,6 +69,7 @@ def test_argument_validation_without_gpu(built):
         amg.make_params((4, 4, 4, 4), (1, 1, 1, 1), 7),           # ntv > 6 Vb
         amg.make_params((4, 4, 4, 4), (2, 2, 2, 2), 8, max_nrhs=0),
         amg.make_params((4, 4, 4, 4), (2, 2, 2, 2), 8, link_prec=9),
+        amg.make_params((4, 4, 4, 4), (2, 2, 2, 2), 8, setup_arith=2),
     ]
     for p in bad:
         st = amg.lib.amg_setup_coarse(ctypes.byref(p), 16, 16, None, ctypes.byref(h))
