@@ -218,7 +218,7 @@ inline size_t coarse_elem_bytes(const amg_coarse* h) { return h->p.vec_prec == A
 amg_status amg_internal_setup(amg_coarse* h, const double2* U, const double2* tv, cudaStream_t s);
 // assembly partial sums ([Vc][5 jobs][2 slots][nc][nc], the layout combine_kernel reads) in pairs of floats
 amg_status amg_internal_assemble_pair(const Geom& g, const double2* R, const double2* U, const double2* clov,
-                                      double2* part, double m0, cudaStream_t st);
+                                      double2* part, double m0, unsigned* err, cudaStream_t st);
 amg_status amg_internal_restrict(amg_coarse* h, const void* y, void* yc, int nrhs, cudaStream_t s);
 amg_status amg_internal_apply(amg_coarse* h, const void* xc, void* yc, int nrhs, cudaStream_t s);
 amg_status amg_internal_prolong(amg_coarse* h, const void* xc, void* x, int nrhs, cudaStream_t s);

@@ -614,7 +614,7 @@ amg_status amg_internal_setup(amg_coarse* h, const double2* U, const double2* tv
   const size_t part_elems = (size_t)g.Vc * 5 * 2 * g.nc * g.nc;
   AMG_CUDA_TRY(cudaMallocAsync((void**)&part, part_elems * sizeof(double2), st));
   if (h->p.setup_arith == AMG_SETUP_F32PAIR) {
-    AMG_TRY_INTERNAL(amg_internal_assemble_pair(g, h->R64, U, h->clover, part, h->p.m0, st));
+    AMG_TRY_INTERNAL(amg_internal_assemble_pair(g, h->R64, U, h->clover, part, h->p.m0, h->err, st));
   } else {
     // 2x4 register tiles up to 2 ntv = 40, 4x4 tiles up to 2 ntv = 64; at most 256 threads
     const bool big = g.nc > 40;

@@ -24,6 +24,7 @@
 // the tiles that lie wholly in a chirality off-diagonal quadrant are skipped (those entries are not
 // used).
 #include "amg_internal.cuh"
+#include "pipe.cuh"
 
 namespace {
 
@@ -125,212 +126,361 @@ __device__ __forceinline__ pc neg_b(int mu, int a, const pc& z) {
   return r;
 }
 
+// ------------------------------------------------------------------ one (block, job)
+struct PairJob {
+  long long blk, blk_fwd;
+  int job, mu, stride_mu, Bmu, nface;
+  pc dd;  // 4 + m0
+};
+__device__ inline PairJob pair_job(const Geom& g, long long blk, int job, double m0) {
+  PairJob J;
+  J.blk = blk;
+  J.job = job;
+  J.mu = job < 4 ? job : 0;
+  int Xc[4];
+  long long r = blk;
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    Xc[m] = (int)(r % g.Lc[m]);
+    r /= g.Lc[m];
+  }
+  J.stride_mu = 1;
+  J.Bmu = 1;
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {  // constant indices only
+    if (m < J.mu) J.stride_mu *= g.B[m];
+    if (m == J.mu) {
+      J.Bmu = g.B[m];
+      Xc[m] = (Xc[m] + 1) % g.Lc[m];
+    }
+  }
+  J.blk_fwd = ((long long)(Xc[3] * g.Lc[2] + Xc[2]) * g.Lc[1] + Xc[1]) * g.Lc[0] + Xc[0];
+  J.nface = job < 4 ? (int)g.Vb / J.Bmu : 0;  // sites on the +mu face, visited last
+  J.dd = pc{0.f, 0.f, 0.f, 0.f};
+  split_double(4.0 + m0, J.dd.rh, J.dd.rl);
+  return J;
+}
+// visiting order t -> local site: t = l_mu * nface + r for hop jobs (the face, l_mu = B_mu - 1, last)
+__device__ inline int pair_site(const PairJob& J, int t) {
+  if (J.job == 4) return t;
+  const int lmu = t / J.nface, r = t % J.nface;
+  return (r / J.stride_mu) * (J.stride_mu * J.Bmu) + lmu * J.stride_mu + (r % J.stride_mu);
+}
+
+// A(x) and Bt(x) of one (site, column) into the chunk's shared arrays [6][ncp]; the B columns
+// interleaved by tile, column c at (c % TC) * ntc + c / TC, so that the TC columns of consecutive
+// tile columns are consecutive float4 words (no shared-memory bank conflicts).
+template <int TC>
+__device__ inline void build_item(const Geom& g, const PairJob& J, const double2* __restrict__ R,
+                                  const double2* __restrict__ U, const double2* __restrict__ clov, float4* As,
+                                  float4* Bs, int ncp, int ntc, int t, int c, bool valid) {
+  float4* Ao = As + c;
+  float4* Bo = Bs + (c % TC) * ntc + c / TC;
+  auto put = [&](float4* o, int k, const pc& v) { o[(size_t)k * ncp] = make_float4(v.rh, v.ih, v.rl, v.il); };
+  if (!valid) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      put(Ao, k, pc{0.f, 0.f, 0.f, 0.f});
+      put(Bo, k, pc{0.f, 0.f, 0.f, 0.f});
+    }
+    return;
+  }
+  const int ntv = g.ntv, mu = J.mu;
+  const int sl = pair_site(J, t);
+  const long long site = block_site(g, J.blk, sl);
+  const int hc = c / ntv, j = c % ntv;
+  const double2* Rc = R + ((J.blk * 2 + hc) * (long long)ntv + j) * g.nagg + sl * 6;
+  if (J.job == 4) {
+    // self: A = P(x), Bt = ((4 + m0) + C(x)) P(x) per chirality
+    const double2* C6 = clov + (site * 2 + hc) * 36;
+    pc q[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      q[k] = split_conj(Rc[k]);
+      put(Ao, k, q[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      lacc s{0.f, 0.f, 0.f, 0.f};
+      lacc_fma(s, J.dd, q[k]);
+#pragma unroll
+      for (int kp = 0; kp < 6; ++kp) lacc_fma(s, split_c(C6[k * 6 + kp]), q[kp]);
+      put(Bo, k, lacc_value(s));
+    }
+    return;
+  }
+  // row a of u^dagger z is z_a for the l columns and -b_mu z_b(a) for the r columns, with
+  // b(a) = 1 - a for mu = 0, 1 and b(a) = a for mu = 2, 3; row a is fed by spin b = b(a)
+  const int lmu = (sl / J.stride_mu) % J.Bmu;
+  const bool face = lmu == J.Bmu - 1;
+  const int sn = face ? sl - (J.Bmu - 1) * J.stride_mu : sl + J.stride_mu;
+  const long long bn = face ? J.blk_fwd : J.blk;
+  const double2* Rn = R + ((bn * 2 + hc) * (long long)ntv + j) * g.nagg + sn * 6;
+  const double2* Ul = U + (site * 4 + mu) * 9;
+#pragma unroll 1
+  for (int b = 0; b < 2; ++b) {
+    const int a = (hc == 1 && mu < 2) ? 1 - b : b;
+    // A = u^dagger P(x)
+#pragma unroll
+    for (int col = 0; col < 3; ++col) {
+      const pc v = split_conj(Rc[b * 3 + col]);
+      put(Ao, a * 3 + col, hc == 0 ? v : neg_b(mu, a, v));
+    }
+    // Bt = u^dagger U_mu(x) P(x + mu)
+    pc qn[3];
+#pragma unroll
+    for (int cp = 0; cp < 3; ++cp) qn[cp] = split_conj(Rn[b * 3 + cp]);
+#pragma unroll 1
+    for (int col = 0; col < 3; ++col) {
+      lacc s{0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int cp = 0; cp < 3; ++cp) lacc_fma(s, split_c(Ul[col * 3 + cp]), qn[cp]);
+      const pc z = lacc_value(s);
+      put(Bo, a * 3 + col, hc == 0 ? z : neg_b(mu, a, z));
+    }
+  }
+}
+
+// One site's rank-6 product into the tile's accumulators: a local pair sum over the six rows,
+// then one three-level addition per entry.
+template <int TA, int TC>
+__device__ inline void contract_site(const float4* As, const float4* Bs, int ncp, int ntc, int ta, int tc,
+                                     gacc (&accr)[TA][TC], gacc (&acci)[TA][TC]) {
+  lacc loc[TA][TC];
+#pragma unroll
+  for (int i = 0; i < TA; ++i)
+#pragma unroll
+    for (int jj = 0; jj < TC; ++jj) loc[i][jj] = lacc{0.f, 0.f, 0.f, 0.f};
+#pragma unroll 1  // rolled: the unrolled rank-6 body overflows the instruction cache
+  for (int k = 0; k < 6; ++k) {
+    pc av[TA], bv[TC];
+#pragma unroll
+    for (int i = 0; i < TA; ++i) {
+      const float4 v = As[(size_t)k * ncp + ta * TA + i];
+      av[i] = pc{v.x, v.y, v.z, v.w};
+    }
+#pragma unroll
+    for (int jj = 0; jj < TC; ++jj) {
+      const float4 v = Bs[(size_t)k * ncp + jj * ntc + tc];
+      bv[jj] = pc{v.x, v.y, v.z, v.w};
+    }
+#pragma unroll
+    for (int i = 0; i < TA; ++i)
+#pragma unroll
+      for (int jj = 0; jj < TC; ++jj) lacc_fmac(loc[i][jj], av[i], bv[jj]);
+  }
+#pragma unroll
+  for (int i = 0; i < TA; ++i)
+#pragma unroll
+    for (int jj = 0; jj < TC; ++jj) {
+      gacc_add(accr[i][jj], loc[i][jj].rh, loc[i][jj].rl);
+      gacc_add(acci[i][jj], loc[i][jj].ih, loc[i][jj].il);
+    }
+}
+
+template <int TA, int TC>
+__device__ inline void write_tile(double2* P, int nc, int ta, int tc, gacc (&accr)[TA][TC], gacc (&acci)[TA][TC]) {
+#pragma unroll
+  for (int i = 0; i < TA; ++i)
+#pragma unroll
+    for (int jj = 0; jj < TC; ++jj) {
+      const int a = ta * TA + i, c = tc * TC + jj;
+      if (a < nc && c < nc) P[a * nc + c] = make_double2(gacc_value(accr[i][jj]), gacc_value(acci[i][jj]));
+      accr[i][jj] = acci[i][jj] = gacc{0.f, 0.f, 0.f};
+    }
+}
+
+// tiles wholly off the chirality diagonal carry nothing the self block uses
+template <int TA, int TC>
+__device__ inline bool tile_needed(int job, int ntv, int ta, int tc) {
+  return !(job == 4 && ((ta * TA + TA <= ntv && tc * TC >= ntv) || (ta * TA >= ntv && tc * TC + TC <= ntv)));
+}
+
+// Every thread builds, then every thread contracts (barrier between): the form for nc > 48.
 template <int TA, int TC>
 __global__ void __launch_bounds__(512)
 assemble_pair_kernel(const double2* __restrict__ R, const double2* __restrict__ U,
                      const double2* __restrict__ clov, double2* __restrict__ part, Geom g, double m0,
                      int ncp, int sb_max) {
   extern __shared__ float4 smem4[];
-  const long long blk = blockIdx.x;
-  const int job = blockIdx.y;
-  const int nc = g.nc, ntv = g.ntv, nagg = g.nagg, Vb = (int)g.Vb;
+  const int nc = g.nc, Vb = (int)g.Vb;
   float4* As = smem4;  // [sb][6][ncp] (rh, ih, rl, il)
   float4* Bs = smem4 + (size_t)sb_max * 6 * ncp;
-  const int ntc = ncp / TC, nta = ncp / TA, ntiles = ntc * nta;
+  const int ntc = ncp / TC, ntiles = ntc * (ncp / TA);
   const int tid = threadIdx.x;
   const int ta = tid / ntc, tc = tid % ntc;
-  int Xc[4];
-  {
-    long long r = blk;
-    for (int m = 0; m < 4; ++m) {
-      Xc[m] = (int)(r % g.Lc[m]);
-      r /= g.Lc[m];
-    }
-  }
-  const int mu = job < 4 ? job : 0;
-  int stride_mu = 1, Bmu = 1;
-  long long blk_fwd;
-  {
-    int X[4] = {Xc[0], Xc[1], Xc[2], Xc[3]};
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {  // constant indices only
-      if (m < mu) stride_mu *= g.B[m];
-      if (m == mu) {
-        Bmu = g.B[m];
-        X[m] = (X[m] + 1) % g.Lc[m];
-      }
-    }
-    blk_fwd = ((long long)(X[3] * g.Lc[2] + X[2]) * g.Lc[1] + X[1]) * g.Lc[0] + X[0];
-  }
-  const int nface = job < 4 ? Vb / Bmu : 0;  // sites on the +mu face, visited last
-  // visiting order t -> local site: t = l_mu * nface + r for hop jobs (face: l_mu = B_mu - 1)
-  auto site_of = [&](int t) -> int {
-    if (job == 4) return t;
-    const int lmu = t / nface, r = t % nface;
-    return (r / stride_mu) * (stride_mu * Bmu) + lmu * stride_mu + (r % stride_mu);
-  };
-  // tiles wholly off the chirality diagonal carry nothing the self block uses
-  const bool active = tid < ntiles &&
-                      !(job == 4 && ((ta * TA + TA <= ntv && tc * TC >= ntv) || (ta * TA >= ntv && tc * TC + TC <= ntv)));
+  const PairJob J = pair_job(g, blockIdx.x, blockIdx.y, m0);
+  const bool active = tid < ntiles && tile_needed<TA, TC>(J.job, g.ntv, ta, tc);
   gacc accr[TA][TC], acci[TA][TC];
 #pragma unroll
   for (int i = 0; i < TA; ++i)
 #pragma unroll
     for (int j = 0; j < TC; ++j) accr[i][j] = acci[i][j] = gacc{0.f, 0.f, 0.f};
-  double2* P0 = part + ((blk * 5 + job) * 2 + 0) * (long long)nc * nc;
+  double2* P0 = part + ((J.blk * 5 + J.job) * 2 + 0) * (long long)nc * nc;
   double2* P1 = P0 + (long long)nc * nc;
-  auto flush = [&](double2* P) {
-    if (tid < ntiles) {
-#pragma unroll
-      for (int i = 0; i < TA; ++i)
-#pragma unroll
-        for (int jj = 0; jj < TC; ++jj) {
-          const int a = ta * TA + i, c = tc * TC + jj;
-          if (a < nc && c < nc) P[a * nc + c] = make_double2(gacc_value(accr[i][jj]), gacc_value(acci[i][jj]));
-          accr[i][jj] = acci[i][jj] = gacc{0.f, 0.f, 0.f};
-        }
-    }
-  };
-  pc dd{0.f, 0.f, 0.f, 0.f};  // 4 + m0 as a pair
-  split_double(4.0 + m0, dd.rh, dd.rl);
   for (int t0 = 0; t0 < Vb; t0 += sb_max) {
     const int nsb = min(sb_max, Vb - t0);
     for (int pr = tid; pr < sb_max * ncp; pr += blockDim.x) {
       const int sb = pr / ncp, c = pr % ncp;
-      float4* Ao = As + (size_t)sb * 6 * ncp + c;
-      float4* Bo = Bs + (size_t)sb * 6 * ncp + c;
-      auto put = [&](float4* o, int k, const pc& v) { o[(size_t)k * ncp] = make_float4(v.rh, v.ih, v.rl, v.il); };
-      if (sb >= nsb || c >= nc) {
-#pragma unroll
-        for (int k = 0; k < 6; ++k) {
-          put(Ao, k, pc{0.f, 0.f, 0.f, 0.f});
-          put(Bo, k, pc{0.f, 0.f, 0.f, 0.f});
-        }
-        continue;
-      }
-      const int sl = site_of(t0 + sb);
-      const long long site = block_site(g, blk, sl);
-      const int hc = c / ntv, j = c % ntv;
-      const double2* Rc = R + ((blk * 2 + hc) * (long long)ntv + j) * nagg + sl * 6;
-      if (job == 4) {
-        // self: A = P(x), Bt = ((4 + m0) + C(x)) P(x) per chirality
-        const double2* C6 = clov + (site * 2 + hc) * 36;
-        pc q[6];
-#pragma unroll
-        for (int k = 0; k < 6; ++k) {
-          q[k] = split_conj(Rc[k]);
-          put(Ao, k, q[k]);
-        }
-#pragma unroll
-        for (int k = 0; k < 6; ++k) {
-          lacc s{0.f, 0.f, 0.f, 0.f};
-          lacc_fma(s, dd, q[k]);
-#pragma unroll
-          for (int kp = 0; kp < 6; ++kp) lacc_fma(s, split_c(C6[k * 6 + kp]), q[kp]);
-          put(Bo, k, lacc_value(s));
-        }
-        continue;
-      }
-      // row a of u^dagger z is z_a for the l columns and -b_mu z_b(a) for the r columns, with
-      // b(a) = 1 - a for mu = 0, 1 and b(a) = a for mu = 2, 3; row a is fed by spin b = b(a)
-      const int lmu = (sl / stride_mu) % Bmu;
-      const bool face = lmu == Bmu - 1;
-      const int sn = face ? sl - (Bmu - 1) * stride_mu : sl + stride_mu;
-      const long long bn = face ? blk_fwd : blk;
-      const double2* Rn = R + ((bn * 2 + hc) * (long long)ntv + j) * nagg + sn * 6;
-      const double2* Ul = U + (site * 4 + mu) * 9;
-#pragma unroll 1
-      for (int b = 0; b < 2; ++b) {
-        const int a = (hc == 1 && mu < 2) ? 1 - b : b;
-        // A = u^dagger P(x)
-#pragma unroll
-        for (int col = 0; col < 3; ++col) {
-          const pc v = split_conj(Rc[b * 3 + col]);
-          put(Ao, a * 3 + col, hc == 0 ? v : neg_b(mu, a, v));
-        }
-        // Bt = u^dagger U_mu(x) P(x + mu)
-        pc qn[3];
-#pragma unroll
-        for (int cp = 0; cp < 3; ++cp) qn[cp] = split_conj(Rn[b * 3 + cp]);
-#pragma unroll 1
-        for (int col = 0; col < 3; ++col) {
-          lacc s{0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-          for (int cp = 0; cp < 3; ++cp) lacc_fma(s, split_c(Ul[col * 3 + cp]), qn[cp]);
-          const pc z = lacc_value(s);
-          put(Bo, a * 3 + col, hc == 0 ? z : neg_b(mu, a, z));
-        }
-      }
+      build_item<TC>(g, J, R, U, clov, As + (size_t)sb * 6 * ncp, Bs + (size_t)sb * 6 * ncp, ncp, ntc, t0 + sb, c,
+                     sb < nsb && c < nc);
     }
     __syncthreads();
     for (int sb = 0; sb < nsb; ++sb) {
-      if (job < 4 && t0 + sb == Vb - nface) flush(P0);  // interior links done: S_mu
-      if (active) {
-        lacc loc[TA][TC];
-#pragma unroll
-        for (int i = 0; i < TA; ++i)
-#pragma unroll
-          for (int jj = 0; jj < TC; ++jj) loc[i][jj] = lacc{0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-        for (int k = 0; k < 6; ++k) {
-          pc av[TA], bv[TC];
-#pragma unroll
-          for (int i = 0; i < TA; ++i) {
-            const float4 v = As[((size_t)sb * 6 + k) * ncp + ta * TA + i];
-            av[i] = pc{v.x, v.y, v.z, v.w};
-          }
-#pragma unroll
-          for (int jj = 0; jj < TC; ++jj) {
-            const float4 v = Bs[((size_t)sb * 6 + k) * ncp + tc * TC + jj];
-            bv[jj] = pc{v.x, v.y, v.z, v.w};
-          }
-#pragma unroll
-          for (int i = 0; i < TA; ++i)
-#pragma unroll
-            for (int jj = 0; jj < TC; ++jj) lacc_fmac(loc[i][jj], av[i], bv[jj]);
-        }
-#pragma unroll
-        for (int i = 0; i < TA; ++i)
-#pragma unroll
-          for (int jj = 0; jj < TC; ++jj) {
-            gacc_add(accr[i][jj], loc[i][jj].rh, loc[i][jj].rl);
-            gacc_add(acci[i][jj], loc[i][jj].ih, loc[i][jj].il);
-          }
-      }
+      if (J.job < 4 && t0 + sb == Vb - J.nface && tid < ntiles) write_tile(P0, nc, ta, tc, accr, acci);  // S_mu
+      if (active) contract_site(As + (size_t)sb * 6 * ncp, Bs + (size_t)sb * 6 * ncp, ncp, ntc, ta, tc, accr, acci);
     }
     __syncthreads();
   }
-  if (job < 4) {
-    flush(P1);  // face links: F_mu
-  } else {
-    flush(P0);  // self; slot 1 is not read for the self job
+  if (tid < ntiles) write_tile(J.job < 4 ? P1 : P0, nc, ta, tc, accr, acci);  // F_mu, or the self block
+}
+
+// Warp-specialised form (nc <= 48): NCW contraction warps (a multiple of four, so that every SM
+// sub-partition carries the same share) and four builder warps, with two chunk buffers handed over
+// through mbarriers (bounded waits; a wait that runs out sets the timeout bit in *err).
+constexpr int kBuilders = 128;
+template <int TA, int TC>
+__global__ void __launch_bounds__(512)
+assemble_pair_ws_kernel(const double2* __restrict__ R, const double2* __restrict__ U,
+                        const double2* __restrict__ clov, double2* __restrict__ part, Geom g, double m0, int ncp,
+                        int sb, int ncons, unsigned* err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  amgpipe::Pipe* pp = reinterpret_cast<amgpipe::Pipe*>(smem_raw);
+  float4* buf = reinterpret_cast<float4*>(smem_raw + amgpipe::kPipeBytes);  // [2][A | B][sb][6][ncp]
+  const size_t half = (size_t)sb * 6 * ncp;
+  const int nc = g.nc, Vb = (int)g.Vb;
+  const int ntc = ncp / TC, ntiles = ntc * (ncp / TA);
+  const int tid = threadIdx.x;
+  const PairJob J = pair_job(g, blockIdx.x, blockIdx.y, m0);
+  const int nch = (Vb + sb - 1) / sb;
+  if (tid == 0) {
+    for (int b = 0; b < 2; ++b) {
+      amgpipe::mbar_init(&pp->full[b], kBuilders);
+      amgpipe::mbar_init(&pp->empty[b], ncons);
+    }
+    pp->abort = 0;
+    amgpipe::fence_mbar_init();
   }
+  __syncthreads();
+  if (tid >= ncons) {
+    // builders
+    const int bt = tid - ncons;
+    for (int ch = 0; ch < nch; ++ch) {
+      const int b = ch & 1;
+      if (ch >= 2 && !amgpipe::wait_phase(&pp->empty[b], ((ch >> 1) - 1) & 1, pp)) {
+        amgpipe::abort_cta(pp, err);
+        break;
+      }
+      const int t0 = ch * sb, nsb = min(sb, Vb - t0);
+      float4* Ab = buf + (size_t)b * 2 * half;
+      for (int pr = bt; pr < sb * ncp; pr += kBuilders) {
+        const int s = pr / ncp, c = pr % ncp;
+        build_item<TC>(g, J, R, U, clov, Ab + (size_t)s * 6 * ncp, Ab + half + (size_t)s * 6 * ncp, ncp, ntc, t0 + s,
+                       c, s < nsb && c < nc);
+      }
+      amgpipe::mbar_arrive(&pp->full[b]);
+    }
+    return;
+  }
+  // contraction
+  const int ta = tid / ntc, tc = tid % ntc;
+  const bool tile = tid < ntiles;
+  const bool active = tile && tile_needed<TA, TC>(J.job, g.ntv, ta, tc);
+  gacc accr[TA][TC], acci[TA][TC];
+#pragma unroll
+  for (int i = 0; i < TA; ++i)
+#pragma unroll
+    for (int j = 0; j < TC; ++j) accr[i][j] = acci[i][j] = gacc{0.f, 0.f, 0.f};
+  double2* P0 = part + ((J.blk * 5 + J.job) * 2 + 0) * (long long)nc * nc;
+  double2* P1 = P0 + (long long)nc * nc;
+  for (int ch = 0; ch < nch; ++ch) {
+    const int b = ch & 1;
+    if (!amgpipe::wait_phase(&pp->full[b], (ch >> 1) & 1, pp)) {
+      amgpipe::abort_cta(pp, err);
+      break;
+    }
+    const int t0 = ch * sb, nsb = min(sb, Vb - t0);
+    const float4* Ab = buf + (size_t)b * 2 * half;
+    for (int s = 0; s < nsb; ++s) {
+      if (J.job < 4 && t0 + s == Vb - J.nface && tile) write_tile(P0, nc, ta, tc, accr, acci);  // S_mu
+      if (active) contract_site(Ab + (size_t)s * 6 * ncp, Ab + half + (size_t)s * 6 * ncp, ncp, ntc, ta, tc, accr, acci);
+    }
+    amgpipe::mbar_arrive(&pp->empty[b]);
+  }
+  if (tile) write_tile(J.job < 4 ? P1 : P0, nc, ta, tc, accr, acci);  // F_mu, or the self block
 }
 
 int round_up_i(int a, int b) { return (a + b - 1) / b * b; }
+int lcm_i(int a, int b) {
+  int x = a, y = b;
+  while (y) {
+    const int t = x % y;
+    x = y;
+    y = t;
+  }
+  return a / x * b;
+}
+
+template <int TA, int TC>
+amg_status launch_ws(const Geom& g, const double2* R, const double2* U, const double2* clov, double2* part,
+                     double m0, unsigned* err, cudaStream_t st) {
+  const int ncp = round_up_i(g.nc, lcm_i(TA, TC));
+  const int ntiles = (ncp / TA) * (ncp / TC);
+  const int ncons = round_up_i(ntiles, 128);
+  const int sb = 8;
+  const size_t sm = amgpipe::kPipeBytes + (size_t)2 * 2 * sb * 6 * ncp * sizeof(float4);
+  AMG_CUDA_TRY(cudaFuncSetAttribute(assemble_pair_ws_kernel<TA, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  assemble_pair_ws_kernel<TA, TC><<<dim3((unsigned)g.Vc, 5), ncons + kBuilders, sm, st>>>(R, U, clov, part, g, m0, ncp,
+                                                                                         sb, ncons, err);
+  AMG_LAUNCH_CHECK();
+  return AMG_OK;
+}
 
 }  // namespace
 
 // Partial sums of the assembly (the layout the combine step reads) in pairs of floats.
 amg_status amg_internal_assemble_pair(const Geom& g, const double2* R, const double2* U, const double2* clov,
-                                      double2* part, double m0, cudaStream_t st) {
-  const bool wide = g.nc > 44;  // 2x2 tiles up to nc = 44 (484 threads), 2x4 tiles up to nc = 64
-  const int TA = 2, TC = wide ? 4 : 2;
+                                      double2* part, double m0, unsigned* err, cudaStream_t st) {
+  if (g.nc <= 48) {
+    // tile shape: fewest tile-rows per SM sub-partition (time), at most 384 contraction threads
+    struct Shape {
+      int ta, tc;
+    };
+    const Shape shapes[] = {{2, 3}, {1, 5}, {2, 2}, {1, 4}, {1, 2}, {1, 1}};
+    int best = -1;
+    long long best_cost = 0;
+    for (int k = 0; k < 6; ++k) {
+      const int ncp = round_up_i(g.nc, lcm_i(shapes[k].ta, shapes[k].tc));
+      const int ntiles = (ncp / shapes[k].ta) * (ncp / shapes[k].tc);
+      const int warps_per_smsp = (ntiles + 127) / 128;
+      if (warps_per_smsp > 3) continue;
+      const long long cost = (long long)warps_per_smsp * shapes[k].ta * shapes[k].tc;
+      if (best < 0 || cost < best_cost) {
+        best = k;
+        best_cost = cost;
+      }
+    }
+    switch (best) {
+      case 0: return launch_ws<2, 3>(g, R, U, clov, part, m0, err, st);
+      case 1: return launch_ws<1, 5>(g, R, U, clov, part, m0, err, st);
+      case 2: return launch_ws<2, 2>(g, R, U, clov, part, m0, err, st);
+      case 3: return launch_ws<1, 4>(g, R, U, clov, part, m0, err, st);
+      case 4: return launch_ws<1, 2>(g, R, U, clov, part, m0, err, st);
+      case 5: return launch_ws<1, 1>(g, R, U, clov, part, m0, err, st);
+      default: return AMG_ERR_UNSUPPORTED;
+    }
+  }
+  // 2x4 tiles up to nc = 64 (512 threads), every thread builds and contracts
+  const int TA = 2, TC = 4;
   const int ncp = round_up_i(g.nc, TC);
   const int ntiles = (ncp / TA) * (ncp / TC);
-  const int T = round_up_i(ntiles < 64 ? 64 : ntiles, 32);
+  const int T = round_up_i(ntiles, 32);
   if (T > 512) return AMG_ERR_UNSUPPORTED;
-  int sb = 8;
-  while (sb > 1 && (size_t)sb * 12 * ncp * sizeof(float4) > 96 * 1024) sb >>= 1;
+  int sb = 16;  // sites per chunk: one CTA per SM (the register file), so most of shared memory
+  while (sb > 1 && (size_t)sb * 12 * ncp * sizeof(float4) > 200 * 1024) sb >>= 1;
   const size_t sm = (size_t)sb * 12 * ncp * sizeof(float4);
-  dim3 grid((unsigned)g.Vc, 5);
-  if (wide) {
-    AMG_CUDA_TRY(cudaFuncSetAttribute(assemble_pair_kernel<2, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    assemble_pair_kernel<2, 4><<<grid, T, sm, st>>>(R, U, clov, part, g, m0, ncp, sb);
-  } else {
-    AMG_CUDA_TRY(cudaFuncSetAttribute(assemble_pair_kernel<2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    assemble_pair_kernel<2, 2><<<grid, T, sm, st>>>(R, U, clov, part, g, m0, ncp, sb);
-  }
+  AMG_CUDA_TRY(cudaFuncSetAttribute(assemble_pair_kernel<2, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  assemble_pair_kernel<2, 4><<<dim3((unsigned)g.Vc, 5), T, sm, st>>>(R, U, clov, part, g, m0, ncp, sb);
   AMG_LAUNCH_CHECK();
   return AMG_OK;
 }
