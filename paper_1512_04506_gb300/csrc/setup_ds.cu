@@ -110,6 +110,38 @@ __device__ __forceinline__ void gacc_add(gacc& g, float h, float l) {
 }
 __device__ __forceinline__ double gacc_value(const gacc& g) { return ((double)g.ll + (double)g.l) + (double)g.h; }
 
+// The same operations on (real, imaginary) lane pairs: one packed FP32x2 instruction per pair
+// (the FP32 pipes run a packed instruction at the rate of two scalar ones, but it takes one
+// issue slot instead of two).
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2& s, float2& e) {
+  s = __fadd2_rn(a, b);
+  const float2 v = __fadd2_rn(s, neg2(a));
+  e = __fadd2_rn(__fadd2_rn(a, neg2(__fadd2_rn(s, neg2(v)))), __fadd2_rn(b, neg2(v)));
+}
+struct lacc2 {
+  float2 h, l;
+};
+// (sh, sl) += (xh + xl)(yh + yl), lane-wise
+__device__ __forceinline__ void pair_fma2(lacc2& s, float2 xh, float2 xl, float2 yh, float2 yl) {
+  const float2 p = __fmul2_rn(xh, yh);
+  const float2 e = __ffma2_rn(xh, yh, neg2(p));
+  const float2 c = __ffma2_rn(xh, yl, __ffma2_rn(xl, yh, e));
+  float2 t;
+  two_sum2(s.h, p, s.h, t);
+  s.l = __fadd2_rn(s.l, __fadd2_rn(t, c));
+}
+struct gacc2 {
+  float2 h, l, ll;
+};
+__device__ __forceinline__ void gacc2_add(gacc2& g, const lacc2& a) {
+  float2 t, u, w, x;
+  two_sum2(g.h, a.h, g.h, t);
+  two_sum2(g.l, a.l, u, w);
+  two_sum2(u, t, g.l, x);
+  g.ll = __fadd2_rn(g.ll, __fadd2_rn(w, x));
+}
+
 // -b_mu(a, b(a)) z for the one nonzero entry of row a of b_mu (-i sigma_x, -i sigma_y, -i sigma_z, 1):
 // b(a) = 1 - a for mu = 0, 1 (off-diagonal), b(a) = a for mu = 2, 3
 __device__ __forceinline__ pc neg_b(int mu, int a, const pc& z) {
@@ -167,21 +199,32 @@ __device__ inline int pair_site(const PairJob& J, int t) {
   return (r / J.stride_mu) * (J.stride_mu * J.Bmu) + lmu * J.stride_mu + (r % J.stride_mu);
 }
 
-// A(x) and Bt(x) of one (site, column) into the chunk's shared arrays [6][ncp]; the B columns
+// A(x) and Bt(x) of one (site, column) into the chunk's shared arrays; the B columns
 // interleaved by tile, column c at (c % TC) * ntc + c / TC, so that the TC columns of consecutive
 // tile columns are consecutive float4 words (no shared-memory bank conflicts).
+//
+// Each value is stored in the two lane-pair forms the contraction multiplies, as two float4 rows
+// [k][form][ncp]: A as (a_r, a_r | lo) and (a_i, -a_i | lo), B as (b_r, b_i | lo) and (b_i, b_r | lo),
+// so that conj(a) b = (a_r, a_r)(b_r, b_i) + (a_i, -a_i)(b_i, b_r) lane-wise.
 template <int TC>
 __device__ inline void build_item(const Geom& g, const PairJob& J, const double2* __restrict__ R,
                                   const double2* __restrict__ U, const double2* __restrict__ clov, float4* As,
                                   float4* Bs, int ncp, int ntc, int t, int c, bool valid) {
   float4* Ao = As + c;
   float4* Bo = Bs + (c % TC) * ntc + c / TC;
-  auto put = [&](float4* o, int k, const pc& v) { o[(size_t)k * ncp] = make_float4(v.rh, v.ih, v.rl, v.il); };
+  auto putA = [&](int k, const pc& v) {
+    Ao[(size_t)(2 * k) * ncp] = make_float4(v.rh, v.rh, v.rl, v.rl);
+    Ao[(size_t)(2 * k + 1) * ncp] = make_float4(v.ih, -v.ih, v.il, -v.il);
+  };
+  auto putB = [&](int k, const pc& v) {
+    Bo[(size_t)(2 * k) * ncp] = make_float4(v.rh, v.ih, v.rl, v.il);
+    Bo[(size_t)(2 * k + 1) * ncp] = make_float4(v.ih, v.rh, v.il, v.rl);
+  };
   if (!valid) {
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
-      put(Ao, k, pc{0.f, 0.f, 0.f, 0.f});
-      put(Bo, k, pc{0.f, 0.f, 0.f, 0.f});
+      putA(k, pc{0.f, 0.f, 0.f, 0.f});
+      putB(k, pc{0.f, 0.f, 0.f, 0.f});
     }
     return;
   }
@@ -197,7 +240,7 @@ __device__ inline void build_item(const Geom& g, const PairJob& J, const double2
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
       q[k] = split_conj(Rc[k]);
-      put(Ao, k, q[k]);
+      putA(k, q[k]);
     }
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
@@ -205,7 +248,7 @@ __device__ inline void build_item(const Geom& g, const PairJob& J, const double2
       lacc_fma(s, J.dd, q[k]);
 #pragma unroll
       for (int kp = 0; kp < 6; ++kp) lacc_fma(s, split_c(C6[k * 6 + kp]), q[kp]);
-      put(Bo, k, lacc_value(s));
+      putB(k, lacc_value(s));
     }
     return;
   }
@@ -224,7 +267,7 @@ __device__ inline void build_item(const Geom& g, const PairJob& J, const double2
 #pragma unroll
     for (int col = 0; col < 3; ++col) {
       const pc v = split_conj(Rc[b * 3 + col]);
-      put(Ao, a * 3 + col, hc == 0 ? v : neg_b(mu, a, v));
+      putA(a * 3 + col, hc == 0 ? v : neg_b(mu, a, v));
     }
     // Bt = u^dagger U_mu(x) P(x + mu)
     pc qn[3];
@@ -236,57 +279,62 @@ __device__ inline void build_item(const Geom& g, const PairJob& J, const double2
 #pragma unroll
       for (int cp = 0; cp < 3; ++cp) lacc_fma(s, split_c(Ul[col * 3 + cp]), qn[cp]);
       const pc z = lacc_value(s);
-      put(Bo, a * 3 + col, hc == 0 ? z : neg_b(mu, a, z));
+      putB(a * 3 + col, hc == 0 ? z : neg_b(mu, a, z));
     }
   }
 }
 
 // One site's rank-6 product into the tile's accumulators: a local pair sum over the six rows,
-// then one three-level addition per entry.
+// then one three-level addition per entry (lanes: real, imaginary part of the entry).
 template <int TA, int TC>
 __device__ inline void contract_site(const float4* As, const float4* Bs, int ncp, int ntc, int ta, int tc,
-                                     gacc (&accr)[TA][TC], gacc (&acci)[TA][TC]) {
-  lacc loc[TA][TC];
+                                     gacc2 (&acc)[TA][TC]) {
+  lacc2 loc[TA][TC];
 #pragma unroll
   for (int i = 0; i < TA; ++i)
 #pragma unroll
-    for (int jj = 0; jj < TC; ++jj) loc[i][jj] = lacc{0.f, 0.f, 0.f, 0.f};
+    for (int jj = 0; jj < TC; ++jj) loc[i][jj] = lacc2{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
 #pragma unroll 1  // rolled: the unrolled rank-6 body overflows the instruction cache
   for (int k = 0; k < 6; ++k) {
-    pc av[TA], bv[TC];
+    float4 a0[TA], a1[TA], b0[TC], b1[TC];
 #pragma unroll
     for (int i = 0; i < TA; ++i) {
-      const float4 v = As[(size_t)k * ncp + ta * TA + i];
-      av[i] = pc{v.x, v.y, v.z, v.w};
+      a0[i] = As[(size_t)(2 * k) * ncp + ta * TA + i];
+      a1[i] = As[(size_t)(2 * k + 1) * ncp + ta * TA + i];
     }
 #pragma unroll
     for (int jj = 0; jj < TC; ++jj) {
-      const float4 v = Bs[(size_t)k * ncp + jj * ntc + tc];
-      bv[jj] = pc{v.x, v.y, v.z, v.w};
+      b0[jj] = Bs[(size_t)(2 * k) * ncp + jj * ntc + tc];
+      b1[jj] = Bs[(size_t)(2 * k + 1) * ncp + jj * ntc + tc];
     }
 #pragma unroll
     for (int i = 0; i < TA; ++i)
 #pragma unroll
-      for (int jj = 0; jj < TC; ++jj) lacc_fmac(loc[i][jj], av[i], bv[jj]);
+      for (int jj = 0; jj < TC; ++jj) {
+        pair_fma2(loc[i][jj], make_float2(a0[i].x, a0[i].y), make_float2(a0[i].z, a0[i].w),
+                  make_float2(b0[jj].x, b0[jj].y), make_float2(b0[jj].z, b0[jj].w));
+        pair_fma2(loc[i][jj], make_float2(a1[i].x, a1[i].y), make_float2(a1[i].z, a1[i].w),
+                  make_float2(b1[jj].x, b1[jj].y), make_float2(b1[jj].z, b1[jj].w));
+      }
   }
 #pragma unroll
   for (int i = 0; i < TA; ++i)
 #pragma unroll
-    for (int jj = 0; jj < TC; ++jj) {
-      gacc_add(accr[i][jj], loc[i][jj].rh, loc[i][jj].rl);
-      gacc_add(acci[i][jj], loc[i][jj].ih, loc[i][jj].il);
-    }
+    for (int jj = 0; jj < TC; ++jj) gacc2_add(acc[i][jj], loc[i][jj]);
 }
 
 template <int TA, int TC>
-__device__ inline void write_tile(double2* P, int nc, int ta, int tc, gacc (&accr)[TA][TC], gacc (&acci)[TA][TC]) {
+__device__ inline void write_tile(double2* P, int nc, int ta, int tc, gacc2 (&acc)[TA][TC]) {
 #pragma unroll
   for (int i = 0; i < TA; ++i)
 #pragma unroll
     for (int jj = 0; jj < TC; ++jj) {
       const int a = ta * TA + i, c = tc * TC + jj;
-      if (a < nc && c < nc) P[a * nc + c] = make_double2(gacc_value(accr[i][jj]), gacc_value(acci[i][jj]));
-      accr[i][jj] = acci[i][jj] = gacc{0.f, 0.f, 0.f};
+      const gacc2& v = acc[i][jj];
+      if (a < nc && c < nc)
+        P[a * nc + c] = make_double2(((double)v.ll.x + (double)v.l.x) + (double)v.h.x,
+                                     ((double)v.ll.y + (double)v.l.y) + (double)v.h.y);
+      acc[i][jj] = gacc2{make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
     }
 }
 
@@ -304,35 +352,35 @@ assemble_pair_kernel(const double2* __restrict__ R, const double2* __restrict__ 
                      int ncp, int sb_max) {
   extern __shared__ float4 smem4[];
   const int nc = g.nc, Vb = (int)g.Vb;
-  float4* As = smem4;  // [sb][6][ncp] (rh, ih, rl, il)
-  float4* Bs = smem4 + (size_t)sb_max * 6 * ncp;
+  float4* As = smem4;  // [sb][6][2 forms][ncp]
+  float4* Bs = smem4 + (size_t)sb_max * 12 * ncp;
   const int ntc = ncp / TC, ntiles = ntc * (ncp / TA);
   const int tid = threadIdx.x;
   const int ta = tid / ntc, tc = tid % ntc;
   const PairJob J = pair_job(g, blockIdx.x, blockIdx.y, m0);
   const bool active = tid < ntiles && tile_needed<TA, TC>(J.job, g.ntv, ta, tc);
-  gacc accr[TA][TC], acci[TA][TC];
+  gacc2 acc[TA][TC];
 #pragma unroll
   for (int i = 0; i < TA; ++i)
 #pragma unroll
-    for (int j = 0; j < TC; ++j) accr[i][j] = acci[i][j] = gacc{0.f, 0.f, 0.f};
+    for (int j = 0; j < TC; ++j) acc[i][j] = gacc2{make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
   double2* P0 = part + ((J.blk * 5 + J.job) * 2 + 0) * (long long)nc * nc;
   double2* P1 = P0 + (long long)nc * nc;
   for (int t0 = 0; t0 < Vb; t0 += sb_max) {
     const int nsb = min(sb_max, Vb - t0);
     for (int pr = tid; pr < sb_max * ncp; pr += blockDim.x) {
       const int sb = pr / ncp, c = pr % ncp;
-      build_item<TC>(g, J, R, U, clov, As + (size_t)sb * 6 * ncp, Bs + (size_t)sb * 6 * ncp, ncp, ntc, t0 + sb, c,
+      build_item<TC>(g, J, R, U, clov, As + (size_t)sb * 12 * ncp, Bs + (size_t)sb * 12 * ncp, ncp, ntc, t0 + sb, c,
                      sb < nsb && c < nc);
     }
     __syncthreads();
     for (int sb = 0; sb < nsb; ++sb) {
-      if (J.job < 4 && t0 + sb == Vb - J.nface && tid < ntiles) write_tile(P0, nc, ta, tc, accr, acci);  // S_mu
-      if (active) contract_site(As + (size_t)sb * 6 * ncp, Bs + (size_t)sb * 6 * ncp, ncp, ntc, ta, tc, accr, acci);
+      if (J.job < 4 && t0 + sb == Vb - J.nface && tid < ntiles) write_tile(P0, nc, ta, tc, acc);  // S_mu
+      if (active) contract_site(As + (size_t)sb * 12 * ncp, Bs + (size_t)sb * 12 * ncp, ncp, ntc, ta, tc, acc);
     }
     __syncthreads();
   }
-  if (tid < ntiles) write_tile(J.job < 4 ? P1 : P0, nc, ta, tc, accr, acci);  // F_mu, or the self block
+  if (tid < ntiles) write_tile(J.job < 4 ? P1 : P0, nc, ta, tc, acc);  // F_mu, or the self block
 }
 
 // Warp-specialised form (nc <= 48): NCW contraction warps (a multiple of four, so that every SM
@@ -346,8 +394,8 @@ assemble_pair_ws_kernel(const double2* __restrict__ R, const double2* __restrict
                         int sb, int ncons, unsigned* err) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   amgpipe::Pipe* pp = reinterpret_cast<amgpipe::Pipe*>(smem_raw);
-  float4* buf = reinterpret_cast<float4*>(smem_raw + amgpipe::kPipeBytes);  // [2][A | B][sb][6][ncp]
-  const size_t half = (size_t)sb * 6 * ncp;
+  float4* buf = reinterpret_cast<float4*>(smem_raw + amgpipe::kPipeBytes);  // [2][A | B][sb][6][2][ncp]
+  const size_t half = (size_t)sb * 12 * ncp;
   const int nc = g.nc, Vb = (int)g.Vb;
   const int ntc = ncp / TC, ntiles = ntc * (ncp / TA);
   const int tid = threadIdx.x;
@@ -375,8 +423,8 @@ assemble_pair_ws_kernel(const double2* __restrict__ R, const double2* __restrict
       float4* Ab = buf + (size_t)b * 2 * half;
       for (int pr = bt; pr < sb * ncp; pr += kBuilders) {
         const int s = pr / ncp, c = pr % ncp;
-        build_item<TC>(g, J, R, U, clov, Ab + (size_t)s * 6 * ncp, Ab + half + (size_t)s * 6 * ncp, ncp, ntc, t0 + s,
-                       c, s < nsb && c < nc);
+        build_item<TC>(g, J, R, U, clov, Ab + (size_t)s * 12 * ncp, Ab + half + (size_t)s * 12 * ncp, ncp, ntc,
+                       t0 + s, c, s < nsb && c < nc);
       }
       amgpipe::mbar_arrive(&pp->full[b]);
     }
@@ -386,11 +434,11 @@ assemble_pair_ws_kernel(const double2* __restrict__ R, const double2* __restrict
   const int ta = tid / ntc, tc = tid % ntc;
   const bool tile = tid < ntiles;
   const bool active = tile && tile_needed<TA, TC>(J.job, g.ntv, ta, tc);
-  gacc accr[TA][TC], acci[TA][TC];
+  gacc2 acc[TA][TC];
 #pragma unroll
   for (int i = 0; i < TA; ++i)
 #pragma unroll
-    for (int j = 0; j < TC; ++j) accr[i][j] = acci[i][j] = gacc{0.f, 0.f, 0.f};
+    for (int j = 0; j < TC; ++j) acc[i][j] = gacc2{make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
   double2* P0 = part + ((J.blk * 5 + J.job) * 2 + 0) * (long long)nc * nc;
   double2* P1 = P0 + (long long)nc * nc;
   for (int ch = 0; ch < nch; ++ch) {
@@ -402,12 +450,12 @@ assemble_pair_ws_kernel(const double2* __restrict__ R, const double2* __restrict
     const int t0 = ch * sb, nsb = min(sb, Vb - t0);
     const float4* Ab = buf + (size_t)b * 2 * half;
     for (int s = 0; s < nsb; ++s) {
-      if (J.job < 4 && t0 + s == Vb - J.nface && tile) write_tile(P0, nc, ta, tc, accr, acci);  // S_mu
-      if (active) contract_site(Ab + (size_t)s * 6 * ncp, Ab + half + (size_t)s * 6 * ncp, ncp, ntc, ta, tc, accr, acci);
+      if (J.job < 4 && t0 + s == Vb - J.nface && tile) write_tile(P0, nc, ta, tc, acc);  // S_mu
+      if (active) contract_site(Ab + (size_t)s * 12 * ncp, Ab + half + (size_t)s * 12 * ncp, ncp, ntc, ta, tc, acc);
     }
     amgpipe::mbar_arrive(&pp->empty[b]);
   }
-  if (tile) write_tile(J.job < 4 ? P1 : P0, nc, ta, tc, accr, acci);  // F_mu, or the self block
+  if (tile) write_tile(J.job < 4 ? P1 : P0, nc, ta, tc, acc);  // F_mu, or the self block
 }
 
 int round_up_i(int a, int b) { return (a + b - 1) / b * b; }
@@ -427,8 +475,8 @@ amg_status launch_ws(const Geom& g, const double2* R, const double2* U, const do
   const int ncp = round_up_i(g.nc, lcm_i(TA, TC));
   const int ntiles = (ncp / TA) * (ncp / TC);
   const int ncons = round_up_i(ntiles, 128);
-  const int sb = 8;
-  const size_t sm = amgpipe::kPipeBytes + (size_t)2 * 2 * sb * 6 * ncp * sizeof(float4);
+  const int sb = 4;
+  const size_t sm = amgpipe::kPipeBytes + (size_t)2 * 2 * sb * 12 * ncp * sizeof(float4);
   AMG_CUDA_TRY(cudaFuncSetAttribute(assemble_pair_ws_kernel<TA, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   assemble_pair_ws_kernel<TA, TC><<<dim3((unsigned)g.Vc, 5), ncons + kBuilders, sm, st>>>(R, U, clov, part, g, m0, ncp,
                                                                                          sb, ncons, err);
@@ -477,8 +525,8 @@ amg_status amg_internal_assemble_pair(const Geom& g, const double2* R, const dou
   const int T = round_up_i(ntiles, 32);
   if (T > 512) return AMG_ERR_UNSUPPORTED;
   int sb = 16;  // sites per chunk: one CTA per SM (the register file), so most of shared memory
-  while (sb > 1 && (size_t)sb * 12 * ncp * sizeof(float4) > 200 * 1024) sb >>= 1;
-  const size_t sm = (size_t)sb * 12 * ncp * sizeof(float4);
+  while (sb > 1 && (size_t)sb * 24 * ncp * sizeof(float4) > 200 * 1024) sb >>= 1;
+  const size_t sm = (size_t)sb * 24 * ncp * sizeof(float4);
   AMG_CUDA_TRY(cudaFuncSetAttribute(assemble_pair_kernel<2, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   assemble_pair_kernel<2, 4><<<dim3((unsigned)g.Vc, 5), T, sm, st>>>(R, U, clov, part, g, m0, ncp, sb);
   AMG_LAUNCH_CHECK();
