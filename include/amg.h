@@ -99,7 +99,9 @@ typedef struct amg_coarse *amg_handle;
  * Builds the clover field C from d_U, orthonormalises the test vectors on
  * every aggregate A_i^h by block classical Gram-Schmidt (Sec. 3, "Gram-Schmidt
  * on aggregates"), assembles the self block and the four forward blocks of
- * D_c = R D P (Eq. cgo, Alg. 7) and fills the four backward blocks from
+ * D_c = R D P (Eq. cgo, Alg. 7; all 2 ntv columns of P at once, as
+ * Sec. 3 suggests, in FP64 or, with setup_arith = AMG_SETUP_F32PAIR, in pairs
+ * of FP32 numbers) and fills the four backward blocks from
  * Eq. dagger, then stores R and D_c in r_prec / link_prec (Sec. 3: D_c may be
  * kept in half precision).  The handle owns every buffer it allocates; the
  * inputs are read only and may be freed once the call returns.  This call
