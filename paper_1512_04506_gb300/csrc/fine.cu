@@ -69,9 +69,10 @@ __device__ __forceinline__ void adagmul(int mu, C v0, C v1, C& o0, C& o1) {
   else { o0 = v0; o1 = v1; }
 }
 
-// out += -1/2 (1 - g_mu) U p   (FWD) or   out += -1/2 (1 + g_mu) U^dag p   (!FWD); p, out: [spin][colour]
+// out += -1/2 (1 - g_mu) U p   (FWD) or   out += -1/2 (1 + g_mu) U^dag p   (!FWD); p, out: [spin][colour];
+// u: the link's 3x3 entries
 template <bool FWD, int mu, typename C>
-__device__ __forceinline__ void hop(const C* __restrict__ U, const C p[12], C out[12]) {
+__device__ __forceinline__ void hop_u(const C u[9], const C p[12], C out[12]) {
   C h[2][3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -80,9 +81,6 @@ __device__ __forceinline__ void hop(const C* __restrict__ U, const C p[12], C ou
     h[0][c] = FWD ? zsub(p[c], a0) : zadd(p[c], a0);
     h[1][c] = FWD ? zsub(p[3 + c], a1) : zadd(p[3 + c], a1);
   }
-  C u[9];
-#pragma unroll
-  for (int k = 0; k < 9; ++k) u[k] = U[k];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     C w0 = zzero<C>(), w1 = zzero<C>();
@@ -109,6 +107,14 @@ __device__ __forceinline__ void hop(const C* __restrict__ U, const C p[12], C ou
       out[9 + a] = zsub(out[9 + a], zscale(d1, 0.5));
     }
   }
+}
+
+template <bool FWD, int mu, typename C>
+__device__ __forceinline__ void hop(const C* __restrict__ U, const C p[12], C out[12]) {
+  C u[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) u[k] = U[k];
+  hop_u<FWD, mu>(u, p, out);
 }
 
 // out = (4 + m0) p + C(x) p for the site whose clover blocks start at Cl ([2][6][6])
@@ -226,10 +232,12 @@ __global__ void __launch_bounds__(128) dirac_kernel(const typename Cx<T>::type* 
   }
 }
 
-// Block sum of three values over the CTA (all threads call it; every thread gets the sums).  The
-// warp sums run in the values' own precision, the CTA sum in FP64.
-template <typename T>
-__device__ __forceinline__ void cta_sum3(T v[3], double out[3], double* red) {
+// MR coefficient alpha = <p, rho> / <p, p> from per-thread partial sums v = (<p,p>, Re, Im <p,rho>):
+// warp sums in the values' precision, the CTA sum and the division in FP64 by one thread (FP64 is
+// slow on this GPU: every thread doing them had kept the FP64 pipe busy), alpha broadcast through
+// shared memory.  ok = false when <p, p> = 0.  red: 3 doubles per warp + 3 doubles.
+template <typename T, typename C>
+__device__ __forceinline__ void cta_alpha(T v[3], double* red, C& al, bool& ok) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
 #pragma unroll
   for (int k = 0; k < 3; ++k)
@@ -239,11 +247,22 @@ __device__ __forceinline__ void cta_sum3(T v[3], double out[3], double* red) {
   if (lane == 0)
     for (int k = 0; k < 3; ++k) red[warp * 3 + k] = (double)v[k];
   __syncthreads();
-  for (int k = 0; k < 3; ++k) {
-    double s = 0;
-    for (int w = 0; w < nw; ++w) s += red[w * 3 + k];
-    out[k] = s;
+  double* out = red + 3 * nw;
+  if (threadIdx.x == 0) {
+    double sp = 0, sr = 0, si = 0;
+    for (int w = 0; w < nw; ++w) {
+      sp += red[w * 3];
+      sr += red[w * 3 + 1];
+      si += red[w * 3 + 2];
+    }
+    out[0] = sp > 0 ? sr / sp : 0.0;
+    out[1] = sp > 0 ? si / sp : 0.0;
+    red[3 * nw + 2] = sp > 0 ? 1.0 : 0.0;
   }
+  __syncthreads();
+  al.x = (T)out[0];
+  al.y = (T)out[1];
+  ok = out[2] != 0.0;
 }
 
 // Intra-block hops of the block operator B at local site t: neighbours' rho from shared memory
@@ -267,7 +286,7 @@ __device__ __forceinline__ void block_hops_mu(const FineGeom& g, const C* __rest
 
 // One SAP half sweep on the blocks of one colour: x += MR_{n_mr}(B_b, (y - D x)|_b) per block.
 // grid (Vc / 2, nrhs); blockDim >= Vb (threads past Vb only join the sums); dynamic smem: rho
-// [12][Vb] + 3 doubles per warp.
+// [12][Vb] + 3 doubles per warp + 3 doubles.
 template <typename T>
 __global__ void __launch_bounds__(256) sap_kernel(const typename Cx<T>::type* __restrict__ U,
                                                   const typename Cx<T>::type* __restrict__ Cl,
@@ -339,18 +358,169 @@ __global__ void __launch_bounds__(256) sap_kernel(const typename Cx<T>::type* __
         v[2] += o[q].x * rr[q].y - o[q].y * rr[q].x;      // Im <p, rho>
       }
     }
-    double sums[3];
-    cta_sum3(v, sums, red);  // also orders every read of rho before the writes below
-    if (act && sums[0] > 0) {
-      C al;
-      al.x = (T)(sums[1] / sums[0]);
-      al.y = (T)(sums[2] / sums[0]);
+    C al;
+    bool ok;
+    cta_alpha(v, red, al, ok);  // also orders every read of rho before the writes below
+    if (act && ok) {
 #pragma unroll
       for (int q = 0; q < 12; ++q) {
         zfma(e[q], al, rr[q]);
         C ap = zzero<C>();
         zfma(ap, al, o[q]);
         rho[q * g.Vb + t] = zsub(rr[q], ap);
+      }
+    }
+    __syncthreads();
+  }
+  if (act) {
+#pragma unroll
+    for (int q = 0; q < 12; ++q) {
+      const long long idx = (s * 12 + q) * nrhs + r;
+      x[idx] = zadd(x[idx], e[q]);
+    }
+  }
+}
+
+// The same half sweep with the block's links and clover staged in shared memory once, so that
+// the MR steps read no global memory (FP32; a 4^4 block takes 74 KB of links, 86 KB of clover and
+// 25 KB of rho).  Layouts are component-major, [component][Vb], so that the threads of a warp (one
+// site each) read consecutive words: links [mu][9][Vb]; clover per chirality as its upper triangle
+// with the diagonal, [2][21][Vb] (the blocks are Hermitian, C_ba = conj(C_ab)); rho [12][Vb].
+__device__ __forceinline__ int tri_index(int a, int b) { return a * 6 - a * (a - 1) / 2 + (b - a); }  // a <= b
+
+__device__ __forceinline__ void site_term_packed(const float2* Cs, int Vb, int t, float mass, const float2 p[12],
+                                                 float2 out[12]) {
+#pragma unroll
+  for (int hh = 0; hh < 2; ++hh) {
+    float2 c[21];
+#pragma unroll
+    for (int k = 0; k < 21; ++k) c[k] = Cs[(hh * 21 + k) * Vb + t];
+#pragma unroll
+    for (int a = 0; a < 6; ++a) {
+      float2 acc = zscale(p[hh * 6 + a], mass);
+#pragma unroll
+      for (int b = 0; b < 6; ++b) {
+        if (a <= b) zfma(acc, c[tri_index(a, b)], p[hh * 6 + b]);
+        else zfmac(acc, c[tri_index(b, a)], p[hh * 6 + b]);
+      }
+      out[hh * 6 + a] = acc;
+    }
+  }
+}
+
+template <int mu>
+__device__ __forceinline__ void block_hops_smem(const float2* Us, const float2* rho, int Vb, int t, const int lc[4],
+                                                int bmu, int stride, float2 o[12]) {
+  float2 p[12], u[9];
+  if (lc[mu] + 1 < bmu) {
+#pragma unroll
+    for (int q = 0; q < 12; ++q) p[q] = rho[q * Vb + t + stride];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) u[k] = Us[(mu * 9 + k) * Vb + t];
+    hop_u<true, mu>(u, p, o);
+  }
+  if (lc[mu] > 0) {
+#pragma unroll
+    for (int q = 0; q < 12; ++q) p[q] = rho[q * Vb + t - stride];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) u[k] = Us[(mu * 9 + k) * Vb + t - stride];
+    hop_u<false, mu>(u, p, o);
+  }
+}
+
+__global__ void __launch_bounds__(256, 1) sap_smem_kernel(const float2* __restrict__ U, const float2* __restrict__ Cl,
+                                                          const float2* __restrict__ y, float2* __restrict__ x,
+                                                          FineGeom g, float mass, int nrhs, int colour, int n_mr) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int Vb = g.Vb;
+  float2* Us = reinterpret_cast<float2*>(smem);
+  float2* Cs = Us + (size_t)36 * Vb;
+  float2* rho = Cs + (size_t)42 * Vb;
+  double* red = reinterpret_cast<double*>(rho + (size_t)12 * Vb);
+  const int r = blockIdx.y;
+  const long long k = blockIdx.x;
+  const int half = g.Lc[0] / 2;
+  long long row = k / half;
+  const int Y = (int)(row % g.Lc[1]);
+  row /= g.Lc[1];
+  const int Z = (int)(row % g.Lc[2]);
+  const int Tt = (int)(row / g.Lc[2]);
+  const int X = 2 * (int)(k % half) + ((colour + Y + Z + Tt) & 1);
+  const int t = threadIdx.x;
+  const bool act = t < Vb;
+  int lc[4] = {0, 0, 0, 0}, xs[4] = {0, 0, 0, 0};
+  long long s = 0;
+  if (act) {
+    lc[0] = t % g.B[0];
+    lc[1] = (t / g.B[0]) % g.B[1];
+    lc[2] = (t / (g.B[0] * g.B[1])) % g.B[2];
+    lc[3] = t / (g.B[0] * g.B[1] * g.B[2]);
+    xs[0] = X * g.B[0] + lc[0];
+    xs[1] = Y * g.B[1] + lc[1];
+    xs[2] = Z * g.B[2] + lc[2];
+    xs[3] = Tt * g.B[3] + lc[3];
+    s = site_of(g, xs);
+  }
+  const int st1 = g.B[0], st2 = g.B[0] * g.B[1], st3 = g.B[0] * g.B[1] * g.B[2];
+  float2 o[12], e[12];
+  if (act) {
+    // stage this site's links and clover
+    const float4* U4 = reinterpret_cast<const float4*>(U + s * 36);
+#pragma unroll
+    for (int q = 0; q < 18; ++q) {
+      const float4 f = __ldg(U4 + q);
+      Us[(2 * q) * Vb + t] = make_float2(f.x, f.y);
+      Us[(2 * q + 1) * Vb + t] = make_float2(f.z, f.w);
+    }
+#pragma unroll
+    for (int hh = 0; hh < 2; ++hh)
+#pragma unroll
+      for (int a = 0; a < 6; ++a)
+#pragma unroll
+        for (int b = a; b < 6; ++b) Cs[(hh * 21 + tri_index(a, b)) * Vb + t] = __ldg(Cl + s * 72 + (hh * 6 + a) * 6 + b);
+    // residual r = y - D x on this site (full D: neighbours outside the block have the other colour)
+    float2 p[12];
+    load12(x, s, nrhs, r, p);
+    site_term(Cl + s * 72, mass, p, o);
+    all_hops(g, U, x, s, xs, nrhs, r, o);
+    load12(y, s, nrhs, r, p);
+#pragma unroll
+    for (int q = 0; q < 12; ++q) {
+      rho[q * Vb + t] = zsub(p[q], o[q]);
+      e[q] = zzero<float2>();
+    }
+  }
+  __syncthreads();
+#pragma unroll 1
+  for (int it = 0; it < n_mr; ++it) {
+    // p = B rho at this site: site term plus the hops that stay inside the block
+    float v[3] = {0, 0, 0};
+    float2 rr[12];
+    if (act) {
+#pragma unroll
+      for (int q = 0; q < 12; ++q) rr[q] = rho[q * Vb + t];
+      site_term_packed(Cs, Vb, t, mass, rr, o);
+      block_hops_smem<0>(Us, rho, Vb, t, lc, g.B[0], 1, o);
+      block_hops_smem<1>(Us, rho, Vb, t, lc, g.B[1], st1, o);
+      block_hops_smem<2>(Us, rho, Vb, t, lc, g.B[2], st2, o);
+      block_hops_smem<3>(Us, rho, Vb, t, lc, g.B[3], st3, o);
+#pragma unroll
+      for (int q = 0; q < 12; ++q) {
+        v[0] += o[q].x * o[q].x + o[q].y * o[q].y;        // <p, p>
+        v[1] += o[q].x * rr[q].x + o[q].y * rr[q].y;      // Re <p, rho>
+        v[2] += o[q].x * rr[q].y - o[q].y * rr[q].x;      // Im <p, rho>
+      }
+    }
+    float2 al;
+    bool ok;
+    cta_alpha(v, red, al, ok);  // also orders every read of rho before the writes below
+    if (act && ok) {
+#pragma unroll
+      for (int q = 0; q < 12; ++q) {
+        zfma(e[q], al, rr[q]);
+        float2 ap = zzero<float2>();
+        zfma(ap, al, o[q]);
+        rho[q * Vb + t] = zsub(rr[q], ap);
       }
     }
     __syncthreads();
@@ -534,7 +704,24 @@ template <typename T>
 amg_status launch_sap(amg_coarse* h, const void* y, void* x, int nrhs, int n_cycles, int n_mr, cudaStream_t st) {
   using C = typename Cx<T>::type;
   const int threads = (h->g.Vb + 31) / 32 * 32;
-  const size_t smem = (size_t)h->g.Vb * 12 * sizeof(C) + (size_t)(threads / 32) * 3 * sizeof(double);
+  if (sizeof(T) == 4) {
+    // links, clover and rho of a block in shared memory
+    const size_t sm2 = (size_t)h->g.Vb * (36 + 42 + 12) * sizeof(float2) + (size_t)(threads / 32 + 1) * 3 * sizeof(double);
+    if (threads <= 256 && sm2 <= 227 * 1024) {
+      AMG_CUDA_TRY(cudaFuncSetAttribute(sap_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
+      const dim3 grid((unsigned)(h->g.Vc / 2), (unsigned)nrhs);
+      const float mass = (float)(4.0 + h->p.m0);
+      for (int c = 0; c < n_cycles; ++c)
+        for (int colour = 0; colour < 2; ++colour) {
+          sap_smem_kernel<<<grid, threads, sm2, st>>>((const float2*)h->fU, (const float2*)h->fC, (const float2*)y,
+                                                      (float2*)x, fine_geom(h), mass, nrhs, colour, n_mr);
+          AMG_LAUNCH_CHECK();
+          h->launches++;
+        }
+      return AMG_OK;
+    }
+  }
+  const size_t smem = (size_t)h->g.Vb * 12 * sizeof(C) + (size_t)(threads / 32 + 1) * 3 * sizeof(double);
   if (threads > 256 || smem > 227 * 1024) return AMG_ERR_UNSUPPORTED;
   AMG_CUDA_TRY(cudaFuncSetAttribute(sap_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const dim3 grid((unsigned)(h->g.Vc / 2), (unsigned)nrhs);
