@@ -55,6 +55,9 @@ TRAFFIC_MRHS_FP32 = 1461702400
 # DRAM traffic / algorithmic bytes of the fused batch launch, from the reduced-volume capture
 # (profiles/batch_kernel_small_mixed.md); the full launch's traffic is taken in that proportion
 BATCH_TRAFFIC_RATIO = 0.990
+# DRAM traffic / algorithmic bytes of one SAP half sweep, from the 16^4 capture
+# (profiles/sap_16x4.md: 42.94 MB for 65,536 sites x 624 B); the 32^4 launch is taken in proportion
+SAP_TRAFFIC_RATIO = 1.050
 METRIC = "coarse-grid correction GB/s & % HBM roofline; batched-mixed vs plain speedup"
 WORKLOAD = "fp32_32^4_b4_ntv20: 32^4 Wilson-clover, 4^4 blocks -> 8^4 coarse, Ntv=20, 1 RHS, " \
            "FP64 setup, FP32 R and D_c; step = R y, FGMRES(30) to 0.05 (<=200 applies), P x_c"
@@ -734,9 +737,11 @@ def run_vcycle(args):
                                "(FGMRES(30) to 0.05) + %d SAP cycles of %d MR steps per 4^4 block; FP32" % (n_smoother, n_mr),
                    "bytes_per_step": step_bytes, "coarse_applies": applies, "n_smoother": n_smoother, "n_mr": n_mr,
                    "l2": "256 MB flush before each step"},
-        "roofline": {"bound": "hbm", "kernel": "sap_kernel<float> (one half sweep: residual + %d MR steps per block)"
-                     % n_mr, "achieved": round(sap_gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                     "frac": round(sap_gbs / peaks["hbm_gbs"], 4), "peak_source": src, "traffic": None,
+        "roofline": {"bound": "hbm", "kernel": "sap_smem_kernel (one half sweep: residual + %d MR steps per block, "
+                     "links and clover in shared memory)" % n_mr, "achieved": round(sap_gbs, 1), "peak": peaks["hbm_gbs"],
+                     "unit": "GB/s", "frac": round(sap_gbs / peaks["hbm_gbs"], 4), "peak_source": src,
+                     "traffic": round(SAP_TRAFFIC_RATIO * half_bytes) if not args.lattice else None,
+                     "traffic_note": "16^4 capture's traffic / algorithmic bytes x this launch's bytes",
                      "bytes_per_launch": half_bytes, "avg_launch_us": round(t_sap * 1e6, 2),
                      "step_share": round(2 * n_smoother * t_sap / (t / args.steps), 3)},
         "kernels": {"dirac": {"us": round(t_d * 1e6, 1), "GB/s": round(d_gbs, 1),
