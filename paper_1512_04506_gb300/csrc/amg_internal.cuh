@@ -219,6 +219,8 @@ amg_status amg_internal_setup(amg_coarse* h, const double2* U, const double2* tv
 // assembly partial sums ([Vc][5 jobs][2 slots][nc][nc], the layout combine_kernel reads) in pairs of floats
 amg_status amg_internal_assemble_pair(const Geom& g, const double2* R, const double2* U, const double2* clov,
                                       double2* part, double m0, unsigned* err, cudaStream_t st);
+// Gram-Schmidt per aggregate in pairs of floats (AMG_ERR_UNSUPPORTED above 1536 entries per aggregate)
+amg_status amg_internal_gs_pair(const Geom& g, const double2* tv, double2* R, unsigned* err, cudaStream_t st);
 amg_status amg_internal_restrict(amg_coarse* h, const void* y, void* yc, int nrhs, cudaStream_t s);
 amg_status amg_internal_apply(amg_coarse* h, const void* xc, void* yc, int nrhs, cudaStream_t s);
 amg_status amg_internal_prolong(amg_coarse* h, const void* xc, void* x, int nrhs, cudaStream_t s);

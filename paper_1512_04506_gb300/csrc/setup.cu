@@ -602,11 +602,15 @@ amg_status amg_internal_setup(amg_coarse* h, const double2* U, const double2* tv
   }
   AMG_CUDA_TRY(cudaEventRecord(ev[1], st));
   // Gram-Schmidt, one CTA per aggregate
-  {
+  amg_status gs_pair = AMG_ERR_UNSUPPORTED;
+  if (h->p.setup_arith == AMG_SETUP_F32PAIR) gs_pair = amg_internal_gs_pair(g, tv, h->R64, h->err, st);
+  if (gs_pair == AMG_ERR_UNSUPPORTED) {
     int T = round_up(g.nagg < 256 ? g.nagg : 256, 32);
     if ((g.nagg + T - 1) / T > GS_EMAX) return AMG_ERR_UNSUPPORTED;
     gs_kernel<<<(unsigned)(g.Vc * 2), T, 0, st>>>(tv, h->R64, g, h->err);
     AMG_LAUNCH_CHECK();
+  } else if (gs_pair != AMG_OK) {
+    return gs_pair;
   }
   AMG_CUDA_TRY(cudaEventRecord(ev[2], st));
   // assembly

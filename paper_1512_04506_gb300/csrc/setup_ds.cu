@@ -95,20 +95,6 @@ __device__ __forceinline__ pc lacc_value(const lacc& s) {  // normalised pair (|
   two_sum(s.ih, s.il, r.ih, r.il);
   return r;
 }
-// three-level accumulator of one real component
-struct gacc {
-  float h, l, ll;
-};
-__device__ __forceinline__ void gacc_add(gacc& g, float h, float l) {
-  float s, t, u, w, v, x;
-  two_sum(g.h, h, s, t);
-  g.h = s;
-  two_sum(g.l, l, u, w);
-  two_sum(u, t, v, x);
-  g.l = v;
-  g.ll = __fadd_rn(g.ll, __fadd_rn(w, x));
-}
-__device__ __forceinline__ double gacc_value(const gacc& g) { return ((double)g.ll + (double)g.l) + (double)g.h; }
 
 // The same operations on (real, imaginary) lane pairs: one packed FP32x2 instruction per pair
 // (the FP32 pipes run a packed instruction at the rate of two scalar ones, but it takes one
@@ -458,6 +444,237 @@ assemble_pair_ws_kernel(const double2* __restrict__ R, const double2* __restrict
   if (tile) write_tile(J.job < 4 ? P1 : P0, nc, ta, tc, acc);  // F_mu, or the self block
 }
 
+// ------------------------------------------------------------------ Gram-Schmidt in pairs
+// The FP64 kernel's algorithm (block classical Gram-Schmidt on column blocks of 4, each projection
+// applied twice, then the block's columns one by one, again twice) with every value a pair of
+// floats.  One CTA of up to 512 threads per aggregate; element n of the aggregate in thread n mod T
+// (at most GS_PE elements per thread).  Block sums: pair sums per thread, warp shuffles with pair
+// additions (TwoSum on both parts), then one warp over the warps' partial sums.
+constexpr int GS_PNB = 4;  // columns per block
+constexpr int GS_PKG = 2;  // earlier columns per dot-product round
+constexpr int GS_PE = 3;   // elements per thread: aggregates of up to 3 x 512 = 1536 = 6 x 4^4 entries
+
+__device__ __forceinline__ void pair_add(float& h, float& l, float h2, float l2) {
+  float s, t, u, w;
+  two_sum(h, h2, s, t);
+  two_sum(l, l2, u, w);
+  t = __fadd_rn(t, u);
+  two_sum(s, t, h, l);
+  l = __fadd_rn(l, w);
+}
+__device__ __forceinline__ void pc_add(pc& a, const pc& b) {
+  pair_add(a.rh, a.rl, b.rh, b.rl);
+  pair_add(a.ih, a.il, b.ih, b.il);
+}
+__device__ __forceinline__ pc pc_shfl_xor(const pc& a, int o) {
+  return pc{__shfl_xor_sync(0xffffffffu, a.rh, o), __shfl_xor_sync(0xffffffffu, a.ih, o),
+            __shfl_xor_sync(0xffffffffu, a.rl, o), __shfl_xor_sync(0xffffffffu, a.il, o)};
+}
+// CTA sum of K complex pairs; every thread gets the sums.  red: [32][K] float4.
+template <int K>
+__device__ inline void pc_block_sum(pc (&v)[K], float4* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+#pragma unroll
+    for (int o = 16; o; o >>= 1) pc_add(v[k], pc_shfl_xor(v[k], o));
+  __syncthreads();  // red may still be read by the previous call
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < K; ++k) red[warp * K + k] = make_float4(v[k].rh, v[k].ih, v[k].rl, v[k].il);
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      pc t = pc{0.f, 0.f, 0.f, 0.f};
+      if (lane < nw) {
+        const float4 f = red[lane * K + k];
+        t = pc{f.x, f.y, f.z, f.w};
+      }
+#pragma unroll
+      for (int o = 16; o; o >>= 1) pc_add(t, pc_shfl_xor(t, o));
+      v[k] = t;
+    }
+  }
+  __syncthreads();
+  if (warp == 0)
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+      if (lane == k) red[32 * K + k] = make_float4(v[k].rh, v[k].ih, v[k].rl, v[k].il);
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const float4 f = red[32 * K + k];
+    v[k] = pc{f.x, f.y, f.z, f.w};
+  }
+}
+__device__ __forceinline__ pc pc_mul_sub(const pc& w, const pc& q, const pc& cf) {  // w - q cf
+  lacc s{w.rh, w.rl, w.ih, w.il};
+  lacc_fma(s, pc{-q.rh, -q.ih, -q.rl, -q.il}, cf);
+  return lacc_value(s);
+}
+
+__global__ void __launch_bounds__(512) gs_pair_kernel(const double2* __restrict__ tv, double2* __restrict__ R, Geom g,
+                                                      unsigned* err) {
+  __shared__ float4 red[32 * GS_PKG * GS_PNB + GS_PKG * GS_PNB];
+  __shared__ float4 coef[AMG_MAX_NTV * GS_PNB];
+  const long long agg = blockIdx.x;
+  const long long blk = agg >> 1;
+  const int h = (int)(agg & 1);
+  const int T = blockDim.x, tid = threadIdx.x, ntv = g.ntv, nagg = g.nagg;
+  long long tvoff[GS_PE];
+  bool valid[GS_PE];
+#pragma unroll
+  for (int e = 0; e < GS_PE; ++e) {
+    const int n = tid + e * T;
+    valid[e] = n < nagg;
+    tvoff[e] = 0;
+    if (valid[e]) {
+      const int sl = n / 6, a = (n % 6) / 3, col = n % 3;
+      const long long site = block_site(g, blk, sl);
+      tvoff[e] = ((site * 4 + 2 * h + a) * 3 + col) * (long long)ntv;
+    }
+  }
+  double2* Rblk = R + agg * (long long)ntv * nagg;
+  const pc zero{0.f, 0.f, 0.f, 0.f};
+  pc w[GS_PE][GS_PNB];
+  for (int j0 = 0; j0 < ntv; j0 += GS_PNB) {
+    const int nb = min(GS_PNB, ntv - j0);
+#pragma unroll
+    for (int e = 0; e < GS_PE; ++e)
+#pragma unroll
+      for (int c = 0; c < GS_PNB; ++c) w[e][c] = (valid[e] && c < nb) ? split_c(tv[tvoff[e] + j0 + c]) : zero;
+    double n0[GS_PNB];
+    {
+      pc nn[GS_PNB];
+#pragma unroll
+      for (int c = 0; c < GS_PNB; ++c) {
+        lacc s{0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int e = 0; e < GS_PE; ++e) lacc_fmac(s, w[e][c], w[e][c]);
+        nn[c] = lacc_value(s);
+      }
+      pc_block_sum<GS_PNB>(nn, red);
+#pragma unroll
+      for (int c = 0; c < GS_PNB; ++c) n0[c] = (double)nn[c].rh + (double)nn[c].rl;
+    }
+    // projection against the earlier columns (all coefficients from the same vectors), twice
+    for (int pass = 0; pass < 2 && j0 > 0; ++pass) {
+      for (int k0 = 0; k0 < j0; k0 += GS_PKG) {
+        // this thread's (at most GS_PE) products per entry in one unnormalised pair each
+        lacc da[GS_PKG * GS_PNB];
+#pragma unroll
+        for (int q = 0; q < GS_PKG * GS_PNB; ++q) da[q] = lacc{0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int e = 0; e < GS_PE; ++e) {
+          if (!valid[e]) continue;
+          const int n = tid + e * T;
+#pragma unroll
+          for (int kk = 0; kk < GS_PKG; ++kk) {
+            const pc r = split_c(Rblk[(long long)(k0 + kk) * nagg + n]);  // conj(q_k)
+#pragma unroll
+            for (int c = 0; c < GS_PNB; ++c) lacc_fma(da[kk * GS_PNB + c], r, w[e][c]);
+          }
+        }
+        pc d[GS_PKG * GS_PNB];
+#pragma unroll
+        for (int q = 0; q < GS_PKG * GS_PNB; ++q) d[q] = lacc_value(da[q]);
+        pc_block_sum<GS_PKG * GS_PNB>(d, red);
+#pragma unroll
+        for (int q = 0; q < GS_PKG * GS_PNB; ++q)
+          if (tid == q && k0 + q / GS_PNB < j0) coef[k0 * GS_PNB + q] = make_float4(d[q].rh, d[q].ih, d[q].rl, d[q].il);
+      }
+      __syncthreads();
+      // w -= sum_k q_k coef_k in unnormalised pairs, renormalised every 8 columns
+      lacc wa[GS_PE][GS_PNB];
+#pragma unroll
+      for (int e = 0; e < GS_PE; ++e)
+#pragma unroll
+        for (int c = 0; c < GS_PNB; ++c) wa[e][c] = lacc{w[e][c].rh, w[e][c].rl, w[e][c].ih, w[e][c].il};
+      for (int k = 0; k < j0; ++k) {
+#pragma unroll
+        for (int e = 0; e < GS_PE; ++e) {
+          if (!valid[e]) continue;
+          const int n = tid + e * T;
+          const pc q = split_conj(Rblk[(long long)k * nagg + n]);
+          const pc mq{-q.rh, -q.ih, -q.rl, -q.il};
+#pragma unroll
+          for (int c = 0; c < GS_PNB; ++c) {
+            const float4 f = coef[k * GS_PNB + c];
+            lacc_fma(wa[e][c], mq, pc{f.x, f.y, f.z, f.w});
+          }
+        }
+        if ((k & 7) == 7)
+#pragma unroll
+          for (int e = 0; e < GS_PE; ++e)
+#pragma unroll
+            for (int c = 0; c < GS_PNB; ++c) {
+              const pc v = lacc_value(wa[e][c]);
+              wa[e][c] = lacc{v.rh, v.rl, v.ih, v.il};
+            }
+      }
+#pragma unroll
+      for (int e = 0; e < GS_PE; ++e)
+#pragma unroll
+        for (int c = 0; c < GS_PNB; ++c) w[e][c] = lacc_value(wa[e][c]);
+      __syncthreads();
+    }
+    // orthonormalise inside the block
+#pragma unroll
+    for (int c = 0; c < GS_PNB; ++c) {
+      if (c >= nb) break;
+      for (int pass = 0; pass < 2 && c > 0; ++pass) {
+        pc d[GS_PNB];
+#pragma unroll
+        for (int cp = 0; cp < GS_PNB; ++cp) {
+          lacc s{0.f, 0.f, 0.f, 0.f};
+          if (cp < c)
+#pragma unroll
+            for (int e = 0; e < GS_PE; ++e) lacc_fmac(s, w[e][cp], w[e][c]);
+          d[cp] = lacc_value(s);
+        }
+        pc_block_sum<GS_PNB>(d, red);
+#pragma unroll
+        for (int e = 0; e < GS_PE; ++e)
+#pragma unroll
+          for (int cp = 0; cp < GS_PNB; ++cp)
+            if (cp < c) w[e][c] = pc_mul_sub(w[e][c], w[e][cp], d[cp]);
+      }
+      pc nn[1];
+      {
+        lacc s{0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int e = 0; e < GS_PE; ++e) lacc_fmac(s, w[e][c], w[e][c]);
+        nn[0] = lacc_value(s);
+      }
+      pc_block_sum<1>(nn, red);
+      const double nrm = sqrt((double)nn[0].rh + (double)nn[0].rl);
+      if (!(nrm > 1e-12 * sqrt(n0[c]))) {
+        if (tid == 0) atomicOr(err, AMG_EBIT_RANK);
+      }
+      pc inv{0.f, 0.f, 0.f, 0.f};
+      split_double(nrm > 0 ? 1.0 / nrm : 0.0, inv.rh, inv.rl);
+#pragma unroll
+      for (int e = 0; e < GS_PE; ++e) {
+        lacc s{0.f, 0.f, 0.f, 0.f};
+        lacc_fma(s, inv, w[e][c]);
+        w[e][c] = lacc_value(s);
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < GS_PE; ++e) {
+      if (!valid[e]) continue;
+      const int n = tid + e * T;
+#pragma unroll
+      for (int c = 0; c < GS_PNB; ++c)
+        if (c < nb)
+          Rblk[(long long)(j0 + c) * nagg + n] =
+              make_double2((double)w[e][c].rh + (double)w[e][c].rl, -((double)w[e][c].ih + (double)w[e][c].il));
+    }
+    __syncthreads();
+  }
+}
+
 int round_up_i(int a, int b) { return (a + b - 1) / b * b; }
 int lcm_i(int a, int b) {
   int x = a, y = b;
@@ -529,6 +746,17 @@ amg_status amg_internal_assemble_pair(const Geom& g, const double2* R, const dou
   const size_t sm = (size_t)sb * 24 * ncp * sizeof(float4);
   AMG_CUDA_TRY(cudaFuncSetAttribute(assemble_pair_kernel<2, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   assemble_pair_kernel<2, 4><<<dim3((unsigned)g.Vc, 5), T, sm, st>>>(R, U, clov, part, g, m0, ncp, sb);
+  AMG_LAUNCH_CHECK();
+  return AMG_OK;
+}
+
+// Gram-Schmidt of every aggregate in pairs of floats; AMG_ERR_UNSUPPORTED when an aggregate has
+// more than 1536 entries (the FP64 kernel then serves).
+amg_status amg_internal_gs_pair(const Geom& g, const double2* tv, double2* R, unsigned* err, cudaStream_t st) {
+  if (g.nagg > GS_PE * 512) return AMG_ERR_UNSUPPORTED;
+  int T = round_up_i((g.nagg + GS_PE - 1) / GS_PE, 32);
+  if (T < 64) T = 64;
+  gs_pair_kernel<<<(unsigned)(g.Vc * 2), T, 0, st>>>(tv, R, g, err);
   AMG_LAUNCH_CHECK();
   return AMG_OK;
 }

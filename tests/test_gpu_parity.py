@@ -254,13 +254,14 @@ def test_cgc_composition(amg, ragged32):
         assert H.rel(coarse.coarse_apply(c.Dc, xc[..., r], c.Lc), yc[..., r]) < 1.2e-5
 
 
-def test_rank_deficient_test_vectors_reported(amg):
+@pytest.mark.parametrize("arith", [0, 1], ids=["fp64", "f32pair"])
+def test_rank_deficient_test_vectors_reported(amg, arith):
     L, B, ntv = (4, 4, 4, 4), (2, 2, 2, 2), 4
     sites = si.all_sites(L)
     U = torch.from_numpy(si.links(5, 0.3, sites)).cuda()
     tvh = si.test_vectors(5, ntv, sites)
     tvh[..., 3] = tvh[..., 0] * (1 - 2j) + tvh[..., 1]
-    p = amg.make_params(L, B, ntv, 1, H.M0, H.CSW, amg.AMG_FP64, amg.AMG_FP64, amg.AMG_FP64)
+    p = amg.make_params(L, B, ntv, 1, H.M0, H.CSW, amg.AMG_FP64, amg.AMG_FP64, amg.AMG_FP64, setup_arith=arith)
     h, st = amg.amg_setup_coarse(p, U, torch.from_numpy(tvh).cuda(), torch.cuda.current_stream(),
                                  allow_rank_deficient=True)
     assert st == amg.AMG_ERR_RANK_DEFICIENT

@@ -1,9 +1,10 @@
-"""GPU parity of the D_c assembly in pairs of FP32 numbers (setup_arith = AMG_SETUP_F32PAIR).
+"""GPU parity of the setup in pairs of FP32 numbers (setup_arith = AMG_SETUP_F32PAIR: the
+Gram-Schmidt and the D_c assembly).
 
 Every case runs the setup twice on the same inputs, once per arithmetic, and checks the pair
-result against the FP64 oracle (1e-12 relative L2 per stencil direction, the FP64 setup's bar)
-and against the library's own FP64 assembly (1e-13: the two differ by the pairs' 47-bit
-rounding, about 1e-15).  The cases cover both tilings (2x2 tiles up to nc = 44, 2x4 beyond),
+results (R and D_c) against the FP64 oracle (1e-12 relative L2, per stencil direction for D_c:
+the FP64 setup's bar) and against the library's own FP64 setup (1e-13: the two differ by the
+pairs' 47-bit rounding).  The cases cover both tilings (2x2 tiles up to nc = 44, 2x4 beyond),
 the widest of each, padded tile columns, an odd Ntv (tiles across the chirality boundary, which
 the self job's quadrant skip must not drop), a block extent of 1 (every link of that direction
 leaves the block) and blocks whose +mu face does not start on a chunk of 8 sites.
@@ -69,6 +70,14 @@ def test_pair_assembly_matches_oracle_and_fp64(amg, L, B, ntv, eps, seed):
     h64 = _setup(amg, L, B, ntv, U, tv, amg.AMG_SETUP_FP64)
     hp = _setup(amg, L, B, ntv, U, tv, amg.AMG_SETUP_F32PAIR)
     try:
+        nagg = 6 * int(np.prod(B))
+        R64 = torch.empty((Vc, 2, ntv, nagg), dtype=torch.complex128, device="cuda")
+        Rp = torch.empty_like(R64)
+        amg.amg_export_R(h64, R64)
+        amg.amg_export_R(hp, Rp)
+        torch.cuda.synchronize()
+        assert H.rel(Rp.cpu().numpy(), H.q_to_lib_R(Q)) < 1e-12
+        assert H.rel(Rp.cpu().numpy(), R64.cpu().numpy()) < 1e-13
         D64 = _export_dc(amg, h64, Vc, nc)
         Dp = _export_dc(amg, hp, Vc, nc)
         got = Dp.cpu().numpy()
@@ -113,7 +122,7 @@ def test_pair_assembly_full_size_32x4(amg):
             i = int(lat.coarse_index(np.array(X), Lc))
             _, Dref, _, _ = H.patch_reference(seed, eps, L, B, ntv, X)
             assert H.rel(Dp[i].cpu().numpy(), Dref) < 1e-12, X
-        assert tp[2] < t64[2], (tp, t64)
+        assert tp[1] < t64[1] and tp[2] < t64[2], (tp, t64)
     finally:
         amg.amg_destroy(h64)
         amg.amg_destroy(hp)
