@@ -66,12 +66,14 @@ typedef enum {
     AMG_BF16 = 3
 } amg_prec;
 
-/* Arithmetic of the D_c = R D P assembly in amg_setup_coarse (clover and Gram-Schmidt stay FP64). */
+/* Arithmetic of the Gram-Schmidt and of the D_c = R D P assembly in amg_setup_coarse (the
+ * clover field stays FP64). */
 typedef enum {
     AMG_SETUP_FP64 = 0,     /* doubles on the FP64 pipe                                      */
     AMG_SETUP_F32PAIR = 1   /* each number an unevaluated sum of two floats (~47 bits), sums by
                                TwoSum and products by the FMA residual, on the FP32 pipes;
-                               results agree with FP64 to about 1e-14 relative              */
+                               R and D_c agree with FP64 to about 1e-14 relative; aggregates
+                               of more than 1536 entries fall back to the FP64 Gram-Schmidt */
 } amg_setup_arith;
 
 typedef struct {
