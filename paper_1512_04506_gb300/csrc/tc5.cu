@@ -18,7 +18,8 @@
 //
 // Operands.  The streamed D_c is A and lives in tensor memory (two FP16 per column): with N = 32 an
 // A operand in shared memory would be fetched again for every instruction.  A warps (lane
-// quadrants 0, 1) copy row q of a bulk-copied block to lane q with tcgen05.st; B warps write the neighbour's columns, split, as the B operand in shared memory
+// quadrants 0, 1) copy row q of a bulk-copied block to lane q with tcgen05.st; builder warps write the
+// neighbour's columns, split, as the B operand in shared memory
 // (K-major, no swizzle: core matrices of 8 rows x 16 bytes, adjacent in K 128 bytes apart, in N
 // 16 nc bytes apart).  One thread issues the MMAs; tcgen05.commit tells the builders when an A
 // stage and its B buffer may be reused and the epilogue when a block's product is complete.  Each
@@ -33,8 +34,8 @@
 //
 // Roles (704 threads): warps 0-15 write the operands in two groups of eight (w / 8) that take
 // alternate blocks, so that two blocks are prepared at once; in a group, warps with w % 4 < 2 copy
-// the A_hi rows of their lane quadrant and plane, the others write B and (FP32 storage) copy the
-// A_lo rows; warps 16-19 (quadrants 0-3) read, scale and sum the block products, the A_lo rows'
+// the A_hi rows of their lane quadrant and plane, the others (FP32 storage) the A_lo rows; B is
+// written by all eight (FP32 storage) or by the four non-A warps (FP16); warps 16-19 (quadrants 0-3) read, scale and sum the block products, the A_lo rows'
 // sums handed to the A_hi rows' warps through shared memory once per site, and store y; warp 20
 // lane 0 issues the bulk copies; warp 21 allocates tensor memory and lane 0 issues the MMAs.  Every wait is bounded; a wait that runs out raises the CTA's abort flag and sets the
 // timeout bit of the error word, after which every role leaves its loop, the MMA thread waits
@@ -166,7 +167,7 @@ struct T5Args {
 // Tensor-memory plan: A stages of nc columns (FP32 storage: A_hi in lanes 0 .. nc - 1 and A_lo in
 // lanes 64 .. 64 + nc - 1 of the same columns, so that one M = 128 instruction covers both) and
 // 64-column accumulators within 512 columns (accumulators first, A stages from column 64 NACC).
-__host__ __device__ constexpr int t5_nst(int nc) { return 4; }
+__host__ __device__ constexpr int t5_nst(int nc) { return 4; }  // five (where they fit) measured slower
 __host__ __device__ constexpr int t5_nacc(int nc) { return (512 - 4 * nc) / 64 >= 4 ? 4 : 3; }
 
 // Bytes of one B buffer (hi or lo): 32 / 8 column groups x (2 nc / 8) core matrices x 128 bytes.
@@ -374,7 +375,8 @@ __global__ void __launch_bounds__(kT5Threads, 1) apply_tc5_kernel(const T5Args a
   } else {
     // ---------------------------------------------------------------- builders
     // Two groups (w / 8) take alternate blocks.  In a group, A warps (w % 4 < 2): row q = lane of
-    // quadrant w % 4, plane (w / 4) % 2; B warps (w % 4 >= 2): threads 0 .. 127 of the B operand.
+    // quadrant w % 4, plane (w / 4) % 2; the others (FP32 storage) the A_lo rows of the same plane.
+    // B: FP32 storage all eight warps, FP16 storage the four non-A warps.
     const int grp = warp >> 3;
     const bool awarp = (warp & 3) < 2;    // A_hi rows (quadrants 0, 1); the others write B and, for FP32
                                           // storage, the A_lo rows (quadrants 2, 3: lanes 64 + q)
@@ -385,7 +387,10 @@ __global__ void __launch_bounds__(kT5Threads, 1) apply_tc5_kernel(const T5Args a
     const uint32_t lane_off = (uint32_t)(32 * (warp & 3)) << 16;
     const int rot = row_ok ? tc_rot(q, P) : 0;
     const size_t lo_off = awarp ? 0 : (size_t)2 * NC * NC * 2;  // the lo planes follow the hi planes
-    const int bt = (((warp >> 2) & 1) * 2 + (warp & 3) - 2) * 32 + lane;  // B warps: 0 .. 127
+    // B threads: FP32 storage all eight warps of the group (0 .. 255: the A_lo warps would otherwise
+    // carry B on top of their rows), FP16 storage the four non-A warps (0 .. 127)
+    constexpr int BT = F32 ? 256 : 128;
+    const int bt = F32 ? (warp & 7) * 32 + lane : (((warp >> 2) & 1) * 2 + (warp & 3) - 2) * 32 + lane;
     bool ok = true;
     long long blk = 0;
     float nd, nx;
@@ -429,7 +434,7 @@ __global__ void __launch_bounds__(kT5Threads, 1) apply_tc5_kernel(const T5Args a
           }
           tc5_wait_st();
         }
-        if (!awarp) {
+        if (F32 || !awarp) {
           // B (K x 32): column n < 16 = real part of right-hand side n, 16 + n its imaginary part;
           // B = [[x_re, x_im], [-x_im, x_re]]' of the neighbour, split into FP16 hi + lo.  A thread
           // takes rows kk, kk + 1 (kk even) of one right-hand side m: two (re, im) loads, packed
@@ -438,7 +443,7 @@ __global__ void __launch_bounds__(kT5Threads, 1) apply_tc5_kernel(const T5Args a
           unsigned char* bhi = bbuf + (size_t)(2 * st) * bbytes;
           unsigned char* blo = bhi + bbytes;
           const float inv = inv_blk;
-          for (int e = bt; e < NC * 8; e += 128) {
+          for (int e = bt; e < NC * 8; e += BT) {
             const int kk = 2 * (e >> 4), m = e & 15;
             float2 x0 = make_float2(0.f, 0.f), x1 = make_float2(0.f, 0.f);
             if (m < nrhs) {
