@@ -109,12 +109,48 @@ __device__ __forceinline__ void hop_u(const C u[9], const C p[12], C out[12]) {
   }
 }
 
+// The 3x3 link at U9 = U + (s 4 + mu) 9.  FP32: 72 bytes from an offset 16-byte aligned for even mu
+// and 8 bytes past that for odd mu (s 4 + mu has the parity of mu), so four 16-byte loads and one
+// 8-byte load.
+template <int mu>
+__device__ __forceinline__ void load_link(const double2* __restrict__ U9, double2 u[9]) {
+#pragma unroll
+  for (int k = 0; k < 9; ++k) u[k] = __ldg(U9 + k);
+}
+template <int mu>
+__device__ __forceinline__ void load_link(const float2* __restrict__ U9, float2 u[9]) {
+  constexpr int o = mu & 1;  // entries before the first 16-byte boundary
+  if (o) u[0] = __ldg(U9);
+  const float4* q = reinterpret_cast<const float4*>(U9 + o);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float4 f = __ldg(q + k);
+    u[o + 2 * k] = make_float2(f.x, f.y);
+    u[o + 2 * k + 1] = make_float2(f.z, f.w);
+  }
+  if (!o) u[8] = __ldg(U9 + 8);
+}
+
 template <bool FWD, int mu, typename C>
 __device__ __forceinline__ void hop(const C* __restrict__ U, const C p[12], C out[12]) {
   C u[9];
-#pragma unroll
-  for (int k = 0; k < 9; ++k) u[k] = U[k];
+  load_link<mu>(U, u);
   hop_u<FWD, mu>(u, p, out);
+}
+
+// Row of six clover entries (FP32: three 16-byte loads)
+__device__ __forceinline__ void clover_row(const double2* __restrict__ row, double2 c[6]) {
+#pragma unroll
+  for (int b = 0; b < 6; ++b) c[b] = __ldg(row + b);
+}
+__device__ __forceinline__ void clover_row(const float2* __restrict__ row, float2 c[6]) {
+  const float4* r4 = reinterpret_cast<const float4*>(row);
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    const float4 f = __ldg(r4 + b);
+    c[2 * b] = make_float2(f.x, f.y);
+    c[2 * b + 1] = make_float2(f.z, f.w);
+  }
 }
 
 // out = (4 + m0) p + C(x) p for the site whose clover blocks start at Cl ([2][6][6])
@@ -124,9 +160,10 @@ __device__ __forceinline__ void site_term(const C* __restrict__ Cl, T mass, cons
   for (int hh = 0; hh < 2; ++hh) {
 #pragma unroll
     for (int a = 0; a < 6; ++a) {
-      C acc = zscale(p[hh * 6 + a], mass);
+      C acc = zscale(p[hh * 6 + a], mass), c[6];
+      clover_row(Cl + (hh * 6 + a) * 6, c);
 #pragma unroll
-      for (int b = 0; b < 6; ++b) zfma(acc, Cl[(hh * 6 + a) * 6 + b], p[hh * 6 + b]);
+      for (int b = 0; b < 6; ++b) zfma(acc, c[b], p[hh * 6 + b]);
       out[hh * 6 + a] = acc;
     }
   }
@@ -233,9 +270,10 @@ __global__ void __launch_bounds__(128) dirac_kernel(const typename Cx<T>::type* 
 }
 
 // MR coefficient alpha = <p, rho> / <p, p> from per-thread partial sums v = (<p,p>, Re, Im <p,rho>):
-// warp sums in the values' precision, the CTA sum and the division in FP64 by one thread (FP64 is
-// slow on this GPU: every thread doing them had kept the FP64 pipe busy), alpha broadcast through
-// shared memory.  ok = false when <p, p> = 0.  red: 3 doubles per warp + 3 doubles.
+// warp sums, then the CTA sum and the division by one thread, all in the vector precision (FP64
+// is slow on this GPU: every thread summing and dividing in FP64 had kept the FP64 pipe busy, and
+// one thread's FP64 division held the whole CTA at the barrier), alpha broadcast through shared
+// memory.  ok = false when <p, p> = 0.  red: 3 doubles per warp + 3 doubles.
 template <typename T, typename C>
 __device__ __forceinline__ void cta_alpha(T v[3], double* red, C& al, bool& ok) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
@@ -249,14 +287,14 @@ __device__ __forceinline__ void cta_alpha(T v[3], double* red, C& al, bool& ok) 
   __syncthreads();
   double* out = red + 3 * nw;
   if (threadIdx.x == 0) {
-    double sp = 0, sr = 0, si = 0;
+    T sp = 0, sr = 0, si = 0;
     for (int w = 0; w < nw; ++w) {
-      sp += red[w * 3];
-      sr += red[w * 3 + 1];
-      si += red[w * 3 + 2];
+      sp += (T)red[w * 3];
+      sr += (T)red[w * 3 + 1];
+      si += (T)red[w * 3 + 2];
     }
-    out[0] = sp > 0 ? sr / sp : 0.0;
-    out[1] = sp > 0 ? si / sp : 0.0;
+    out[0] = sp > 0 ? (double)(sr / sp) : 0.0;
+    out[1] = sp > 0 ? (double)(si / sp) : 0.0;
     red[3 * nw + 2] = sp > 0 ? 1.0 : 0.0;
   }
   __syncthreads();
@@ -428,6 +466,29 @@ __device__ __forceinline__ void block_hops_smem(const float2* Us, const float2* 
   }
 }
 
+// Both hops of direction mu of the full D at site s (neighbour spinors from global memory), links
+// from the staged block where they lie in it: the forward link always, the backward one unless the
+// neighbour is outside the block.
+template <int mu>
+__device__ __forceinline__ void residual_hops(const FineGeom& g, const float2* __restrict__ U, const float2* Us,
+                                              const float2* __restrict__ v, long long s, const int x[4], const int lc[4],
+                                              int Vb, int t, int stride, int nrhs, int r, float2 o[12]) {
+  float2 p[12], u[9];
+  load12(v, nbr_site<mu, 1>(g, s, x), nrhs, r, p);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) u[k] = Us[(mu * 9 + k) * Vb + t];
+  hop_u<true, mu>(u, p, o);
+  const long long sb = nbr_site<mu, -1>(g, s, x);
+  load12(v, sb, nrhs, r, p);
+  if (lc[mu] > 0) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) u[k] = Us[(mu * 9 + k) * Vb + t - stride];
+  } else {
+    load_link<mu>(U + (sb * 4 + mu) * 9, u);
+  }
+  hop_u<false, mu>(u, p, o);
+}
+
 __global__ void __launch_bounds__(256, 1) sap_smem_kernel(const float2* __restrict__ U, const float2* __restrict__ Cl,
                                                           const float2* __restrict__ y, float2* __restrict__ x,
                                                           FineGeom g, float mass, int nrhs, int colour, int n_mr) {
@@ -472,17 +533,30 @@ __global__ void __launch_bounds__(256, 1) sap_smem_kernel(const float2* __restri
       Us[(2 * q) * Vb + t] = make_float2(f.x, f.y);
       Us[(2 * q + 1) * Vb + t] = make_float2(f.z, f.w);
     }
+    // clover rows as 16-byte pairs (entries b, b + 1); the upper triangle kept
+    const float4* C4 = reinterpret_cast<const float4*>(Cl + s * 72);
 #pragma unroll
     for (int hh = 0; hh < 2; ++hh)
 #pragma unroll
       for (int a = 0; a < 6; ++a)
 #pragma unroll
-        for (int b = a; b < 6; ++b) Cs[(hh * 21 + tri_index(a, b)) * Vb + t] = __ldg(Cl + s * 72 + (hh * 6 + a) * 6 + b);
-    // residual r = y - D x on this site (full D: neighbours outside the block have the other colour)
+        for (int b2 = a / 2; b2 < 3; ++b2) {
+          const float4 f = __ldg(C4 + (hh * 6 + a) * 3 + b2);
+          if (2 * b2 >= a) Cs[(hh * 21 + tri_index(a, 2 * b2)) * Vb + t] = make_float2(f.x, f.y);
+          Cs[(hh * 21 + tri_index(a, 2 * b2 + 1)) * Vb + t] = make_float2(f.z, f.w);
+        }
+  }
+  __syncthreads();  // links and clover staged
+  if (act) {
+    // residual r = y - D x on this site (full D: neighbours outside the block have the other colour);
+    // the clover, the forward links and the backward links inside the block from shared memory
     float2 p[12];
     load12(x, s, nrhs, r, p);
-    site_term(Cl + s * 72, mass, p, o);
-    all_hops(g, U, x, s, xs, nrhs, r, o);
+    site_term_packed(Cs, Vb, t, mass, p, o);
+    residual_hops<0>(g, U, Us, x, s, xs, lc, Vb, t, 1, nrhs, r, o);
+    residual_hops<1>(g, U, Us, x, s, xs, lc, Vb, t, st1, nrhs, r, o);
+    residual_hops<2>(g, U, Us, x, s, xs, lc, Vb, t, st2, nrhs, r, o);
+    residual_hops<3>(g, U, Us, x, s, xs, lc, Vb, t, st3, nrhs, r, o);
     load12(y, s, nrhs, r, p);
 #pragma unroll
     for (int q = 0; q < 12; ++q) {
