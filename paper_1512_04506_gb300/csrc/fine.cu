@@ -611,23 +611,40 @@ __global__ void __launch_bounds__(256, 1) sap_smem_kernel(const float2* __restri
 // ------------------------------------------------------------------ outer FGMRES vector kernels
 constexpr int FT = 256;
 
-// part[i][r] += sum_n conj(V_i[n, r]) w[n, r] for i < nv (FP64 sums; one atomic per CTA and pair)
+// Arithmetic of the outer FGMRES vector kernels: per element in the vectors' precision (FP64 is
+// slow on this GPU; an FP32 vector gains nothing from FP64 products), per-thread partial sums in
+// that precision (a few dozen elements each), sums across threads and CTAs in FP64.  The per-column
+// coefficients are converted to the vectors' precision once per CTA, in shared memory.
+template <typename C> struct Real;
+template <> struct Real<float2> { using type = float; };
+template <> struct Real<double2> { using type = double; };
+
+template <typename C>
+__device__ __forceinline__ C to_c(double2 v) {
+  C o;
+  o.x = (typename Real<C>::type)v.x;
+  o.y = (typename Real<C>::type)v.y;
+  return o;
+}
+
+// part[i][r] += sum_n conj(V_i[n, r]) w[n, r] for i < nv (one FP64 atomic per CTA and pair)
 template <typename C>
 __global__ void __launch_bounds__(FT) fdots_kernel(const C* __restrict__ Vb, long long vstride, int nv,
                                                    const C* __restrict__ w, long long n, int nrhs, double2* out) {
+  using R = typename Real<C>::type;
   __shared__ double2 red[FT];
   const int i = blockIdx.y;
   const C* v = Vb + vstride * i;
   const int per = FT / nrhs * nrhs;  // threads per CTA that take part (a multiple of nrhs)
-  double2 acc = make_double2(0, 0);
+  R ax = 0, ay = 0;
   if (threadIdx.x < per) {
     for (long long e = blockIdx.x * (long long)per + threadIdx.x; e < n * nrhs; e += (long long)gridDim.x * per) {
       const C a = v[e], b = w[e];
-      acc.x += (double)a.x * b.x + (double)a.y * b.y;
-      acc.y += (double)a.x * b.y - (double)a.y * b.x;
+      ax = fma(a.x, b.x, fma(a.y, b.y, ax));
+      ay = fma(a.x, b.y, fma(-a.y, b.x, ay));
     }
   }
-  red[threadIdx.x] = acc;
+  red[threadIdx.x] = make_double2((double)ax, (double)ay);
   __syncthreads();
   if (threadIdx.x < nrhs) {
     double2 s = make_double2(0, 0);
@@ -640,32 +657,42 @@ __global__ void __launch_bounds__(FT) fdots_kernel(const C* __restrict__ Vb, lon
   }
 }
 
+constexpr int kFMaxCoef = 1024;  // coefficients cached per CTA (nv x nrhs); more are read from global memory
+
+template <typename C>
+__device__ __forceinline__ C coef_at(const C* cached, const double2* __restrict__ g, bool use_cache, int k) {
+  return use_cache ? cached[k] : to_c<C>(g[k]);
+}
+
 // w -= sum_{i < nv} h[i][r] V_i ; nrm2[r] += |w|^2 (after the update)
 template <typename C>
 __global__ void __launch_bounds__(FT) fupdate_kernel(const C* __restrict__ Vb, long long vstride, int nv,
                                                      const double2* __restrict__ h, C* __restrict__ w, long long n,
                                                      int nrhs, double* nrm2) {
+  using R = typename Real<C>::type;
   __shared__ double red[FT];
+  __shared__ C hc[kFMaxCoef];
+  const bool cached = nv * nrhs <= kFMaxCoef;
+  if (cached)
+    for (int k = threadIdx.x; k < nv * nrhs; k += blockDim.x) hc[k] = to_c<C>(h[k]);
+  __syncthreads();
   const int per = FT / nrhs * nrhs;
-  double acc = 0;
+  R acc = 0;
   if (threadIdx.x < per) {
     for (long long e = blockIdx.x * (long long)per + threadIdx.x; e < n * nrhs; e += (long long)gridDim.x * per) {
       const int r = (int)(e % nrhs);
-      double2 a = make_double2((double)w[e].x, (double)w[e].y);
+      C a = w[e];
       for (int i = 0; i < nv; ++i) {
         const C v = Vb[vstride * i + e];
-        const double2 c = h[i * nrhs + r];
+        const C c = coef_at(hc, h, cached, i * nrhs + r);
         a.x -= c.x * v.x - c.y * v.y;
         a.y -= c.x * v.y + c.y * v.x;
       }
-      C o;
-      o.x = a.x;
-      o.y = a.y;
-      w[e] = o;
-      acc += (double)o.x * o.x + (double)o.y * o.y;
+      w[e] = a;
+      acc = fma(a.x, a.x, fma(a.y, a.y, acc));
     }
   }
-  red[threadIdx.x] = acc;
+  red[threadIdx.x] = (double)acc;
   __syncthreads();
   if (threadIdx.x < nrhs) {
     double s = 0;
@@ -677,9 +704,12 @@ __global__ void __launch_bounds__(FT) fupdate_kernel(const C* __restrict__ Vb, l
 // y = a[r] * x (a per column, complex); y may be x
 template <typename C>
 __global__ void fscale_kernel(const C* x, C* y, const double2* __restrict__ a, long long n, int nrhs) {
+  __shared__ C ac[64];  // nrhs <= 64
+  if (threadIdx.x < nrhs) ac[threadIdx.x] = to_c<C>(a[threadIdx.x]);
+  __syncthreads();
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n * nrhs;
        e += (long long)gridDim.x * blockDim.x) {
-    const double2 c = a[e % nrhs];
+    const C c = ac[e % nrhs];
     const C v = x[e];
     C o;
     o.x = c.x * v.x - c.y * v.y;
@@ -692,33 +722,36 @@ __global__ void fscale_kernel(const C* x, C* y, const double2* __restrict__ a, l
 template <typename C>
 __global__ void fcombine_kernel(const C* __restrict__ Xb, long long vstride, int nv, const double2* __restrict__ c,
                                 C* __restrict__ y, long long n, int nrhs) {
+  __shared__ C cc[kFMaxCoef];
+  const bool cached = nv * nrhs <= kFMaxCoef;
+  if (cached)
+    for (int k = threadIdx.x; k < nv * nrhs; k += blockDim.x) cc[k] = to_c<C>(c[k]);
+  __syncthreads();
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n * nrhs;
        e += (long long)gridDim.x * blockDim.x) {
     const int r = (int)(e % nrhs);
-    double2 a = make_double2((double)y[e].x, (double)y[e].y);
+    C a = y[e];
     for (int i = 0; i < nv; ++i) {
       const C v = Xb[vstride * i + e];
-      const double2 k = c[i * nrhs + r];
+      const C k = coef_at(cc, c, cached, i * nrhs + r);
       a.x += k.x * v.x - k.y * v.y;
       a.y += k.x * v.y + k.y * v.x;
     }
-    C o;
-    o.x = a.x;
-    o.y = a.y;
-    y[e] = o;
+    y[e] = a;
   }
 }
 
 // nrm2[r] += |v|^2
 template <typename C>
 __global__ void __launch_bounds__(FT) fnorm_kernel(const C* __restrict__ v, long long n, int nrhs, double* nrm2) {
+  using R = typename Real<C>::type;
   __shared__ double red[FT];
   const int per = FT / nrhs * nrhs;
-  double acc = 0;
+  R acc = 0;
   if (threadIdx.x < per)
     for (long long e = blockIdx.x * (long long)per + threadIdx.x; e < n * nrhs; e += (long long)gridDim.x * per)
-      acc += (double)v[e].x * v[e].x + (double)v[e].y * v[e].y;
-  red[threadIdx.x] = acc;
+      acc = fma(v[e].x, v[e].x, fma(v[e].y, v[e].y, acc));
+  red[threadIdx.x] = (double)acc;
   __syncthreads();
   if (threadIdx.x < nrhs) {
     double s = 0;
@@ -750,7 +783,6 @@ __global__ void to_prec_kernel(const double2* __restrict__ in, typename Cx<T>::t
 }
 
 bool fine_fp64(const amg_coarse* h) { return h->p.vec_prec == AMG_FP64; }
-size_t fine_elem(const amg_coarse* h) { return fine_fp64(h) ? sizeof(double2) : sizeof(float2); }
 
 template <typename T>
 amg_status launch_dirac(amg_coarse* h, const void* psi, const void* y, void* out, int nrhs, cudaStream_t st) {
