@@ -156,7 +156,7 @@ struct T5Args {
                       // (16-byte pieces of 8 rotated by tc_rot(r, nc / 8)): FP32 storage split at setup
                       // into hi + lo, FP16 storage as stored
   const float* ds;    // [Vc][9] scale of each stencil block (FP32: power of two; FP16: the stored scale)
-  const float* X;     // [Vc][nc][tf32_xpitch(nrhs)] FP32 coarse rows (already times xscale)
+  const float* X;     // [Vc][nc][2 nrhs] FP32 coarse rows (already times xscale)
   const float* xs;    // [Vc] power-of-two scale of each site's rows
   const int* nbr;
   float2* y;          // [Vc][nc][nrhs] FP32
@@ -173,7 +173,10 @@ __host__ __device__ constexpr int t5_nacc(int nc) { return (512 - 4 * nc) / 64 >
 // Bytes of one B buffer (hi or lo): 32 / 8 column groups x (2 nc / 8) core matrices x 128 bytes.
 __host__ __device__ inline unsigned t5_bbytes(int nc) { return 4u * (unsigned)(2 * nc / 8) * 128u; }
 __host__ __device__ inline unsigned t5_dbytes(int nc, bool f32) { return (unsigned)((f32 ? 8 : 4) * nc * nc); }
-__host__ __device__ inline unsigned t5_xbytes(int nc, int nrhs) { return (unsigned)(nc * tf32_xpitch(nrhs) * 4); }
+// Coarse rows of the bulk copies: 2 nrhs floats, unpadded (the B writers read them as 8-byte words, 16
+// consecutive per half warp, which no pitch makes conflict; padding only added bytes to the copy stream)
+__host__ __device__ inline int t5_xpitch(int nrhs) { return 2 * nrhs; }
+__host__ __device__ inline unsigned t5_xbytes(int nc, int nrhs) { return (unsigned)(nc * t5_xpitch(nrhs) * 4); }
 
 // The scales of site i's nine blocks, lane d (< 9) holding block d: s_D and s_x of its neighbour.
 // Each role loads the next site's while it works on the current one (the loads are dependent:
@@ -201,7 +204,7 @@ __global__ void __launch_bounds__(kT5Threads, 1) apply_tc5_kernel(const T5Args a
   constexpr uint32_t kAcc = 0, kA = 64u * NACC;
   constexpr int EPI = F32 ? 4 : 2;       // epilogue warps (lane quadrants 0 .. EPI - 1)
   static_assert(kA + NST * AW <= 512, "tensor-memory columns");
-  const int XP = 2 * nrhs + (nrhs % 8 == 0 ? 8 : 0);      // tf32_xpitch(nrhs)
+  const int XP = t5_xpitch(nrhs);
   const unsigned xbytes = (unsigned)(NC * XP * 4);
   extern __shared__ __align__(128) unsigned char sm[];
   Pipe* pp = reinterpret_cast<Pipe*>(sm);
@@ -482,12 +485,12 @@ __global__ void __launch_bounds__(kT5Threads, 1) apply_tc5_kernel(const T5Args a
 }
 
 // FP32 coarse vector x (times xscale[r]; the scaled vector also to vout) -> FP32 rows of
-// tf32_xpitch(nrhs) floats and the power-of-two scale of each site: one warp per site.
+// t5_xpitch(nrhs) floats and the power-of-two scale of each site: one warp per site.
 __global__ void xc_rows_pow2_kernel(const float2* __restrict__ x, float* __restrict__ X, float* __restrict__ xs,
                                     long long Vc, int nc, int nrhs, const double* __restrict__ xscale,
                                     float2* __restrict__ vout, const int* __restrict__ skip) {
   if (skip && *skip) return;
-  const int XP = 2 * nrhs + (nrhs % 8 == 0 ? 8 : 0);
+  const int XP = t5_xpitch(nrhs);
   const int lane = threadIdx.x & 31;
   const long long w0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -588,7 +591,7 @@ amg_status amg_internal_tc5_prepare(amg_coarse* h, cudaStream_t st) {
   const Geom& g = h->g;
   const int nmax = h->p.max_nrhs < 16 ? h->p.max_nrhs : 16;
   h->tc5_xbytes = 0;
-  for (int n = 1; n <= nmax; ++n)  // the row pitch is not monotone in nrhs: take the largest
+  for (int n = 1; n <= nmax; ++n)  // rows sized for the largest column count
     if ((size_t)g.Vc * t5_xbytes(g.nc, n) > h->tc5_xbytes) h->tc5_xbytes = (size_t)g.Vc * t5_xbytes(g.nc, n);
   AMG_CUDA_TRY(cudaMalloc(&h->tc5_x, h->tc5_xbytes));
   AMG_CUDA_TRY(cudaMalloc(&h->tc5_xs, (size_t)g.Vc * sizeof(float)));
