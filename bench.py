@@ -50,9 +50,8 @@ TC16_KERNELS = {"restrict": "restrict_tc_kernel<16> (Y_c = R Y, BF16 R, 16 RHS)"
 # profiles/apply_mrhs_fp16_32x3x64_ntv24.md)
 TRAFFIC_FP16_APPLY = 692893440
 # DRAM bytes of one FP32 16-column tcgen05 apply at 32^3 x 64, Ntv = 24: the 16^3 x 32 capture
-# (profiles/apply_tc5_fp32_16x3x32_ntv24_nrhs16.md) x 16 sites; None until the current kernel's
-# counters are taken
-TRAFFIC_MRHS_FP32 = None
+# (profiles/apply_tc5_fp32_16x3x32_ntv24_nrhs16.md, 90,586.9 KB for 512 sites) x 16 sites
+TRAFFIC_MRHS_FP32 = 1449390080
 # DRAM traffic / algorithmic bytes of the fused batch launch, from the reduced-volume capture
 # (profiles/batch_kernel_small_mixed.md); the full launch's traffic is taken in that proportion
 BATCH_TRAFFIC_RATIO = 0.990
