@@ -39,10 +39,10 @@ APPLIES_PER_STEP = 2
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the 32^4 workload, from
 # the ncu captures of the 24^4 case summarised under profiles/ scaled by the number of blocks /
 # coarse sites (the per-unit work is the same); valid for the kernels as captured.
-TRAFFIC = {"restrict": 2124549284, "prolong": 2124409312, "apply": 483073946}
+TRAFFIC = {"restrict": 2124549284, "prolong": 2124409312, "apply": 483471208}
 # the same for the 48^3 x 96 tensor-core workload (captures of the 24^3 x 48 case, x16; the apply
 # figure is the tensor-core kernel alone, without the FP32 -> BF16 conversion launch)
-TRAFFIC_TC16 = {"restrict": 20641533184, "prolong": 19744555008, "apply": 3677028352}
+TRAFFIC_TC16 = {"restrict": 20641533184, "prolong": 19751972864, "apply": 3679113216}
 TC16_KERNELS = {"restrict": "restrict_tc_kernel<16> (Y_c = R Y, BF16 R, 16 RHS)",
                 "apply": "xc_to_bf16_kernel<16> + apply_tc_kernel<16> (D_c X_c, BF16 D_c, 16 RHS)",
                 "prolong": "prolong_tc_kernel<16> (X = P X_c, BF16 R, 16 RHS)"}

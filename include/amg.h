@@ -51,7 +51,7 @@ extern "C" {
 typedef enum {
     AMG_OK = 0,
     AMG_ERR_INVALID_ARG = 1,     /* a size, pointer or precision was rejected           */
-    AMG_ERR_UNSUPPORTED = 2,     /* valid request that this build does not implement     */
+    AMG_ERR_UNSUPPORTED = 2,     /* valid request that the library does not implement    */
     AMG_ERR_OOM = 3,             /* device allocation failed                             */
     AMG_ERR_CUDA = 4,            /* a CUDA runtime call or launch failed                 */
     AMG_ERR_TIMEOUT = 5,         /* a bounded device-side wait ran out                   */
