@@ -55,9 +55,9 @@ TRAFFIC_MRHS_FP32 = 1449390080
 # DRAM traffic / algorithmic bytes of the fused batch launch, from the reduced-volume capture
 # (profiles/batch_kernel_small_mixed.md); the full launch's traffic is taken in that proportion
 BATCH_TRAFFIC_RATIO = 0.990
-# DRAM traffic / algorithmic bytes of one SAP half sweep, from the 16^4 capture
-# (profiles/sap_16x4.md: 42.94 MB for 65,536 sites x 624 B); the 32^4 launch is taken in proportion
-SAP_TRAFFIC_RATIO = 1.050
+# DRAM traffic / algorithmic bytes of one SAP half sweep, from the 16^4 capture (profiles/sap_16x4.md:
+# 35.57 MB for 65,536 sites x 504 B); the 32^4 launch is taken in proportion
+SAP_TRAFFIC_RATIO = 1.077
 METRIC = "coarse-grid correction GB/s & % HBM roofline; batched-mixed vs plain speedup"
 WORKLOAD = "fp32_32^4_b4_ntv20: 32^4 Wilson-clover, 4^4 blocks -> 8^4 coarse, Ntv=20, 1 RHS, " \
            "FP64 setup, FP32 R and D_c; step = R y, FGMRES(30) to 0.05 (<=200 applies), P x_c"
@@ -688,9 +688,10 @@ def run_vcycle(args):
     and the outer FGMRES(30) preconditioned with the V-cycle to relative residual 1e-5 (Sec. 1).
 
     Algorithmic bytes (FP32 complex = 8 B) per fine site: D reads 4 links (288 B), the clover
-    (576 B), psi (96 B) and writes out (96 B) = 1056 B; one SAP half sweep reads, per site of its
-    colour, the links, the clover, y and x and writes x (1152 B), and reads x on the other colour's
-    sites once (96 B): 624 B per fine site of the lattice."""
+    (two Hermitian 6x6 blocks as upper triangles, 336 B), psi (96 B) and writes out (96 B) = 816 B;
+    one SAP half sweep reads, per site of its colour, the links, the clover, y and x and writes x
+    (912 B), and reads x on the other colour's sites once (96 B): 504 B per fine site of the
+    lattice."""
     import torch
     import paper_1512_04506_gb300 as amg
     from synth import device as sd
@@ -722,8 +723,8 @@ def run_vcycle(args):
     amg.amg_destroy(h)
     if status != amg.AMG_OK:
         raise RuntimeError(amg.amg_status_string(status))
-    d_bytes = V * 1056
-    half_bytes = V * 624
+    d_bytes = V * 816
+    half_bytes = V * 504
     cgc_bytes, _ = bytes_model(applies, arnoldi_iterations(applies))
     step_bytes = cgc_bytes + 2 * n_smoother * half_bytes
     peaks, src = measured_peaks()
@@ -740,7 +741,7 @@ def run_vcycle(args):
         "roofline": {"bound": "hbm", "kernel": "sap_smem_kernel (one half sweep: residual + %d MR steps per block, "
                      "links and clover in shared memory)" % n_mr, "achieved": round(sap_gbs, 1), "peak": peaks["hbm_gbs"],
                      "unit": "GB/s", "frac": round(sap_gbs / peaks["hbm_gbs"], 4), "peak_source": src,
-                     "traffic": round(SAP_TRAFFIC_RATIO * half_bytes) if not args.lattice else None,
+                     "traffic": round(SAP_TRAFFIC_RATIO * half_bytes) if SAP_TRAFFIC_RATIO and not args.lattice else None,
                      "traffic_note": "16^4 capture's traffic / algorithmic bytes x this launch's bytes",
                      "bytes_per_launch": half_bytes, "avg_launch_us": round(t_sap * 1e6, 2),
                      "step_share": round(2 * n_smoother * t_sap / (t / args.steps), 3)},

@@ -138,19 +138,10 @@ __device__ __forceinline__ void hop(const C* __restrict__ U, const C p[12], C ou
   hop_u<FWD, mu>(u, p, out);
 }
 
-// Row of six clover entries (FP32: three 16-byte loads)
+// Row of six clover entries (FP64 blocks)
 __device__ __forceinline__ void clover_row(const double2* __restrict__ row, double2 c[6]) {
 #pragma unroll
   for (int b = 0; b < 6; ++b) c[b] = __ldg(row + b);
-}
-__device__ __forceinline__ void clover_row(const float2* __restrict__ row, float2 c[6]) {
-  const float4* r4 = reinterpret_cast<const float4*>(row);
-#pragma unroll
-  for (int b = 0; b < 3; ++b) {
-    const float4 f = __ldg(r4 + b);
-    c[2 * b] = make_float2(f.x, f.y);
-    c[2 * b + 1] = make_float2(f.z, f.w);
-  }
 }
 
 // out = (4 + m0) p + C(x) p for the site whose clover blocks start at Cl ([2][6][6])
@@ -167,6 +158,43 @@ __device__ __forceinline__ void site_term(const C* __restrict__ Cl, T mass, cons
       out[hh * 6 + a] = acc;
     }
   }
+}
+
+__host__ __device__ __forceinline__ int tri_index(int a, int b) { return a * 6 - a * (a - 1) / 2 + (b - a); }  // a <= b
+
+// FP32 clover of one site in HBM as the two Hermitian blocks' upper triangles with the diagonal
+// (21 entries each in tri_index order, one padding entry after each: 44 complex, 352 bytes instead
+// of 576; C_ba = conj(C_ab)), read with 16-byte loads
+constexpr int kClPacked = 44;
+__device__ __forceinline__ void site_term_hp(const float2* __restrict__ Cl, float mass, const float2 p[12],
+                                             float2 out[12]) {
+#pragma unroll
+  for (int hh = 0; hh < 2; ++hh) {
+    float2 c[22];
+    const float4* q = reinterpret_cast<const float4*>(Cl + hh * 22);
+#pragma unroll
+    for (int k = 0; k < 11; ++k) {
+      const float4 f = __ldg(q + k);
+      c[2 * k] = make_float2(f.x, f.y);
+      c[2 * k + 1] = make_float2(f.z, f.w);
+    }
+#pragma unroll
+    for (int a = 0; a < 6; ++a) {
+      float2 acc = zscale(p[hh * 6 + a], mass);
+#pragma unroll
+      for (int b = 0; b < 6; ++b) {
+        if (a <= b) zfma(acc, c[tri_index(a, b)], p[hh * 6 + b]);
+        else zfmac(acc, c[tri_index(b, a)], p[hh * 6 + b]);
+      }
+      out[hh * 6 + a] = acc;
+    }
+  }
+}
+// the site term of site s: FP32 from the packed clover, FP64 from the full [2][6][6] blocks
+template <typename C, typename T>
+__device__ __forceinline__ void site_term_at(const C* __restrict__ Cl, long long s, T mass, const C p[12], C out[12]) {
+  if constexpr (sizeof(C) == 8) site_term_hp(Cl + s * kClPacked, mass, p, out);
+  else site_term(Cl + s * 72, mass, p, out);
 }
 
 struct FineGeom {
@@ -257,7 +285,7 @@ __global__ void __launch_bounds__(128) dirac_kernel(const typename Cx<T>::type* 
     site_coords(g, s, x);
     C p[12], o[12];
     load12(psi, s, nrhs, r, p);
-    site_term(Cl + s * 72, mass, p, o);
+    site_term_at(Cl, s, mass, p, o);
     all_hops(g, U, psi, s, x, nrhs, r, o);
     if (SUB) {
       load12(y, s, nrhs, r, p);
@@ -366,7 +394,7 @@ __global__ void __launch_bounds__(256) sap_kernel(const typename Cx<T>::type* __
   if (act) {
     C p[12];
     load12(x, s, nrhs, r, p);
-    site_term(Cl + s * 72, mass, p, o);
+    site_term_at(Cl, s, mass, p, o);
     all_hops(g, U, x, s, xs, nrhs, r, o);
     load12(y, s, nrhs, r, p);
 #pragma unroll
@@ -384,7 +412,7 @@ __global__ void __launch_bounds__(256) sap_kernel(const typename Cx<T>::type* __
     if (act) {
 #pragma unroll
       for (int q = 0; q < 12; ++q) rr[q] = rho[q * g.Vb + t];
-      site_term(Cl + s * 72, mass, rr, o);
+      site_term_at(Cl, s, mass, rr, o);
       block_hops_mu<0>(g, U, rho, t, s, xs, lc, 1, o);
       block_hops_mu<1>(g, U, rho, t, s, xs, lc, st1, o);
       block_hops_mu<2>(g, U, rho, t, s, xs, lc, st2, o);
@@ -424,8 +452,6 @@ __global__ void __launch_bounds__(256) sap_kernel(const typename Cx<T>::type* __
 // 25 KB of rho).  Layouts are component-major, [component][Vb], so that the threads of a warp (one
 // site each) read consecutive words: links [mu][9][Vb]; clover per chirality as its upper triangle
 // with the diagonal, [2][21][Vb] (the blocks are Hermitian, C_ba = conj(C_ab)); rho [12][Vb].
-__device__ __forceinline__ int tri_index(int a, int b) { return a * 6 - a * (a - 1) / 2 + (b - a); }  // a <= b
-
 __device__ __forceinline__ void site_term_packed(const float2* Cs, int Vb, int t, float mass, const float2 p[12],
                                                  float2 out[12]) {
 #pragma unroll
@@ -533,18 +559,16 @@ __global__ void __launch_bounds__(256, 1) sap_smem_kernel(const float2* __restri
       Us[(2 * q) * Vb + t] = make_float2(f.x, f.y);
       Us[(2 * q + 1) * Vb + t] = make_float2(f.z, f.w);
     }
-    // clover rows as 16-byte pairs (entries b, b + 1); the upper triangle kept
-    const float4* C4 = reinterpret_cast<const float4*>(Cl + s * 72);
+    // the packed clover (two upper triangles of 21 entries, each padded to 22) with 16-byte loads
+    const float4* C4 = reinterpret_cast<const float4*>(Cl + s * kClPacked);
 #pragma unroll
     for (int hh = 0; hh < 2; ++hh)
 #pragma unroll
-      for (int a = 0; a < 6; ++a)
-#pragma unroll
-        for (int b2 = a / 2; b2 < 3; ++b2) {
-          const float4 f = __ldg(C4 + (hh * 6 + a) * 3 + b2);
-          if (2 * b2 >= a) Cs[(hh * 21 + tri_index(a, 2 * b2)) * Vb + t] = make_float2(f.x, f.y);
-          Cs[(hh * 21 + tri_index(a, 2 * b2 + 1)) * Vb + t] = make_float2(f.z, f.w);
-        }
+      for (int k = 0; k < 11; ++k) {
+        const float4 f = __ldg(C4 + hh * 11 + k);
+        Cs[(hh * 21 + 2 * k) * Vb + t] = make_float2(f.x, f.y);
+        if (2 * k + 1 < 21) Cs[(hh * 21 + 2 * k + 1) * Vb + t] = make_float2(f.z, f.w);
+      }
   }
   __syncthreads();  // links and clover staged
   if (act) {
@@ -770,6 +794,24 @@ FineGeom fine_geom(const amg_coarse* h) {
   g.V = h->g.V;
   g.Vb = (int)h->g.Vb;
   return g;
+}
+
+// FP64 clover blocks [V][2][6][6] -> FP32 packed upper triangles [V][2][22] (tri_index order, the last
+// entry of each chirality zero)
+__global__ void clover_pack_kernel(const double2* __restrict__ in, float2* __restrict__ out, long long V) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < V * 44; e += (long long)gridDim.x * blockDim.x) {
+    const long long s = e / 44;
+    const int hh = (int)(e % 44) / 22, k = (int)(e % 22);
+    float2 v = make_float2(0.f, 0.f);
+    if (k < 21) {
+      int a = 0;
+      while (tri_index(a, 5) < k) ++a;  // row of entry k: the first row whose last entry is >= k
+      const int b = a + (k - tri_index(a, a));
+      const double2 d = in[(s * 2 + hh) * 36 + a * 6 + b];
+      v = make_float2((float)d.x, (float)d.y);
+    }
+    out[e] = v;
+  }
 }
 
 template <typename T>
@@ -1159,17 +1201,17 @@ amg_status amg_setup_fine(amg_handle h, const void* d_U, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   h->last_stream = st;
   amg_internal_free_fine(h);
-  const long long nU = h->g.V * 36, nC = h->g.V * 72;
+  const long long nU = h->g.V * 36;
   if (fine_fp64(h)) {
     AMG_CUDA_TRY(cudaMalloc(&h->fU, nU * sizeof(double2)));
     AMG_CUDA_TRY(cudaMemcpyAsync(h->fU, d_U, nU * sizeof(double2), cudaMemcpyDeviceToDevice, st));
     h->fC = h->clover;
   } else {
     AMG_CUDA_TRY(cudaMalloc(&h->fU, nU * sizeof(float2)));
-    AMG_CUDA_TRY(cudaMalloc(&h->fC, nC * sizeof(float2)));
+    AMG_CUDA_TRY(cudaMalloc(&h->fC, h->g.V * kClPacked * sizeof(float2)));
     to_prec_kernel<float><<<4 * amg_sm_count(), 256, 0, st>>>((const double2*)d_U, (float2*)h->fU, nU);
     AMG_LAUNCH_CHECK();
-    to_prec_kernel<float><<<4 * amg_sm_count(), 256, 0, st>>>(h->clover, (float2*)h->fC, nC);
+    clover_pack_kernel<<<4 * amg_sm_count(), 256, 0, st>>>(h->clover, (float2*)h->fC, h->g.V);
     AMG_LAUNCH_CHECK();
     h->launches += 2;
   }
