@@ -588,10 +588,10 @@ __global__ void r_to_fp32_kernel(const double2* __restrict__ R, float2* __restri
 // ------------------------------------------------------------------ host driver
 static int round_up(int a, int b) { return (a + b - 1) / b * b; }
 
-amg_status amg_internal_setup(amg_coarse* h, const double2* U, const double2* tv, cudaStream_t st) {
+// The setup's steps; the caller owns the timing events and frees `part` if a step fails.
+static amg_status setup_body(amg_coarse* h, const double2* U, const double2* tv, cudaStream_t st, cudaEvent_t (&ev)[5],
+                             double2*& part) {
   const Geom& g = h->g;
-  cudaEvent_t ev[5];
-  for (int k = 0; k < 5; ++k) AMG_CUDA_TRY(cudaEventCreate(&ev[k]));
   AMG_CUDA_TRY(cudaEventRecord(ev[0], st));
   // clover
   {
@@ -614,7 +614,6 @@ amg_status amg_internal_setup(amg_coarse* h, const double2* U, const double2* tv
   }
   AMG_CUDA_TRY(cudaEventRecord(ev[2], st));
   // assembly
-  double2* part = nullptr;
   const size_t part_elems = (size_t)g.Vc * 5 * 2 * g.nc * g.nc;
   AMG_CUDA_TRY(cudaMallocAsync((void**)&part, part_elems * sizeof(double2), st));
   if (h->p.setup_arith == AMG_SETUP_F32PAIR) {
@@ -647,6 +646,7 @@ amg_status amg_internal_setup(amg_coarse* h, const double2* U, const double2* tv
   }
   AMG_CUDA_TRY(cudaEventRecord(ev[3], st));
   AMG_CUDA_TRY(cudaFreeAsync(part, st));
+  part = nullptr;
   // storage precisions
   {
     const unsigned nblk = (unsigned)(g.Vc * 9);
@@ -671,7 +671,6 @@ amg_status amg_internal_setup(amg_coarse* h, const double2* U, const double2* tv
   AMG_CUDA_TRY(cudaEventRecord(ev[4], st));
   AMG_CUDA_TRY(cudaEventSynchronize(ev[4]));
   for (int k = 0; k < 4; ++k) cudaEventElapsedTime(&h->setup_ms[k], ev[k], ev[k + 1]);
-  for (int k = 0; k < 5; ++k) cudaEventDestroy(ev[k]);
   unsigned e = 0;
   AMG_CUDA_TRY(cudaMemcpy(&e, h->err, sizeof(unsigned), cudaMemcpyDeviceToHost));
   if (e & AMG_EBIT_RANK) return AMG_ERR_RANK_DEFICIENT;
@@ -680,4 +679,23 @@ amg_status amg_internal_setup(amg_coarse* h, const double2* U, const double2* tv
     return AMG_ERR_CUDA;
   }
   return AMG_OK;
+}
+
+amg_status amg_internal_setup(amg_coarse* h, const double2* U, const double2* tv, cudaStream_t st) {
+  cudaEvent_t ev[5] = {};
+  double2* part = nullptr;
+  amg_status s = AMG_OK;
+  for (int k = 0; k < 5 && s == AMG_OK; ++k) {
+    const cudaError_t c = cudaEventCreate(&ev[k]);
+    if (c != cudaSuccess) {
+      amg_note_cuda_error(__FILE__, __LINE__, c);
+      ev[k] = nullptr;
+      s = AMG_ERR_CUDA;
+    }
+  }
+  if (s == AMG_OK) s = setup_body(h, U, tv, st, ev, part);
+  if (part) cudaFreeAsync(part, st);  // a step failed between the allocation and its release
+  for (int k = 0; k < 5; ++k)
+    if (ev[k]) cudaEventDestroy(ev[k]);
+  return s;
 }
