@@ -59,3 +59,30 @@ def test_reference_arm_runs_the_gpu_arms_step_on_every_core(monkeypatch):
     cores = len(os.sched_getaffinity(0))
     assert res["cpu_baseline"]["cores"] == res["cpu_baseline"]["threads"] == cores
     assert res["value"] > 0 and res["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_setup_report_counts_the_rank6_sums():
+    # 48^3 x 96, Ntv = 24: per fine site four hop jobs over all (2 Ntv)^2 entries and the self job
+    # over its two chirality-diagonal quadrants, six rows each, 8 flops per complex multiply-add
+    V, ntv = 48 ** 3 * 96, 24
+    per_site = 6 * (4 * (2 * ntv) ** 2 + 2 * ntv ** 2)
+    flop = 8 * V * per_site
+    rep = bench.setup_report([150.0, 860.0, 1742.0, 25.0], V, ntv)
+    assert rep["assembly_tflop"] == round(flop / 1e12, 3) == 5.284
+    assert abs(rep["assembly_fp64_equiv_tflops"] - flop / 1.742 / 1e12) < 1e-3
+    assert rep["assembly"] == 1742.0 and rep["gram_schmidt"] == 860.0
+    assert rep["fp64_peak_tflops"] == 1.25 and rep["assembly_arith"] == "f32pair"
+
+
+def test_fine_grid_byte_models():
+    # FP32 complex = 8 bytes: D reads 4 links (4 x 9), the clover as two Hermitian upper triangles
+    # (2 x 21), psi (12) and writes out (12); a SAP half sweep per site of its colour reads the
+    # links, the clover, y and x and writes x, and reads the other colour's x once
+    c8 = 8
+    d = (4 * 9 + 2 * 21 + 12 + 12) * c8
+    sap_colour_site = (4 * 9 + 2 * 21 + 3 * 12) * c8
+    assert d == 816
+    assert (sap_colour_site + 12 * c8) // 2 == 504
+    import inspect
+    src = inspect.getsource(bench.run_vcycle)
+    assert "d_bytes = V * 816" in src and "half_bytes = V * 504" in src
