@@ -331,6 +331,31 @@ __device__ __forceinline__ void cta_alpha(T v[3], double* red, C& al, bool& ok) 
   ok = out[2] != 0.0;
 }
 
+// The same coefficient with one barrier: each warp's lane 0 writes the warp's partial sums to its
+// slot of red (3 values per warp, FP32), and after the barrier every thread sums the slots in warp
+// order and divides, so that all threads hold the same alpha (the order and the arithmetic of
+// cta_alpha, hence the same value).  Callers alternate between two red buffers from one step to the
+// next, so that a step's writes never meet the previous step's reads.
+__device__ __forceinline__ void cta_alpha_all(float v[3], float* red, float2& al, bool& ok) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+  if (lane == 0)
+    for (int k = 0; k < 3; ++k) red[warp * 3 + k] = v[k];
+  __syncthreads();
+  float sp = 0, sr = 0, si = 0;
+  for (int w = 0; w < nw; ++w) {
+    sp += red[w * 3];
+    sr += red[w * 3 + 1];
+    si += red[w * 3 + 2];
+  }
+  ok = sp > 0;
+  al.x = ok ? sr / sp : 0.f;
+  al.y = ok ? si / sp : 0.f;
+}
+
 // Intra-block hops of the block operator B at local site t: neighbours' rho from shared memory
 // (component-major: rho[q * Vb + t]), links from global memory.
 template <int mu, typename C>
@@ -523,7 +548,8 @@ __global__ void __launch_bounds__(256, 1) sap_smem_kernel(const float2* __restri
   float2* Us = reinterpret_cast<float2*>(smem);
   float2* Cs = Us + (size_t)36 * Vb;
   float2* rho = Cs + (size_t)42 * Vb;
-  double* red = reinterpret_cast<double*>(rho + (size_t)12 * Vb);
+  // two buffers of the MR coefficient's warp sums, 3 floats per warp each
+  float* redf = reinterpret_cast<float*>(rho + (size_t)12 * Vb);
   const int r = blockIdx.y;
   const long long k = blockIdx.x;
   const int half = g.Lc[0] / 2;
@@ -611,7 +637,8 @@ __global__ void __launch_bounds__(256, 1) sap_smem_kernel(const float2* __restri
     }
     float2 al;
     bool ok;
-    cta_alpha(v, red, al, ok);  // also orders every read of rho before the writes below
+    // also orders every read of rho before the writes below
+    cta_alpha_all(v, redf + (it & 1) * 3 * ((blockDim.x + 31) >> 5), al, ok);
     if (act && ok) {
 #pragma unroll
       for (int q = 0; q < 12; ++q) {
@@ -853,8 +880,8 @@ amg_status launch_sap(amg_coarse* h, const void* y, void* x, int nrhs, int n_cyc
   using C = typename Cx<T>::type;
   const int threads = (h->g.Vb + 31) / 32 * 32;
   if (sizeof(T) == 4) {
-    // links, clover and rho of a block in shared memory
-    const size_t sm2 = (size_t)h->g.Vb * (36 + 42 + 12) * sizeof(float2) + (size_t)(threads / 32 + 1) * 3 * sizeof(double);
+    // links, clover and rho of a block, then two buffers of the MR coefficient's warp sums
+    const size_t sm2 = (size_t)h->g.Vb * (36 + 42 + 12) * sizeof(float2) + (size_t)(threads / 32) * 2 * 3 * sizeof(float);
     if (threads <= 256 && sm2 <= 227 * 1024) {
       AMG_CUDA_TRY(cudaFuncSetAttribute(sap_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
       const dim3 grid((unsigned)(h->g.Vc / 2), (unsigned)nrhs);
