@@ -473,17 +473,65 @@ __global__ void __launch_bounds__(256) sap_kernel(const typename Cx<T>::type* __
 }
 
 // The same half sweep with the block's links and clover staged in shared memory once, so that
-// the MR steps read no global memory (FP32; a 4^4 block takes 74 KB of links, 86 KB of clover and
-// 25 KB of rho).  Layouts are component-major, [component][Vb], so that the threads of a warp (one
-// site each) read consecutive words: links [mu][9][Vb]; clover per chirality as its upper triangle
-// with the diagonal, [2][21][Vb] (the blocks are Hermitian, C_ba = conj(C_ab)); rho [12][Vb].
-__device__ __forceinline__ void site_term_packed(const float2* Cs, int Vb, int t, float mass, const float2 p[12],
+// the MR steps read no global memory (FP32; a 4^4 block takes 74 KB of links, 90 KB of clover and
+// 25 KB of rho).  Every staged record keeps its HBM order in pairs of entries, one float4 per pair,
+// laid out [pair][Vb]: the threads of a warp (one site each) then read 512 consecutive bytes with
+// 16-byte loads, and the staging copies the 16-byte pieces as they lie in HBM (cp.async, no
+// register round trip).  Links [18][Vb] (the site's 36 entries, 9 per direction); clover [22][Vb]
+// (per chirality the upper triangle with the diagonal, 21 entries padded to 22: the blocks are
+// Hermitian, C_ba = conj(C_ab)); rho [6][Vb].
+__device__ __forceinline__ float2 lo2(float4 f) { return make_float2(f.x, f.y); }
+__device__ __forceinline__ float2 hi2(float4 f) { return make_float2(f.z, f.w); }
+// Entry e of a staged record at local site t (the low or high half of pair e / 2)
+__device__ __forceinline__ float2 staged_entry(const float4* S, int Vb, int t, int e) {
+  return reinterpret_cast<const float2*>(S + (size_t)(e >> 1) * Vb + t)[e & 1];
+}
+// The link of direction mu at local site t: entries 9 mu .. 9 mu + 8, four pairs and one half
+template <int mu>
+__device__ __forceinline__ void staged_link(const float4* Us, int Vb, int t, float2 u[9]) {
+  constexpr int e0 = 9 * mu, o = e0 & 1, p0 = e0 >> 1;
+  if (o) u[0] = staged_entry(Us, Vb, t, e0);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float4 f = Us[(size_t)(p0 + o + k) * Vb + t];
+    u[o + 2 * k] = lo2(f);
+    u[o + 2 * k + 1] = hi2(f);
+  }
+  if (!o) u[8] = staged_entry(Us, Vb, t, e0 + 8);
+}
+__device__ __forceinline__ void staged_spinor(const float4* R, int Vb, int t, float2 p[12]) {
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const float4 f = R[(size_t)k * Vb + t];
+    p[2 * k] = lo2(f);
+    p[2 * k + 1] = hi2(f);
+  }
+}
+__device__ __forceinline__ void store_spinor(float4* R, int Vb, int t, const float2 p[12]) {
+#pragma unroll
+  for (int k = 0; k < 6; ++k) R[(size_t)k * Vb + t] = make_float4(p[2 * k].x, p[2 * k].y, p[2 * k + 1].x, p[2 * k + 1].y);
+}
+// 16-byte global -> shared copy that bypasses the registers (and L1)
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
+__device__ __forceinline__ void site_term_packed(const float4* Cs, int Vb, int t, float mass, const float2 p[12],
                                                  float2 out[12]) {
 #pragma unroll
   for (int hh = 0; hh < 2; ++hh) {
     float2 c[21];
 #pragma unroll
-    for (int k = 0; k < 21; ++k) c[k] = Cs[(hh * 21 + k) * Vb + t];
+    for (int k = 0; k < 10; ++k) {
+      const float4 f = Cs[(size_t)(hh * 11 + k) * Vb + t];
+      c[2 * k] = lo2(f);
+      c[2 * k + 1] = hi2(f);
+    }
+    c[20] = staged_entry(Cs, Vb, t, hh * 22 + 20);
 #pragma unroll
     for (int a = 0; a < 6; ++a) {
       float2 acc = zscale(p[hh * 6 + a], mass);
@@ -498,21 +546,17 @@ __device__ __forceinline__ void site_term_packed(const float2* Cs, int Vb, int t
 }
 
 template <int mu>
-__device__ __forceinline__ void block_hops_smem(const float2* Us, const float2* rho, int Vb, int t, const int lc[4],
+__device__ __forceinline__ void block_hops_smem(const float4* Us, const float4* rho, int Vb, int t, const int lc[4],
                                                 int bmu, int stride, float2 o[12]) {
   float2 p[12], u[9];
   if (lc[mu] + 1 < bmu) {
-#pragma unroll
-    for (int q = 0; q < 12; ++q) p[q] = rho[q * Vb + t + stride];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) u[k] = Us[(mu * 9 + k) * Vb + t];
+    staged_spinor(rho, Vb, t + stride, p);
+    staged_link<mu>(Us, Vb, t, u);
     hop_u<true, mu>(u, p, o);
   }
   if (lc[mu] > 0) {
-#pragma unroll
-    for (int q = 0; q < 12; ++q) p[q] = rho[q * Vb + t - stride];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) u[k] = Us[(mu * 9 + k) * Vb + t - stride];
+    staged_spinor(rho, Vb, t - stride, p);
+    staged_link<mu>(Us, Vb, t - stride, u);
     hop_u<false, mu>(u, p, o);
   }
 }
@@ -521,19 +565,17 @@ __device__ __forceinline__ void block_hops_smem(const float2* Us, const float2* 
 // from the staged block where they lie in it: the forward link always, the backward one unless the
 // neighbour is outside the block.
 template <int mu>
-__device__ __forceinline__ void residual_hops(const FineGeom& g, const float2* __restrict__ U, const float2* Us,
+__device__ __forceinline__ void residual_hops(const FineGeom& g, const float2* __restrict__ U, const float4* Us,
                                               const float2* __restrict__ v, long long s, const int x[4], const int lc[4],
                                               int Vb, int t, int stride, int nrhs, int r, float2 o[12]) {
   float2 p[12], u[9];
   load12(v, nbr_site<mu, 1>(g, s, x), nrhs, r, p);
-#pragma unroll
-  for (int k = 0; k < 9; ++k) u[k] = Us[(mu * 9 + k) * Vb + t];
+  staged_link<mu>(Us, Vb, t, u);
   hop_u<true, mu>(u, p, o);
   const long long sb = nbr_site<mu, -1>(g, s, x);
   load12(v, sb, nrhs, r, p);
   if (lc[mu] > 0) {
-#pragma unroll
-    for (int k = 0; k < 9; ++k) u[k] = Us[(mu * 9 + k) * Vb + t - stride];
+    staged_link<mu>(Us, Vb, t - stride, u);
   } else {
     load_link<mu>(U + (sb * 4 + mu) * 9, u);
   }
@@ -545,11 +587,11 @@ __global__ void __launch_bounds__(256, 1) sap_smem_kernel(const float2* __restri
                                                           FineGeom g, float mass, int nrhs, int colour, int n_mr) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int Vb = g.Vb;
-  float2* Us = reinterpret_cast<float2*>(smem);
-  float2* Cs = Us + (size_t)36 * Vb;
-  float2* rho = Cs + (size_t)42 * Vb;
+  float4* Us = reinterpret_cast<float4*>(smem);
+  float4* Cs = Us + (size_t)18 * Vb;
+  float4* rho = Cs + (size_t)22 * Vb;
   // two buffers of the MR coefficient's warp sums, 3 floats per warp each
-  float* redf = reinterpret_cast<float*>(rho + (size_t)12 * Vb);
+  float* redf = reinterpret_cast<float*>(rho + (size_t)6 * Vb);
   const int r = blockIdx.y;
   const long long k = blockIdx.x;
   const int half = g.Lc[0] / 2;
@@ -577,25 +619,15 @@ __global__ void __launch_bounds__(256, 1) sap_smem_kernel(const float2* __restri
   const int st1 = g.B[0], st2 = g.B[0] * g.B[1], st3 = g.B[0] * g.B[1] * g.B[2];
   float2 o[12], e[12];
   if (act) {
-    // stage this site's links and clover
+    // stage this site's links (288 bytes) and packed clover (352 bytes) as they lie in HBM
     const float4* U4 = reinterpret_cast<const float4*>(U + s * 36);
 #pragma unroll
-    for (int q = 0; q < 18; ++q) {
-      const float4 f = __ldg(U4 + q);
-      Us[(2 * q) * Vb + t] = make_float2(f.x, f.y);
-      Us[(2 * q + 1) * Vb + t] = make_float2(f.z, f.w);
-    }
-    // the packed clover (two upper triangles of 21 entries, each padded to 22) with 16-byte loads
+    for (int q = 0; q < 18; ++q) cp_async16(Us + (size_t)q * Vb + t, U4 + q);
     const float4* C4 = reinterpret_cast<const float4*>(Cl + s * kClPacked);
 #pragma unroll
-    for (int hh = 0; hh < 2; ++hh)
-#pragma unroll
-      for (int k = 0; k < 11; ++k) {
-        const float4 f = __ldg(C4 + hh * 11 + k);
-        Cs[(hh * 21 + 2 * k) * Vb + t] = make_float2(f.x, f.y);
-        if (2 * k + 1 < 21) Cs[(hh * 21 + 2 * k + 1) * Vb + t] = make_float2(f.z, f.w);
-      }
+    for (int q = 0; q < 22; ++q) cp_async16(Cs + (size_t)q * Vb + t, C4 + q);
   }
+  cp_async_wait_all();
   __syncthreads();  // links and clover staged
   if (act) {
     // residual r = y - D x on this site (full D: neighbours outside the block have the other colour);
@@ -610,9 +642,10 @@ __global__ void __launch_bounds__(256, 1) sap_smem_kernel(const float2* __restri
     load12(y, s, nrhs, r, p);
 #pragma unroll
     for (int q = 0; q < 12; ++q) {
-      rho[q * Vb + t] = zsub(p[q], o[q]);
+      p[q] = zsub(p[q], o[q]);
       e[q] = zzero<float2>();
     }
+    store_spinor(rho, Vb, t, p);
   }
   __syncthreads();
 #pragma unroll 1
@@ -621,8 +654,7 @@ __global__ void __launch_bounds__(256, 1) sap_smem_kernel(const float2* __restri
     float v[3] = {0, 0, 0};
     float2 rr[12];
     if (act) {
-#pragma unroll
-      for (int q = 0; q < 12; ++q) rr[q] = rho[q * Vb + t];
+      staged_spinor(rho, Vb, t, rr);
       site_term_packed(Cs, Vb, t, mass, rr, o);
       block_hops_smem<0>(Us, rho, Vb, t, lc, g.B[0], 1, o);
       block_hops_smem<1>(Us, rho, Vb, t, lc, g.B[1], st1, o);
@@ -640,21 +672,36 @@ __global__ void __launch_bounds__(256, 1) sap_smem_kernel(const float2* __restri
     // also orders every read of rho before the writes below
     cta_alpha_all(v, redf + (it & 1) * 3 * ((blockDim.x + 31) >> 5), al, ok);
     if (act && ok) {
+      float2 nr[12];
 #pragma unroll
       for (int q = 0; q < 12; ++q) {
         zfma(e[q], al, rr[q]);
         float2 ap = zzero<float2>();
         zfma(ap, al, o[q]);
-        rho[q * Vb + t] = zsub(rr[q], ap);
+        nr[q] = zsub(rr[q], ap);
       }
+      store_spinor(rho, Vb, t, nr);
     }
     __syncthreads();
   }
   if (act) {
+    if (nrhs == 1) {  // one column: the site's 96 bytes as six 16-byte words
+      float4* x4 = reinterpret_cast<float4*>(x + s * 12);
 #pragma unroll
-    for (int q = 0; q < 12; ++q) {
-      const long long idx = (s * 12 + q) * nrhs + r;
-      x[idx] = zadd(x[idx], e[q]);
+      for (int k = 0; k < 6; ++k) {
+        float4 f = x4[k];
+        f.x += e[2 * k].x;
+        f.y += e[2 * k].y;
+        f.z += e[2 * k + 1].x;
+        f.w += e[2 * k + 1].y;
+        x4[k] = f;
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 12; ++q) {
+        const long long idx = (s * 12 + q) * nrhs + r;
+        x[idx] = zadd(x[idx], e[q]);
+      }
     }
   }
 }
@@ -881,7 +928,7 @@ amg_status launch_sap(amg_coarse* h, const void* y, void* x, int nrhs, int n_cyc
   const int threads = (h->g.Vb + 31) / 32 * 32;
   if (sizeof(T) == 4) {
     // links, clover and rho of a block, then two buffers of the MR coefficient's warp sums
-    const size_t sm2 = (size_t)h->g.Vb * (36 + 42 + 12) * sizeof(float2) + (size_t)(threads / 32) * 2 * 3 * sizeof(float);
+    const size_t sm2 = (size_t)h->g.Vb * (18 + 22 + 6) * sizeof(float4) + (size_t)(threads / 32) * 2 * 3 * sizeof(float);
     if (threads <= 256 && sm2 <= 227 * 1024) {
       AMG_CUDA_TRY(cudaFuncSetAttribute(sap_smem_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
       const dim3 grid((unsigned)(h->g.Vc / 2), (unsigned)nrhs);
