@@ -55,9 +55,9 @@ TRAFFIC_MRHS_FP32 = 1449390080
 # DRAM traffic / algorithmic bytes of the fused batch launch, from the reduced-volume capture
 # (profiles/batch_kernel_small_mixed.md); the full launch's traffic is taken in that proportion
 BATCH_TRAFFIC_RATIO = 0.990
-# DRAM traffic / algorithmic bytes of one SAP half sweep, from the 16^4 capture (profiles/sap_16x4.md);
-# the 32^4 launch is taken in proportion.  None until the current kernel has been captured.
-SAP_TRAFFIC_RATIO = None
+# DRAM traffic / algorithmic bytes of one SAP half sweep, from the 16^4 capture (profiles/sap_16x4.md:
+# 35.56 MB for 65,536 sites x 504 B); the 32^4 launch is taken in proportion
+SAP_TRAFFIC_RATIO = 1.077
 METRIC = "coarse-grid correction GB/s & % HBM roofline; batched-mixed vs plain speedup"
 WORKLOAD = "fp32_32^4_b4_ntv20: 32^4 Wilson-clover, 4^4 blocks -> 8^4 coarse, Ntv=20, 1 RHS, " \
            "FP64 setup, FP32 R and D_c; step = R y, FGMRES(30) to 0.05 (<=200 applies), P x_c"
