@@ -719,7 +719,29 @@ def run_vcycle(args):
     t0 = time.perf_counter()
     sinfo = amg.amg_solve(h, vp, y, u, 1, tol=1e-5, restart=30, max_applies=200, stream=st)
     t_solve = time.perf_counter() - t0
+    # Three levels: the coarse lattice in 2^4 blocks (Ntv2 = 8 random level-1 test vectors), one
+    # two-grid cycle on level 1 (2 MR steps on D_c before and after, level-2 FGMRES(30) to 0.05) in
+    # place of the coarse FGMRES of every V-cycle.
+    B2, ntv2, n_mr2 = (2, 2, 2, 2), 8, 2
+    Lc = tuple(L[m] // B[m] for m in range(4))
+    tv2 = sd.coarse_vector(SEED + 2, NTV, ntv2, Vc, torch.complex128)
+    p2 = amg.make_params(Lc, B2, ntv2, 1, M0, CSW, amg.AMG_FP32, amg.AMG_FP32, amg.AMG_FP32)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h2, _ = amg.amg_setup_level2(h, p2, tv2, st)
+    t_setup2 = time.perf_counter() - t0
+    del tv2
+    amg.amg_attach_level2(h, h2, amg.make_level2_params(n_mr=n_mr2, restart=RESTART, max_applies=MAX_APPLIES,
+                                                        tol=TOL))
+    t3, _ = _timed_steps(lambda: amg.amg_vcycle(h, vp, y, x, 1, st), args.steps, args.warmup, st, flush)
+    t0 = time.perf_counter()
+    sinfo3 = amg.amg_solve(h, vp, y, u, 1, tol=1e-5, restart=30, max_applies=200, stream=st)
+    t_solve3 = time.perf_counter() - t0
+    amg.amg_attach_level2(h, None)
     status = amg.amg_sync_status(h)
+    if status == amg.AMG_OK:
+        status = amg.amg_sync_status(h2)
+    amg.amg_destroy(h2)
     amg.amg_destroy(h)
     if status != amg.AMG_OK:
         raise RuntimeError(amg.amg_status_string(status))
@@ -751,6 +773,13 @@ def run_vcycle(args):
                                        "frac": round(sap_gbs / peaks["hbm_gbs"], 4)}},
         "outer_solve": {"tol": 1e-5, "applies_of_D": sinfo[0][0], "relres": sinfo[0][1],
                         "seconds": round(t_solve, 4), "restart": 30},
+        "three_level": {"level2": "%dx%dx%dx%d coarse lattice in 2^4 blocks -> %dx%dx%dx%d, Ntv2 = %d random level-1 "
+                                  "test vectors" % (Lc + tuple(Lc[m] // B2[m] for m in range(4)) + (ntv2,)),
+                        "cycle": "one two-grid cycle on level 1 per V-cycle: %d MR steps on D_c before and after, "
+                                 "level-2 FGMRES(%d) to %g" % (n_mr2, RESTART, TOL),
+                        "setup2_ms": round(1000 * t_setup2, 2), "vcycle_ms": round(1000 * t3 / args.steps, 4),
+                        "outer_solve": {"tol": 1e-5, "applies_of_D": sinfo3[0][0], "relres": sinfo3[0][1],
+                                        "seconds": round(t_solve3, 4), "restart": 30}},
         "clocks": clk,
     }
 

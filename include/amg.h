@@ -292,6 +292,65 @@ amg_status amg_adaptive_setup(amg_handle h, const amg_vcycle_params *vp, const v
 amg_status amg_solve(amg_handle h, const amg_vcycle_params *vp, const void *d_f, void *d_u, int nrhs,
                      double tol, int restart, int max_applies, void *stream, double *info);
 
+/* ------------------------------------------------------------------ a third level.  Sec. 3 builds
+ * two levels and notes that the method carries over to three, save for a smoother on a coarse
+ * grid, which the paper does not have.  Here the coarse lattice is coarsened once more: blocks
+ * p2->B of coarse sites, each with two aggregates (the l and r halves of every coarse site's
+ * 2 ntv components, so that D_cc keeps the gamma_5 structure of D_c), aggregate dofs enumerated
+ * (site in block, lexicographic x fastest; component) slowest first.  R2 holds per aggregate the
+ * Gram-Schmidt orthonormalised test vectors (Alg. 5's construction one level down), P2 = R2^dag
+ * and D_cc = R2 D_c P2 (Eq. cgo).  The smoother on the coarse grid is n_mr minimal-residual steps
+ * on D_c from zero, run as FGMRES(1) (the one-vector case of Alg. 2's solver; each step after the
+ * first recomputes the residual, so n_mr steps take 2 n_mr - 1 applications of D_c).  Level-1
+ * vectors are coarse vectors of the level-1 handle ([Vc1][2][ntv1][nrhs]), level-2 vectors
+ * [Vc2][2][ntv2][nrhs], both in vec_prec. */
+
+/*
+ * amg_setup_level2 -- a level-2 handle from the level-1 handle h1 (its D_c) and the level-2 test
+ * vectors d_tv2 ([Vc1][2][ntv1][ntv2] complex double, device, not retained).  p2: L = the coarse
+ * lattice of h1 (L_mu / B_mu of h1), B = the level-2 blocks (every L_mu / B_mu >= 2), ntv = ntv2
+ * <= min(32, ntv1 V_block2), vec_prec = that of h1 (FP64 or FP32) with link_prec and r_prec equal
+ * to it, max_nrhs as for any handle.  The result is an ordinary coarse handle for D_cc
+ * (amg_coarse_apply, amg_coarse_solve, amg_export_R (R2), amg_export_Dc (D_cc), amg_destroy work on
+ * it) plus amg_restrict2 / amg_prolong2.  Setup in FP64; synchronises the stream.
+ * AMG_ERR_RANK_DEFICIENT (handle returned) if the test vectors lose rank on an aggregate.
+ */
+amg_status amg_setup_level2(amg_handle h1, const amg_params *p2, const void *d_tv2, void *stream,
+                            amg_handle *out);
+
+/* amg_restrict2 -- y_cc = R2 y_c (level-1 vector in, level-2 vector out; device, distinct). */
+amg_status amg_restrict2(amg_handle h2, const void *d_yc, void *d_ycc, int nrhs, void *stream);
+
+/* amg_prolong2 -- x_c = P2 x_cc (level-2 vector in, level-1 vector out, overwritten). */
+amg_status amg_prolong2(amg_handle h2, const void *d_xcc, void *d_xc, int nrhs, void *stream);
+
+/* Parameters of the two-grid cycle on level 1: n_mr minimal-residual steps on D_c before and after
+ * the correction (0: none), and the level-2 solve FGMRES(restart) to tol, at most max_applies
+ * applications of D_cc. */
+typedef struct {
+  int n_mr;
+  int restart;
+  int max_applies;
+  double tol;
+} amg_level2_params;
+
+/*
+ * amg_attach_level2 -- makes h2 (from amg_setup_level2 on h1) the third level of h1: from then on
+ * the coarse-grid correction inside amg_vcycle, amg_solve and amg_adaptive_setup's passes uses one
+ * two-grid cycle on level 1 (amg_two_grid) in place of the coarse FGMRES (vp's coarse_* fields are
+ * then unused), which makes the V-cycle a three-level one.  h2 = NULL detaches.  Destroying either
+ * handle detaches them.  lp is copied.
+ */
+amg_status amg_attach_level2(amg_handle h1, amg_handle h2, const amg_level2_params *lp);
+
+/*
+ * amg_two_grid -- one two-grid cycle for D_c x_c = y_c on level 1 with the attached level 2:
+ * x = MR(y); x += P2 x_cc, x_cc the level-2 FGMRES solution of D_cc x_cc = R2 (y - D_c x);
+ * x += MR(y - D_c x).  y_c and x_c device, distinct; x_c overwritten.  Its level-1 and level-2
+ * work vectors are allocated in h1 on first use.
+ */
+amg_status amg_two_grid(amg_handle h1, const void *d_yc, void *d_xc, int nrhs, void *stream);
+
 /*
  * amg_batch_cgc -- x_k = P_k D_ck R_k y_k for n lattices (handles hs[k]) in one
  * persistent launch [Alg. 2's restriction, coarse operator and prolongation; Sec. 3 runs its

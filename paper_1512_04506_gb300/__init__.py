@@ -56,6 +56,15 @@ class amg_vcycle_params(ctypes.Structure):
     ]
 
 
+class amg_level2_params(ctypes.Structure):
+    _fields_ = [
+        ("n_mr", ctypes.c_int),
+        ("restart", ctypes.c_int),
+        ("max_applies", ctypes.c_int),
+        ("tol", ctypes.c_double),
+    ]
+
+
 class AmgError(RuntimeError):
     def __init__(self, status, where):
         self.status = status
@@ -97,6 +106,11 @@ _proto = {
     "amg_batch_test_hook": [_vp, _i],
     "amg_solve_test_hook": [_vp, _i],
     "amg_grid_cap_test_hook": [_vp, _i],
+    "amg_setup_level2": [_vp, ctypes.POINTER(amg_params), _vp, _vp, ctypes.POINTER(_vp)],
+    "amg_restrict2": [_vp, _vp, _vp, _i, _vp],
+    "amg_prolong2": [_vp, _vp, _vp, _i, _vp],
+    "amg_attach_level2": [_vp, _vp, ctypes.POINTER(amg_level2_params)],
+    "amg_two_grid": [_vp, _vp, _vp, _i, _vp],
     "amg_export_R": [_vp, _vp],
     "amg_export_Dc": [_vp, _vp],
     "amg_export_clover": [_vp, _vp],
@@ -258,6 +272,36 @@ def amg_sap(h, y, x, nrhs=1, n_cycles=1, n_mr=4, stream=None):
 
 def amg_vcycle(h, vp, y, x, nrhs=1, stream=None):
     return _check(lib.amg_vcycle(h, ctypes.byref(vp), ptr(y), ptr(x), nrhs, stream_ptr(stream)), "amg_vcycle")
+
+
+def amg_setup_level2(h1, params2, tv2, stream=None, allow_rank_deficient=False):
+    """Level-2 handle from the level-1 handle h1 and level-1 test vectors tv2; returns (handle, status)."""
+    h = _vp()
+    st = lib.amg_setup_level2(h1, ctypes.byref(params2), ptr(tv2), stream_ptr(stream), ctypes.byref(h))
+    _check(st, "amg_setup_level2", (AMG_ERR_RANK_DEFICIENT,) if allow_rank_deficient else ())
+    return h.value, st
+
+
+def amg_restrict2(h2, yc, ycc, nrhs=1, stream=None):
+    return _check(lib.amg_restrict2(h2, ptr(yc), ptr(ycc), nrhs, stream_ptr(stream)), "amg_restrict2")
+
+
+def amg_prolong2(h2, xcc, xc, nrhs=1, stream=None):
+    return _check(lib.amg_prolong2(h2, ptr(xcc), ptr(xc), nrhs, stream_ptr(stream)), "amg_prolong2")
+
+
+def make_level2_params(n_mr=2, restart=30, max_applies=200, tol=0.05):
+    return amg_level2_params(n_mr, restart, max_applies, tol)
+
+
+def amg_attach_level2(h1, h2, lp=None):
+    """Makes h2 the third level of h1 (h2 None detaches)."""
+    return _check(lib.amg_attach_level2(h1, h2, ctypes.byref(lp) if lp is not None else None),
+                  "amg_attach_level2")
+
+
+def amg_two_grid(h1, yc, xc, nrhs=1, stream=None):
+    return _check(lib.amg_two_grid(h1, ptr(yc), ptr(xc), nrhs, stream_ptr(stream)), "amg_two_grid")
 
 
 def amg_adaptive_setup(h, vp, U, tv, n_setup=1, stream=None, allow_rank_deficient=False):

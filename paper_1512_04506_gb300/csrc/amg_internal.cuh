@@ -163,6 +163,15 @@ struct amg_coarse {
   void* fC = nullptr;         // clover [V][2][6][6] in vec_prec (aliases clover for FP64)
   void* fwork = nullptr;      // outer FGMRES workspace (fine Krylov basis, Z vectors, sums)
   size_t fwork_bytes = 0;
+  // Three levels (level2.cu).  A level-2 handle (level == 2) holds R2 in R64 ([Vc2][2][ntv2]
+  // [Vb2 ntv1], row j = conj(q_j)), D_cc in Dc64 / Dq and its neighbour table; its geometry g has
+  // L = the level-1 lattice, B = the level-2 blocks, V = Vc1 and nagg = Vb2 ntv1.
+  int level = 1;
+  amg_coarse* next = nullptr;  // level 1: the attached level-2 handle (its two-grid cycle replaces the coarse solve)
+  amg_coarse* prev = nullptr;  // level 2: the level-1 handle it is attached to
+  amg_level2_params l2p = {};  // level 1: the two-grid cycle's parameters
+  void* l2work = nullptr;      // level 1: two level-1 and two level-2 vectors of the two-grid cycle
+  size_t l2work_bytes = 0;
 };
 
 // Grid of a grid-stride launch over `items` work items with `resident` CTAs resident at once: the
@@ -215,6 +224,9 @@ inline size_t vec_elem_bytes(amg_prec p) {
 inline size_t coarse_elem_bytes(const amg_coarse* h) { return h->p.vec_prec == AMG_FP64 ? 16 : 8; }
 
 // Entry points of the translation units, used by the C ABI layer.
+// Three levels: the coarse-grid correction of the fine level with the attached level-2 handle's
+// two-grid cycle in place of the coarse solve (restriction, one two-grid cycle, prolongation).
+amg_status amg_internal_cgc3(amg_coarse* h, const void* y, void* x, int nrhs, cudaStream_t s);
 amg_status amg_internal_setup(amg_coarse* h, const double2* U, const double2* tv, cudaStream_t s);
 // assembly partial sums ([Vc][5 jobs][2 slots][nc][nc], the layout combine_kernel reads) in pairs of floats
 amg_status amg_internal_assemble_pair(const Geom& g, const double2* R, const double2* U, const double2* clov,

@@ -83,6 +83,9 @@ Geom make_geom(const amg_params* p) {
 
 void free_handle(amg_coarse* h) {
   if (!h) return;
+  if (h->next) h->next->prev = nullptr;  // an attached level 2 / level 1 forgets this handle
+  if (h->prev) h->prev->next = nullptr;
+  cudaFree(h->l2work);
   cudaFree(h->clover);
   if (h->Rq != (void*)h->R64) cudaFree(h->Rq);
   cudaFree(h->R64);

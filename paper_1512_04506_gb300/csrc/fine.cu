@@ -985,7 +985,10 @@ amg_status check_vp(const amg_vcycle_params* vp) {
 
 amg_status vcycle_impl(amg_coarse* h, const amg_vcycle_params* vp, const void* y, void* x, int nrhs,
                        cudaStream_t st) {
-  AMG_TRY_INTERNAL(amg_cgc(h, y, x, nrhs, vp->coarse_tol, vp->coarse_restart, vp->coarse_max_applies, st, nullptr));
+  if (h->next)  // three levels: one two-grid cycle on level 1 in place of the coarse solve
+    AMG_TRY_INTERNAL(amg_internal_cgc3(h, y, x, nrhs, st));
+  else
+    AMG_TRY_INTERNAL(amg_cgc(h, y, x, nrhs, vp->coarse_tol, vp->coarse_restart, vp->coarse_max_applies, st, nullptr));
   if (vp->n_smoother > 0) AMG_TRY_INTERNAL(sap_any(h, y, x, nrhs, vp->n_smoother, vp->n_mr, st));
   return AMG_OK;
 }

@@ -83,3 +83,20 @@ def test_argument_validation_without_gpu(built):
     assert amg.lib.amg_setup_coarse(ctypes.byref(p), 16, 16, None, ctypes.byref(h)) == amg.AMG_ERR_UNSUPPORTED
     assert amg.lib.amg_restrict(None, 16, 16, 1, None) == amg.AMG_ERR_INVALID_ARG
     assert amg.lib.amg_destroy(None) == amg.AMG_ERR_INVALID_ARG
+
+
+def test_level2_params_layout_and_validation(built):
+    """amg_level2_params is int n_mr, restart, max_applies, double tol; the three-level calls
+    reject missing handles and parameters before any CUDA call."""
+    import paper_1512_04506_gb300 as amg
+    assert ctypes.sizeof(amg.amg_level2_params) == 24
+    assert amg.amg_level2_params.tol.offset == 16
+    h = ctypes.c_void_p()
+    p = amg.make_params((4, 4, 4, 4), (2, 2, 2, 2), 4)
+    assert amg.lib.amg_setup_level2(None, ctypes.byref(p), 16, None, ctypes.byref(h)) == amg.AMG_ERR_INVALID_ARG
+    assert amg.lib.amg_setup_level2(None, ctypes.byref(p), 16, None, None) == amg.AMG_ERR_INVALID_ARG
+    lp = amg.make_level2_params()
+    assert amg.lib.amg_attach_level2(None, None, ctypes.byref(lp)) == amg.AMG_ERR_INVALID_ARG
+    assert amg.lib.amg_two_grid(None, 16, 32, 1, None) == amg.AMG_ERR_INVALID_ARG
+    assert amg.lib.amg_restrict2(None, 16, 32, 1, None) == amg.AMG_ERR_INVALID_ARG
+    assert amg.lib.amg_prolong2(None, 16, 32, 1, None) == amg.AMG_ERR_INVALID_ARG
