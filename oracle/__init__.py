@@ -20,6 +20,10 @@ Modules (each function cites the passage of arXiv:1512.04506 it follows):
 * ``mg``      -- the two-level method around the coarse-grid correction: the
                  V-cycle (Alg. 1), the adaptive setup (Alg. 4) and the outer
                  FGMRES solve of D u = f (Sec. 1).
+* ``mg3``     -- a third level (Sec. 3 notes the method carries over): the
+                 coarse lattice coarsened once more, R2, D_cc = R2 D_c P2, a
+                 minimal-residual smoother on D_c, the two-grid cycle on level 1
+                 and the three-level V-cycle.
 
 All arithmetic is complex128.  Where the paper is silent (gamma basis, sign
 and normalisation of D, the clover term, boundary conditions) the readings
