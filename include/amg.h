@@ -336,10 +336,11 @@ typedef struct {
 
 /*
  * amg_attach_level2 -- makes h2 (from amg_setup_level2 on h1) the third level of h1: from then on
- * the coarse-grid correction inside amg_vcycle, amg_solve and amg_adaptive_setup's passes uses one
- * two-grid cycle on level 1 (amg_two_grid) in place of the coarse FGMRES (vp's coarse_* fields are
- * then unused), which makes the V-cycle a three-level one.  h2 = NULL detaches.  Destroying either
- * handle detaches them.  lp is copied.
+ * the coarse-grid correction inside amg_vcycle and amg_solve uses one two-grid cycle on level 1
+ * (amg_two_grid) in place of the coarse FGMRES (vp's coarse_* fields are then unused), which makes
+ * the V-cycle a three-level one.  h2 = NULL detaches.  Destroying either handle detaches them.  lp
+ * is copied.  amg_adaptive_setup rebuilds D_c and so refuses (AMG_ERR_INVALID_ARG) while a level 2
+ * is attached: detach, run it, then build and attach a new level 2.
  */
 amg_status amg_attach_level2(amg_handle h1, amg_handle h2, const amg_level2_params *lp);
 

@@ -1324,6 +1324,7 @@ amg_status amg_adaptive_setup(amg_handle h, const amg_vcycle_params* vp, const v
                               void* stream) {
   if (!h || !d_U || !d_tv || !aligned16(d_U) || !aligned16(d_tv) || n_setup < 0) return AMG_ERR_INVALID_ARG;
   AMG_TRY_INTERNAL(check_vp(vp));
+  if (h->next) return AMG_ERR_INVALID_ARG;  // an attached level 2 would keep D_cc of the old D_c
   if (!h->fU) return AMG_ERR_UNSUPPORTED;
   if (!sap_supported(h)) return AMG_ERR_UNSUPPORTED;
   cudaStream_t st = (cudaStream_t)stream;

@@ -181,3 +181,20 @@ def test_three_level_outer_solve_converges(amg, prec):
         assert amg.amg_sync_status(c.h1) == amg.AMG_OK
     finally:
         c.close()
+
+
+def test_adaptive_setup_refuses_with_level2_attached(amg, three):
+    """The adaptive setup rebuilds D_c, which would leave an attached D_cc stale: it refuses
+    until the level 2 is detached."""
+    c = three
+    vp = amg.make_vcycle_params(n_smoother=1, n_mr=2)
+    amg.amg_attach_level2(c.h1, c.h2, amg.make_level2_params())
+    try:
+        U = torch.from_numpy(si.links(c.seed, 0.3, si.all_sites(c.L))).cuda()
+        tv = torch.from_numpy(c.tvh.copy()).cuda()
+        with pytest.raises(amg.AmgError) as e:
+            amg.amg_adaptive_setup(c.h1, vp, U, tv, n_setup=0, stream=c.stream)
+        assert e.value.status == amg.AMG_ERR_INVALID_ARG
+    finally:
+        amg.amg_attach_level2(c.h1, None)
+    assert amg.amg_sync_status(c.h1) == amg.AMG_OK
