@@ -312,7 +312,9 @@ amg_status amg_solve(amg_handle h, const amg_vcycle_params *vp, const void *d_f,
  * <= min(32, ntv1 V_block2), vec_prec = that of h1 (FP64 or FP32) with link_prec and r_prec equal
  * to it, max_nrhs as for any handle.  The result is an ordinary coarse handle for D_cc
  * (amg_coarse_apply, amg_coarse_solve, amg_export_R (R2), amg_export_Dc (D_cc), amg_destroy work on
- * it) plus amg_restrict2 / amg_prolong2.  Setup in FP64; synchronises the stream.
+ * it) plus amg_restrict2 / amg_prolong2; the calls that need a fine lattice (amg_restrict,
+ * amg_prolong, amg_cgc, the batch calls, amg_export_clover, amg_setup_fine, amg_setup_evenodd)
+ * return AMG_ERR_UNSUPPORTED for it.  Setup in FP64; synchronises the stream.
  * AMG_ERR_RANK_DEFICIENT (handle returned) if the test vectors lose rank on an aggregate.
  */
 amg_status amg_setup_level2(amg_handle h1, const amg_params *p2, const void *d_tv2, void *stream,

@@ -277,6 +277,7 @@ extern "C" {
 
 amg_status amg_restrict(amg_handle h, const void* d_y, void* d_yc, int nrhs, void* stream) {
   AMG_TRY(check_apply_args(h, d_y, d_yc, nrhs));
+  if (h->level != 1) return AMG_ERR_UNSUPPORTED;  // a level-2 handle has no fine lattice
   h->last_stream = (cudaStream_t)stream;
   return amg_internal_restrict(h, d_y, d_yc, nrhs, (cudaStream_t)stream);
 }
@@ -290,6 +291,7 @@ amg_status amg_coarse_apply(amg_handle h, const void* d_xc, void* d_yc, int nrhs
 
 amg_status amg_prolong(amg_handle h, const void* d_xc, void* d_x, int nrhs, void* stream) {
   AMG_TRY(check_apply_args(h, d_xc, d_x, nrhs));
+  if (h->level != 1) return AMG_ERR_UNSUPPORTED;
   h->last_stream = (cudaStream_t)stream;
   return amg_internal_prolong(h, d_xc, d_x, nrhs, (cudaStream_t)stream);
 }
@@ -305,6 +307,7 @@ amg_status amg_coarse_solve(amg_handle h, const void* d_b, void* d_x, int nrhs, 
 amg_status amg_cgc(amg_handle h, const void* d_y, void* d_x, int nrhs, double tol, int restart,
                    int max_applies, void* stream, double* info) {
   AMG_TRY(check_apply_args(h, d_y, d_x, nrhs));
+  if (h->level != 1) return AMG_ERR_UNSUPPORTED;
   cudaStream_t st = (cudaStream_t)stream;
   h->last_stream = st;
   const size_t bytes = (size_t)h->g.Vc * h->g.nc * nrhs * coarse_elem_bytes(h);
@@ -328,6 +331,7 @@ amg_status amg_batch_cgc(const amg_handle* hs, int n, const void* const* d_y, vo
   if (!hs || n < 1 || !d_y || !d_x || !nrhs) return AMG_ERR_INVALID_ARG;
   for (int k = 0; k < n; ++k) {
     AMG_TRY(check_apply_args(hs[k], d_y[k], d_x[k], nrhs[k]));
+    if (hs[k]->level != 1) return AMG_ERR_UNSUPPORTED;
   }
   for (int k = 0; k < n; ++k) hs[k]->last_stream = (cudaStream_t)stream;
   return amg_internal_batch(const_cast<amg_coarse* const*>(hs), n, d_y, d_x, nrhs, (cudaStream_t)stream);
@@ -352,6 +356,7 @@ amg_status amg_export_Dc(amg_handle h, void* out) {
 
 amg_status amg_export_clover(amg_handle h, void* out) {
   if (!h) return AMG_ERR_INVALID_ARG;
+  if (h->level != 1) return AMG_ERR_UNSUPPORTED;
   return copy_out(h, out, h->clover, (size_t)h->g.V * 72 * sizeof(double2));
 }
 

@@ -495,6 +495,8 @@ extern "C" amg_status amg_batch_autotune(const amg_handle* hs, int n, const void
   if (!hs || n < 1 || !d_y || !d_x || !nrhs) return AMG_ERR_INVALID_ARG;
   for (int k = 0; k < n; ++k)
     if (!hs[k] || !d_y[k] || !d_x[k] || nrhs[k] < 1 || nrhs[k] > hs[k]->p.max_nrhs) return AMG_ERR_INVALID_ARG;
+  for (int k = 0; k < n; ++k)
+    if (hs[k]->level != 1) return AMG_ERR_UNSUPPORTED;  // a level-2 handle has no fine lattice
   cudaStream_t st = (cudaStream_t)stream;
   amg_coarse* const* H = const_cast<amg_coarse* const*>(hs);
   // tensor-core batches: ring stages x CTAs per SM; SIMT-only batches: threads per CTA x CTAs per SM

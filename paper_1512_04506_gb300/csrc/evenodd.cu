@@ -208,6 +208,7 @@ amg_status amg_internal_schur_apply(amg_coarse* h, const void* xe, void* ye, int
 
 extern "C" amg_status amg_setup_evenodd(amg_handle h, void* stream) {
   if (!h) return AMG_ERR_INVALID_ARG;
+  if (h->level != 1) return AMG_ERR_UNSUPPORTED;  // not offered on a level-2 handle
   const Geom& g = h->g;
   for (int mu = 0; mu < 4; ++mu)
     if (g.Lc[mu] % 2) return AMG_ERR_UNSUPPORTED;

@@ -1274,6 +1274,7 @@ extern "C" {
 
 amg_status amg_setup_fine(amg_handle h, const void* d_U, void* stream) {
   if (!h || !d_U || !aligned16(d_U)) return AMG_ERR_INVALID_ARG;
+  if (h->level != 1) return AMG_ERR_UNSUPPORTED;  // a level-2 handle has no fine lattice
   if (h->p.vec_prec != AMG_FP64 && h->p.vec_prec != AMG_FP32) return AMG_ERR_UNSUPPORTED;
   cudaStream_t st = (cudaStream_t)stream;
   h->last_stream = st;
